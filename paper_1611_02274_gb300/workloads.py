@@ -1,0 +1,200 @@
+"""Seeded synthetic workloads for batched ODE integration.
+
+This module only draws random inputs (initial conditions, per-system
+parameters, the shared mass-action network) with numpy's PCG64.  It holds
+none of the integrators' arithmetic: rate constants, stencils, stage
+combinations and error norms are computed by the consumers (the CUDA library
+and the CPU oracle), each in its own code.
+
+Layout is the structure-of-arrays layout of the paper's Section 3 (Source
+Code): unknown ``j`` of system ``i`` sits at ``y[j, i]`` (C order, i.e. the
+flat index ``i + nsys * j``), so neighbouring systems are neighbouring in
+memory.  Parameters use the same layout, ``params[p, i]``.
+
+Workload recipes (all FP64, generated on the host):
+
+* ``vdp``        van der Pol, N=2, mu = 10**U(-1, 1), y0 ~ U[-2, 2]^2,
+                 t in [0, 20], rtol 1e-6, atol 1e-9.
+* ``bruss``      1D Brusselator with n interior points (N = 2n),
+                 diffusion a = 10**U(log10 .01, log10 .05),
+                 u = 1 + sin(2 pi x_k) + U(-.1, .1), v = 3 + U(-.1, .1),
+                 t in [0, 10], rtol 1e-5, atol 1e-8.
+* ``massaction`` one network shared by the batch: 13 species, 27 reactions,
+                 1-2 reactants and 1-2 products each (species drawn uniformly
+                 with replacement), log10 A ~ U[6, 14], b ~ U[-1, 1],
+                 Ea ~ U[0, 20000] K; per system T ~ U[1000, 2000] K and
+                 concentrations U(0, 1] normalised to sum 1;
+                 t in [0, 1e-4], rtol 1e-6, atol 1e-12.
+* ``mixed``      ragged batch: half Brusselator grids with n ~ U{1..128},
+                 half coupled van der Pol chains with n ~ U{1..64}
+                 oscillators, shuffled.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Registered right-hand-side kinds (mirrors the C-ABI enumeration).
+RHS_VDP = 1
+RHS_VDP_CHAIN = 2
+RHS_BRUSS1D = 3
+RHS_MASSACTION = 4
+
+METHOD_RKCK = 0
+METHOD_RKC = 1
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@dataclass
+class Network:
+    """A mass-action reaction network: reactant/product species per reaction
+    (-1 marks an unused slot) and Arrhenius parameters."""
+
+    n_species: int
+    n_reac: np.ndarray      # int32 [R]   1 or 2
+    reac: np.ndarray        # int32 [R,2] species index or -1
+    n_prod: np.ndarray      # int32 [R]
+    prod: np.ndarray        # int32 [R,2]
+    log10A: np.ndarray      # f64 [R]
+    beta: np.ndarray        # f64 [R]
+    Ea: np.ndarray          # f64 [R]  (Kelvin; k = A T^b exp(-Ea/T))
+    kmin: float = 1e-2
+    kmax: float = 1e6
+
+    @property
+    def n_reactions(self) -> int:
+        return int(self.n_reac.shape[0])
+
+
+@dataclass
+class Workload:
+    name: str
+    kind: int
+    method: int
+    nsys: int
+    neq: int
+    y0: np.ndarray          # f64 [neq, nsys]
+    params: np.ndarray      # f64 [n_params, nsys]
+    t0: float
+    tend: float
+    rtol: float
+    atol: float
+    network: Network | None = None
+    bruss_n: int = 0
+    aux: dict = field(default_factory=dict)
+
+
+def make_network(seed: int = 0, n_species: int = 13, n_reactions: int = 27) -> Network:
+    """Draw the shared mass-action network from ``seed``."""
+    rng = _rng(seed)
+    n_reac = rng.integers(1, 3, size=n_reactions).astype(np.int32)
+    n_prod = rng.integers(1, 3, size=n_reactions).astype(np.int32)
+    reac = rng.integers(0, n_species, size=(n_reactions, 2)).astype(np.int32)
+    prod = rng.integers(0, n_species, size=(n_reactions, 2)).astype(np.int32)
+    reac[n_reac == 1, 1] = -1
+    prod[n_prod == 1, 1] = -1
+    log10A = rng.uniform(6.0, 14.0, size=n_reactions)
+    beta = rng.uniform(-1.0, 1.0, size=n_reactions)
+    Ea = rng.uniform(0.0, 20000.0, size=n_reactions)
+    return Network(n_species, n_reac, reac, n_prod, prod, log10A, beta, Ea)
+
+
+def vdp(nsys: int = 4096, seed: int = 0) -> Workload:
+    rng = _rng(seed)
+    mu = 10.0 ** rng.uniform(-1.0, 1.0, size=nsys)
+    y0 = rng.uniform(-2.0, 2.0, size=(2, nsys))
+    return Workload("vdp", RHS_VDP, METHOD_RKCK, nsys, 2, np.ascontiguousarray(y0),
+                    mu[None, :].copy(), 0.0, 20.0, 1e-6, 1e-9)
+
+
+def bruss(nsys: int = 65536, n: int = 32, seed: int = 0) -> Workload:
+    rng = _rng(seed)
+    a = 10.0 ** rng.uniform(np.log10(0.01), np.log10(0.05), size=nsys)
+    x = np.arange(1, n + 1, dtype=np.float64) / (n + 1)
+    u = 1.0 + np.sin(2.0 * np.pi * x)[:, None] + rng.uniform(-0.1, 0.1, size=(n, nsys))
+    v = 3.0 + rng.uniform(-0.1, 0.1, size=(n, nsys))
+    y0 = np.ascontiguousarray(np.concatenate([u, v], axis=0))
+    return Workload("bruss", RHS_BRUSS1D, METHOD_RKC, nsys, 2 * n, y0,
+                    a[None, :].copy(), 0.0, 10.0, 1e-5, 1e-8, bruss_n=n)
+
+
+def massaction(nsys: int = 1 << 20, seed: int = 0, network_seed: int = 0,
+               tend: float = 1e-4) -> Workload:
+    net = make_network(network_seed)
+    rng = _rng(seed)
+    T = rng.uniform(1000.0, 2000.0, size=nsys)
+    c = 1.0 - rng.uniform(0.0, 1.0, size=(net.n_species, nsys))   # U(0, 1]
+    c = c / c.sum(axis=0, keepdims=True)
+    return Workload("massaction", RHS_MASSACTION, METHOD_RKC, nsys, net.n_species,
+                    np.ascontiguousarray(c), T[None, :].copy(), 0.0, tend, 1e-6, 1e-12,
+                    network=net)
+
+
+@dataclass
+class MixedBatch:
+    """Ragged batch.  System i has kind[i] (RHS_BRUSS1D or RHS_VDP_CHAIN),
+    n[i] grid points / oscillators, neq[i] = 2 n[i] unknowns stored
+    contiguously at y0[offset[i] : offset[i] + neq[i]] (unknown-major within
+    a system), one scalar parameter param[i] (a or mu), and method[i]
+    (RKC for Brusselator grids, RKCK for chains)."""
+
+    nsys: int
+    kind: np.ndarray
+    n: np.ndarray
+    neq: np.ndarray
+    offset: np.ndarray      # int64 [nsys + 1]
+    y0: np.ndarray          # f64 [total]
+    param: np.ndarray       # f64 [nsys]
+    method: np.ndarray
+    t0: np.ndarray
+    tend: np.ndarray
+    rtol: np.ndarray
+    atol: np.ndarray
+    coupling: float = 0.1
+
+
+def mixed(nsys: int = 262144, seed: int = 0, max_bruss_n: int = 128,
+          max_chain_n: int = 64) -> MixedBatch:
+    rng = _rng(seed)
+    half = nsys // 2
+    kind = np.concatenate([np.full(half, RHS_BRUSS1D), np.full(nsys - half, RHS_VDP_CHAIN)])
+    rng.shuffle(kind)
+    kind = kind.astype(np.int32)
+    is_b = kind == RHS_BRUSS1D
+    n = np.where(is_b, rng.integers(1, max_bruss_n + 1, size=nsys),
+                 rng.integers(1, max_chain_n + 1, size=nsys)).astype(np.int32)
+    neq = (2 * n).astype(np.int32)
+    offset = np.zeros(nsys + 1, dtype=np.int64)
+    np.cumsum(neq, out=offset[1:])
+    a = 10.0 ** rng.uniform(np.log10(0.01), np.log10(0.05), size=nsys)
+    mu = 10.0 ** rng.uniform(-1.0, 1.0, size=nsys)
+    param = np.where(is_b, a, mu)
+    y0 = np.empty(int(offset[-1]), dtype=np.float64)
+    noise = rng.uniform(-0.1, 0.1, size=int(offset[-1]))
+    chain_ic = rng.uniform(-2.0, 2.0, size=int(offset[-1]))
+    for i in range(nsys):
+        o, k = int(offset[i]), int(n[i])
+        if is_b[i]:
+            x = np.arange(1, k + 1, dtype=np.float64) / (k + 1)
+            y0[o:o + k] = 1.0 + np.sin(2.0 * np.pi * x) + noise[o:o + k]
+            y0[o + k:o + 2 * k] = 3.0 + noise[o + k:o + 2 * k]
+        else:
+            y0[o:o + 2 * k] = chain_ic[o:o + 2 * k]
+    method = np.where(is_b, METHOD_RKC, METHOD_RKCK).astype(np.int32)
+    t0 = np.zeros(nsys)
+    tend = np.where(is_b, 10.0, 20.0)
+    rtol = np.where(is_b, 1e-5, 1e-6)
+    atol = np.where(is_b, 1e-8, 1e-9)
+    return MixedBatch(nsys, kind, n, neq, offset, y0, param, method, t0, tend, rtol, atol)
+
+
+def subset(w: Workload, idx: np.ndarray) -> Workload:
+    """The same workload restricted to systems ``idx`` (SoA columns)."""
+    idx = np.asarray(idx)
+    return Workload(w.name, w.kind, w.method, int(idx.size), w.neq,
+                    np.ascontiguousarray(w.y0[:, idx]), np.ascontiguousarray(w.params[:, idx]),
+                    w.t0, w.tend, w.rtol, w.atol, w.network, w.bruss_n, dict(w.aux))
