@@ -1,0 +1,351 @@
+"""Benchmark: batched RKC integration of the synthetic mass-action workload.
+
+Workload (one step = one pass of the whole hot path over one batch): the
+seeded 13-species / 27-reaction mass-action network, 1,048,576 systems per
+GPU, T ~ U[1000, 2000] K, t in [0, 1e-4], rtol 1e-6, atol 1e-12, integrated
+by RKC through the C ABI.  The metric is ODE systems integrated per second
+by the chosen form (FP32 stages with Kahan-compensated state, FP64
+bookkeeping, persistent work-queue kernel); the plain FP64 form is timed
+beside it on the same inputs, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 run under torch.distributed.run: every rank integrates its own
+batch (seed = rank), no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1611_02274_gb300 import workloads as W  # noqa: E402
+
+NSYS = 1 << 20
+METRIC = "ODE systems integrated/s at rtol 1e-6, chosen vs plain FP64 form; % of FP peak"
+UNIT = "systems/s"
+# nominal ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
+# FP32 128 lanes x 2 flops per SM per clock; FP64 the part's rated 1.25 TFLOP/s
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------ flop accounting
+
+def rhs_flops(w: W.Workload) -> int:
+    """Algorithmic flops of one mass-action RHS: per reaction |R| products
+    (rate constant times concentrations) and |R| + |P| accumulations."""
+    n = w.network
+    return int(np.sum(2 * n.n_reac + n.n_prod))
+
+
+def rkc_flops(w: W.Workload, n_acc, n_rej, n_rhs, n_sr) -> float:
+    """Algorithmic flops of RKC runs from the per-system counters: every RHS
+    evaluation, plus per attempt N (2 + 9 (m - 1) + 11) vector flops, per
+    power iteration 6 N and 8 N for the initial step (FMA = 2 flops)."""
+    N = w.neq
+    A = n_acc.astype(np.float64) + n_rej
+    sum_m = n_rhs.astype(np.float64) - n_sr - 2.0      # minus F(t0) and the initial trial step
+    vec = N * (13.0 * A + 9.0 * (sum_m - A)) + 6.0 * N * n_sr + 8.0 * N
+    return float(np.sum(n_rhs.astype(np.float64) * rhs_flops(w) + vec))
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_02274_gb300 import binding as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = W.massaction(nsys=args.nsys, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    yout = torch.empty_like(y0)
+    cnt = B.counters_like(w.nsys, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec, counters=None):
+        B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
+                    precision=prec, mapping=B.ODE_MAP_QUEUE, stream=stream.cuda_stream)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        evs = []
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()                       # L2 flush between timed iterations
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        total = sum(ms)
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total / steps, ms
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+
+    # chosen form: timed with the clock sampler running
+    with ClockSampler(gpu_id) as clk:
+        ms_chosen, per_step = timed(B.ODE_PREC_MIXED, args.steps, args.warmup)
+    clocks = clk.summary()
+    # counters of one chosen-form pass (for the flop count) and its output
+    step(B.ODE_PREC_MIXED, cnt)
+    torch.cuda.synchronize()
+    c_mixed = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+    y_mixed = yout.cpu().numpy()
+    flops_mixed = rkc_flops(w, c_mixed["n_accept"], c_mixed["n_reject"], c_mixed["n_rhs"], c_mixed["n_specrad_iter"])
+
+    # plain FP64 form on the same inputs
+    ms_plain, _ = timed(B.ODE_PREC_FP64, args.plain_steps, 1)
+    step(B.ODE_PREC_FP64, cnt)
+    torch.cuda.synchronize()
+    c_plain = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+    y_plain = yout.cpu().numpy()
+    flops_plain = rkc_flops(w, c_plain["n_accept"], c_plain["n_reject"], c_plain["n_rhs"], c_plain["n_specrad_iter"])
+
+    # end to end through the C ABI with pinned host buffers
+    hy0 = torch.from_numpy(w.y0).pin_memory()
+    hp = torch.from_numpy(w.params).pin_memory()
+    hy = torch.empty_like(hy0).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
+                    precision=B.ODE_PREC_MIXED, mapping=B.ODE_MAP_QUEUE)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+
+    total_sys = w.nsys * world
+    value = total_sys / (ms_chosen * 1e-3)
+    achieved = flops_mixed / (ms_chosen * 1e-3) / 1e12
+    achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12
+
+    if rank == 0:
+        peak32, _ = B.fma_peak(False, 1 << 20)
+        peak64, _ = B.fma_peak(True, 1 << 14)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_chosen, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded mass-action network and states; no dataset)",
+            "config": {"workload": "massaction-13sp-27rx RKC, 1,048,576 systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
+                       "nsys_per_gpu": w.nsys, "method": "rkc", "form": "chosen: FP32 stages + Kahan state, FP64 bookkeeping, persistent queue",
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
+            "rhs_evals_per_s": float(np.sum(c_mixed["n_rhs"])) * world / (ms_chosen * 1e-3),
+            "plain_fp64": {"value": total_sys / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                           "rhs_evals_per_s": float(np.sum(c_plain["n_rhs"])) * world / (ms_plain * 1e-3),
+                           "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
+                           "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
+            "speedup_chosen_vs_plain": ms_plain / ms_chosen,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_queue<RkcMixed<MassActionModel<16,32>>>",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                         "peak_measured_fma": peak32 / 1e3, "frac_of_measured": achieved / (peak32 / 1e3),
+                         "flops_per_launch": flops_mixed},
+            "fp64_fma_measured_tflops": peak64 / 1e3,
+            "e2e": {"value": total_sys / (e2e_step * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(w.y0.nbytes + w.params.nbytes), "d2h_bytes_per_step": int(w.y0.nbytes)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "status_ok_frac": float(np.mean((c_mixed["status"] & 0xFF) == 0)),
+        }
+        if not args.no_cpu:
+            out["cpu_baseline"], acc = cpu_baseline(w, args, y_mixed, y_plain, c_plain)
+            out["accuracy_vs_oracle"] = acc
+        print(json.dumps(out), flush=True)
+    B.release(h)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, args, y_mixed, y_plain, c_plain):
+    """Time the oracle (as it stands) on a bounded sample of the same batch,
+    and compare both GPU forms with it on that sample."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(123)
+    probe = np.sort(rng.choice(w.nsys, 2048, replace=False))
+    t0 = time.perf_counter()
+    O.integrate_workload(W.subset(w, probe))
+    rate = 2048 / (time.perf_counter() - t0)
+    n = int(min(w.nsys, max(4096, rate * args.cpu_seconds)))
+    idx = np.sort(rng.choice(w.nsys, n, replace=False))
+    sub = W.subset(w, idx)
+    t0 = time.perf_counter()
+    ref = O.integrate_workload(sub)
+    dt = time.perf_counter() - t0
+    e_m = (np.abs(y_mixed[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+    e_p = (np.abs(y_plain[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+    same = (c_plain["n_accept"][idx] == ref.n_accept) & (c_plain["n_reject"][idx] == ref.n_reject)
+    base = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {w.nsys} systems drawn uniformly (seed 123), full interval, all host cores"}
+    acc = {"sample": n, "chosen_max_rel_err": float(e_m.max()), "chosen_p999_rel_err": float(np.quantile(e_m, 0.999)),
+           "chosen_median_rel_err": float(np.median(e_m)),
+           "plain_max_rel_err_same_counts": float(e_p[same].max()) if same.any() else None,
+           "plain_same_counts_frac": float(same.mean())}
+    return base, acc
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The oracle (the paper's algorithm restated in plain C, FP64) timed on
+    the host cores, each step a bounded slice of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    w = W.massaction(nsys=args.nsys, seed=0)
+    cores = os.cpu_count() or 1
+    per = args.ref_sample
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = np.arange(k * per, (k + 1) * per) % w.nsys
+        sub = W.subset(w, idx)
+        t0 = time.perf_counter()
+        O.integrate_workload(sub)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    value = per / (ms * 1e-3)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "massaction-13sp-27rx RKC, t in [0,1e-4], rtol 1e-6, atol 1e-12",
+                      "sample_per_step": per},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{per} consecutive systems per step of the {w.nsys}-system batch"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nsys", type=int, default=NSYS)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * batchode.h -- C ABI of the GB300 batched ODE integration library
+ * (libbatchode.so).
+ *
+ * Integrates very large batches of independent small ODE systems
+ * dy/dt = f(t, y, g) (the paper's Eq. ode, Section 2), each with its own
+ * initial state y(t0) and constant parameters g, by
+ *   - rkck_integrate: adaptive fifth-order Runge-Kutta-Cash-Karp
+ *     (Section 2.1: Table 1, the k1..k6 equations, the error scale and the
+ *     step-size rule Eq. E:hnew; control flow of the rkckDriver listing,
+ *     Section 3.1), and
+ *   - rkc_integrate: stabilised second-order Runge-Kutta-Chebyshev
+ *     (Section 2.2: Eqs. E:rkc0-E:rkcs, Eq. E:rmsE, Eqs. dtnp1 / rkc-f, the
+ *     initial-step and stage-count rules; control flow of the rkcDriver
+ *     listing, Section 3.2, and the Appendix power method).
+ * The right-hand side is one of a small registry of built-in families
+ * (ode_rhs_register).  No PyTorch or CUDA type appears in these signatures;
+ * a stream is passed as an opaque pointer (a cudaStream_t, NULL = the legacy
+ * default stream).
+ *
+ * Memory layout (Section 3, "structure of arrays"): unknown j of system i is
+ * at y[i + nsys * j]; parameter p of system i at params[i + nsys * p].  All
+ * arrays are caller-owned.  By default every array pointer is a DEVICE
+ * pointer on the current device; with opts->io == ODE_IO_HOST they are host
+ * pointers (pinned memory gives asynchronous copies) and the call copies
+ * them in and out through a library-owned device workspace, then
+ * synchronises the stream before returning.  y_out may alias y0.
+ *
+ * Errors: every entry point returns ODE_OK (0) on success or a negative
+ * ODE_ERR_* code; ode_last_error() then describes the failure (thread-local
+ * string, valid until the next call on the same thread).  Argument errors
+ * are detected on the host before any launch.  Per-system outcomes are
+ * written to stats->status: ODE_ST_OK, ODE_ST_H_UNDERFLOW,
+ * ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE, optionally OR-ed with the warning
+ * bit ODE_ST_SPECRAD_NOCONV (RKC power method stopped at 50 iterations).
+ * Launches are asynchronous on the stream unless io == ODE_IO_HOST or
+ * opts->sync != 0.
+ */
+#ifndef BATCHODE_H
+#define BATCHODE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define ODE_OK 0
+#define ODE_ERR_ARG (-1)          /* invalid argument (null, size, tolerance, interval) */
+#define ODE_ERR_HANDLE (-2)       /* unknown or released rhs handle */
+#define ODE_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define ODE_ERR_UNSUPPORTED (-4)  /* combination not built (e.g. dimension too large) */
+#define ODE_ERR_NOMEM (-5)        /* workspace allocation failed */
+
+/* per-system status codes */
+#define ODE_ST_OK 0
+#define ODE_ST_H_UNDERFLOW 1      /* step size fell below the minimum */
+#define ODE_ST_MAX_ATTEMPTS 2     /* attempt cap reached before tend */
+#define ODE_ST_NONFINITE 3        /* NaN error estimate or non-finite state */
+#define ODE_ST_SPECRAD_NOCONV 256 /* warning bit: power method did not converge */
+
+/* right-hand-side families */
+#define ODE_RHS_VDP 1        /* van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1; params [mu]; neq 2 */
+#define ODE_RHS_VDP_CHAIN 2  /* n van der Pol oscillators [x_1..x_n, v_1..v_n], diffusive position
+                                coupling with free ends; params [mu]; neq 2n */
+#define ODE_RHS_BRUSS1D 3    /* 1D Brusselator on n interior points [u_1..u_n, v_1..v_n], Dirichlet
+                                ghosts u = ubc, v = vbc; params [a] (diffusion); neq 2n */
+#define ODE_RHS_MASSACTION 4 /* mass-action kinetics (Section 4.2 omega_i with constant T), Arrhenius
+                                k_j = clip(10^log10A_j T^beta_j exp(-Ea_j / T), kmin, kmax);
+                                params [T]; neq = n_species */
+
+/* precision of the integrator */
+#define ODE_PREC_FP64 0      /* plain form: every operation in FP64, as the paper's listings */
+#define ODE_PREC_MIXED 1     /* FP32 RHS and stage arithmetic with Kahan-compensated FP32 state;
+                                FP64 time, step size, error-norm accumulation and Chebyshev
+                                coefficients */
+
+/* how systems map onto the GPU */
+#define ODE_MAP_AUTO 0       /* autotuned choice (cached per rhs / method / precision) */
+#define ODE_MAP_THREAD 1     /* one thread per system, one launch over the batch (the paper's) */
+#define ODE_MAP_QUEUE 2      /* persistent kernel, one thread per system, systems pulled from a
+                                device work queue one at a time as lanes finish */
+
+#define ODE_IO_DEVICE 0
+#define ODE_IO_HOST 1
+
+typedef struct {
+    int32_t kind;         /* ODE_RHS_* */
+    int32_t neq;          /* unknowns per system */
+    int32_t n_params;     /* per-system parameters (1 for every built-in family) */
+    /* ODE_RHS_MASSACTION only: R reactions, each with n_reac[j] (1 or 2)
+     * reactant and n_prod[j] (1 or 2) product species (indices in
+     * [0, neq), a repeated species counts twice), stored in reac[2 j + q]
+     * and prod[2 j + q]; Arrhenius log10A, beta, Ea (Kelvin) per reaction
+     * and the clip band [kmin, kmax].  Host pointers, copied. */
+    int32_t n_reactions;
+    const int32_t* n_reac;
+    const int32_t* reac;
+    const int32_t* n_prod;
+    const int32_t* prod;
+    const double* log10A;
+    const double* beta;
+    const double* Ea;
+    double kmin, kmax;
+    /* ODE_RHS_BRUSS1D only */
+    double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
+    /* ODE_RHS_VDP_CHAIN only */
+    double coupling;
+} ode_rhs_desc;
+
+typedef struct {
+    int32_t precision;     /* ODE_PREC_* (default FP64) */
+    int32_t mapping;       /* ODE_MAP_* (default AUTO) */
+    int32_t max_attempts;  /* per-system attempt cap; <= 0 means 1,000,000 */
+    int32_t block_size;    /* threads per block; 0 = tuned/default */
+    int32_t io;            /* ODE_IO_DEVICE or ODE_IO_HOST */
+    int32_t sync;          /* nonzero: synchronise the stream before returning */
+    int32_t reserved[10];  /* must be zero */
+} ode_opts;
+
+/* Per-system outputs, each an array of nsys int32 (device pointers unless
+ * io == ODE_IO_HOST) or NULL when not wanted.  n_rhs counts RHS evaluations
+ * as the algorithm defines them: 6 per RKCK attempt; for RKC one initial
+ * F(t0), one per initial-step trial, m per m-stage attempt and one per
+ * power-method iteration. */
+typedef struct {
+    int32_t* n_accept;
+    int32_t* n_reject;
+    int32_t* n_rhs;
+    int32_t* n_specrad_iter;
+    int32_t* status;
+} ode_stats;
+
+/* Register a right-hand side.  The descriptor (and for mass-action the
+ * network arrays) is validated and copied; *rhs_handle receives a positive
+ * handle.  Errors: ODE_ERR_ARG for an unknown kind, neq out of range
+ * (VDP: 2; chain: even, 2..128; Brusselator: even, 2..256; mass-action: 1..32 species,
+ * 1..64 reactions) or bad indices. */
+int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle);
+
+/* Release a handle.  ODE_ERR_HANDLE if it is not registered. */
+int ode_rhs_release(int32_t rhs_handle);
+
+/* Integrate nsys systems from t0 to tend with the adaptive RKCK method.
+ * y0, params: [neq][nsys] and [n_params][nsys] FP64; y_out: [neq][nsys].
+ * rtol > 0, atol >= 0, tend > t0 (tend == t0 copies y0).  opts may be NULL
+ * (defaults).  Errors: ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA,
+ * ODE_ERR_NOMEM, ODE_ERR_UNSUPPORTED. */
+int rkck_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
+                   double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
+                   const ode_stats* stats, void* stream);
+
+/* Same contract with the adaptive RKC method (spectral radius by the
+ * nonlinear power method, re-estimated every 25 accepted steps and after a
+ * rejection). */
+int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
+                  double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
+                  const ode_stats* stats, void* stream);
+
+/* Description of the last error on this thread ("" if none). */
+const char* ode_last_error(void);
+
+/* Library version string. */
+const char* ode_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BATCHODE_H */

@@ -42,6 +42,9 @@
  *       RKCK h < 1e-20 or t + h == t (H_UNDERFLOW), a NaN RKC error or a
  *       non-finite accepted state (NONFINITE).
  *   R9  UROUND is the literal 2.22e-16 of the listings.
+ *   R10 Powers in the step-size rules and the Arrhenius rate use the series
+ *       logarithm / exponential below, a fixed sequence of correctly
+ *       rounded operations, so their values are reproducible bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -187,11 +190,89 @@ static void dydt(const or_sys* s, double t, const double* y, double* f) {
     }
 }
 
+/* ------------------------------------------------ logarithm / exponential
+ *
+ * The step-size rules (err^(-1/4), err^(-1/5), err^(1/3), err^(2/3)) and
+ * the Arrhenius rate need powers.  They are computed here from the textbook
+ * series with only correctly rounded operations (+, -, *, /, frexp, ldexp,
+ * rint), so any implementation that performs the same operations gets the
+ * same bits (R10):
+ *   ln x  : x = 2^k m with m in [sqrt(1/2), sqrt(2)), s = (m - 1)/(m + 1),
+ *           ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ... + s^22/23),
+ *           ln x = k ln2_hi + (k ln2_lo + ln m);
+ *   exp x : k = rint(x log2 e), r = (x - k ln2_hi) - k ln2_lo (Cody & Waite
+ *           reduction, ln2_hi holding 32 significant bits), e^r by its Taylor
+ *           series to r^14/14!, then scaled by 2^k;
+ *   x^y   : exp(y ln x) for x > 0.
+ * Accuracy is a few units in the last place (checked against libm). */
+#define LN2_HI 0.6931471806019545
+#define LN2_LO (-4.2009150726810846e-11)
+#define LOG2E 1.4426950408889634
+#define LN10 2.302585092994046
+#define SQRT_HALF 0.7071067811865476
+
+static double or_log(double x) {
+    if (!(x > 0.0)) return (x == 0.0) ? -INFINITY : NAN;
+    if (isinf(x)) return x;
+    int k;
+    double m = frexp(x, &k);
+    if (m < SQRT_HALF) {
+        m = m * 2.0;
+        k = k - 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double p = 0.043478260869565216;     /* 1/23 */
+    p = p * z + 0.047619047619047616;    /* 1/21 */
+    p = p * z + 0.05263157894736842;     /* 1/19 */
+    p = p * z + 0.058823529411764705;    /* 1/17 */
+    p = p * z + 0.06666666666666667;     /* 1/15 */
+    p = p * z + 0.07692307692307693;     /* 1/13 */
+    p = p * z + 0.09090909090909091;     /* 1/11 */
+    p = p * z + 0.1111111111111111;      /* 1/9 */
+    p = p * z + 0.14285714285714285;     /* 1/7 */
+    p = p * z + 0.2;                     /* 1/5 */
+    p = p * z + 0.3333333333333333;      /* 1/3 */
+    p = p * z + 1.0;
+    double lnm = 2.0 * s * p;
+    double kd = (double)k;
+    return kd * LN2_HI + (kd * LN2_LO + lnm);
+}
+
+static double or_exp(double x) {
+    if (isnan(x)) return x;
+    if (x > 709.0) return INFINITY;
+    if (x < -745.0) return 0.0;
+    double kf = rint(x * LOG2E);
+    double r = (x - kf * LN2_HI) - kf * LN2_LO;
+    double p = 1.1470745597729725e-11;   /* 1/14! */
+    p = p * r + 1.6059043836821613e-10;  /* 1/13! */
+    p = p * r + 2.08767569878681e-09;    /* 1/12! */
+    p = p * r + 2.505210838544172e-08;   /* 1/11! */
+    p = p * r + 2.755731922398589e-07;   /* 1/10! */
+    p = p * r + 2.7557319223985893e-06;  /* 1/9! */
+    p = p * r + 2.48015873015873e-05;    /* 1/8! */
+    p = p * r + 0.0001984126984126984;   /* 1/7! */
+    p = p * r + 0.001388888888888889;    /* 1/6! */
+    p = p * r + 0.008333333333333333;    /* 1/5! */
+    p = p * r + 0.041666666666666664;    /* 1/4! */
+    p = p * r + 0.16666666666666666;     /* 1/3! */
+    p = p * r + 0.5;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    return ldexp(p, (int)kf);
+}
+
+static double or_pow(double x, double y) {
+    if (x == 0.0) return (y > 0.0) ? 0.0 : INFINITY;
+    return or_exp(y * or_log(x));
+}
+
 /* Arrhenius rate constant k = A T^b exp(-Ea / T) of Section 4.2 (Ea in
- * Kelvin, i.e. E/R), clipped to [kmin, kmax]. */
+ * Kelvin, i.e. E/R) with A = 10^log10A, evaluated as one exponential
+ * exp(ln(10) log10A + b ln T - Ea / T), then clipped to [kmin, kmax]. */
 static double arrhenius(double log10A, double b, double Ea, double T, double kmin, double kmax) {
-    double A = pow(10.0, log10A);
-    double k = A * pow(T, b) * exp(-Ea / T);
+    double k = or_exp(LN10 * log10A + b * or_log(T) - Ea / T);
     if (k < kmin) k = kmin;
     if (k > kmax) k = kmax;
     return k;
@@ -305,7 +386,7 @@ static void rkck_system(const or_sys* s, double t, double tend, double rtol, dou
             if (isnan(err) || nan_flag)
                 h = h * P1;
             else
-                h = fmax(SAFETY * h * pow(err, PSHRNK), P1 * h);
+                h = fmax(SAFETY * h * or_pow(err, PSHRNK), P1 * h);
             if (h < hmin || t + h == t) {
                 cnt->status = ST_H_UNDERFLOW;
                 break;
@@ -314,7 +395,7 @@ static void rkck_system(const or_sys* s, double t, double tend, double rtol, dou
             cnt->n_accept += 1;
             t = t + h;
             if (err > ERRCON)
-                h = SAFETY * h * pow(err, PGROW);
+                h = SAFETY * h * or_pow(err, PGROW);
             else
                 h = h * 5.0;
             h = fmax(hmin, fmin(hmax, h));
@@ -552,7 +633,7 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
         }
         if (err > 1.0) {
             cnt->n_reject += 1;
-            h = 0.8 * h / pow(err, 1.0 / 3.0);
+            h = 0.8 * h / or_pow(err, 1.0 / 3.0);
             rejected = 1;
             if (h < hmin) {
                 cnt->status |= ST_H_UNDERFLOW;
@@ -565,11 +646,11 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
             num_step += 1;
             double fac = 10.0;
             if (h_old < UROUND) {
-                double temp2 = pow(err, 1.0 / 3.0);
+                double temp2 = or_pow(err, 1.0 / 3.0);
                 if (0.8 < fac * temp2) fac = 0.8 / temp2;
             } else {
-                double temp1 = 0.8 * h * pow(err_old, 1.0 / 3.0);
-                double temp2 = h_old * pow(err, 2.0 / 3.0);
+                double temp1 = 0.8 * h * or_pow(err_old, 1.0 / 3.0);
+                double temp2 = h_old * or_pow(err, 2.0 / 3.0);
                 if (temp1 < fac * temp2) fac = temp1 / temp2;
             }
             err_old = err;
@@ -749,3 +830,7 @@ double oracle_specrad(const or_model* m, const double* p, double t, const double
 }
 
 int oracle_model_size(void) { return (int)sizeof(or_model); }
+
+double oracle_pow(double x, double y) { return or_pow(x, y); }
+double oracle_exp(double x) { return or_exp(x); }
+double oracle_log(double x) { return or_log(x); }

@@ -54,6 +54,11 @@ def lib():
         L.oracle_specrad.argtypes = [P, P, C.c_double, P, C.c_double, P, P, P]
         L.oracle_specrad.restype = C.c_double
         L.oracle_model_size.restype = C.c_int
+        for fn in ("oracle_pow", "oracle_exp", "oracle_log"):
+            getattr(L, fn).restype = C.c_double
+        L.oracle_pow.argtypes = [C.c_double, C.c_double]
+        L.oracle_exp.argtypes = [C.c_double]
+        L.oracle_log.argtypes = [C.c_double]
         assert L.oracle_model_size() == C.sizeof(Model)
         _lib = L
     return _lib
@@ -192,3 +197,15 @@ def specrad(m: Model, p, y, hmax: float, v, t: float = 0.0):
     st = np.zeros(1, dtype=np.int32)
     r = lib().oracle_specrad(C.byref(m), _p(p), t, _p(y), hmax, _p(v), _p(it), _p(st))
     return r, v, int(it[0]), int(st[0])
+
+
+def series_pow(x: float, y: float) -> float:
+    return lib().oracle_pow(x, y)
+
+
+def series_exp(x: float) -> float:
+    return lib().oracle_exp(x)
+
+
+def series_log(x: float) -> float:
+    return lib().oracle_log(x)

@@ -1,0 +1,198 @@
+"""Thin ctypes binding of ``libbatchode.so`` (the C ABI in include/batchode.h).
+
+Argument marshalling only: every integration step runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (their ``data_ptr``);
+host arrays (numpy, or pinned torch CPU tensors) are passed with
+``io=ODE_IO_HOST``.  There is no CPU fallback: if the library cannot be
+built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import workloads as W
+
+ODE_OK = 0
+ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM = -1, -2, -3, -4, -5
+ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 3
+ODE_ST_SPECRAD_NOCONV = 256
+ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION = 1, 2, 3, 4
+ODE_PREC_FP64, ODE_PREC_MIXED = 0, 1
+ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
+ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
+
+EXPORTED = ["ode_rhs_register", "ode_rhs_release", "rkck_integrate", "rkc_integrate",
+            "ode_last_error", "ode_version", "bode_fma_peak"]
+
+
+class RhsDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("neq", C.c_int32), ("n_params", C.c_int32), ("n_reactions", C.c_int32),
+        ("n_reac", C.POINTER(C.c_int32)), ("reac", C.POINTER(C.c_int32)),
+        ("n_prod", C.POINTER(C.c_int32)), ("prod", C.POINTER(C.c_int32)),
+        ("log10A", C.POINTER(C.c_double)), ("beta", C.POINTER(C.c_double)), ("Ea", C.POINTER(C.c_double)),
+        ("kmin", C.c_double), ("kmax", C.c_double),
+        ("bruss_A", C.c_double), ("bruss_B", C.c_double), ("bruss_ubc", C.c_double), ("bruss_vbc", C.c_double),
+        ("coupling", C.c_double),
+    ]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
+                ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
+                ("reserved", C.c_int32 * 10)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_accept", C.c_void_p), ("n_reject", C.c_void_p), ("n_rhs", C.c_void_p),
+                ("n_specrad_iter", C.c_void_p), ("status", C.c_void_p)]
+
+
+class BatchOdeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"batchode error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbatchode.so")
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbatchode.so is missing at {path}; the CUDA path cannot run")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    L.ode_rhs_register.argtypes = [C.POINTER(RhsDesc), C.POINTER(C.c_int32)]
+    L.ode_rhs_release.argtypes = [C.c_int32]
+    for name in ("rkck_integrate", "rkc_integrate"):
+        fn = getattr(L, name)
+        fn.argtypes = [C.c_int32, C.c_int64, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                       C.POINTER(Opts), P, C.POINTER(Stats), P]
+    L.ode_last_error.restype = C.c_char_p
+    L.ode_version.restype = C.c_char_p
+    L.bode_fma_peak.argtypes = [C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != ODE_OK:
+        raise BatchOdeError(rc, load().ode_last_error().decode())
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def register(kind: int, neq: int, network: W.Network | None = None, bruss=(1.0, 3.0, 1.0, 3.0),
+             coupling: float = 0.1) -> int:
+    """ode_rhs_register for one family; returns the handle."""
+    d = RhsDesc()
+    d.kind, d.neq, d.n_params = kind, neq, 1
+    d.bruss_A, d.bruss_B, d.bruss_ubc, d.bruss_vbc = bruss
+    d.coupling = coupling
+    keep = []
+    if network is not None:
+        arrs = [_i32(network.n_reac), _i32(np.where(network.reac < 0, 0, network.reac).reshape(-1)),
+                _i32(network.n_prod), _i32(np.where(network.prod < 0, 0, network.prod).reshape(-1))]
+        darrs = [_f64(network.log10A), _f64(network.beta), _f64(network.Ea)]
+        keep += arrs + darrs
+        d.n_reactions = network.n_reactions
+        d.n_reac, d.reac, d.n_prod, d.prod = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
+        d.log10A, d.beta, d.Ea = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in darrs]
+        d.kmin, d.kmax = network.kmin, network.kmax
+    h = C.c_int32(0)
+    _check(load().ode_rhs_register(C.byref(d), C.byref(h)))
+    return int(h.value)
+
+
+def register_workload(w: W.Workload) -> int:
+    return register(w.kind, w.neq, network=w.network)
+
+
+def release(handle: int):
+    _check(load().ode_rhs_release(handle))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(x.data_ptr())
+
+
+@dataclass
+class Counters:
+    n_accept: object
+    n_reject: object
+    n_rhs: object
+    n_specrad_iter: object
+    status: object
+
+
+def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
+              y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
+              mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
+              stream=None, sync: bool = False):
+    """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
+    tensor for device io, numpy array for host io); returns y_out."""
+    host = isinstance(y0, np.ndarray)
+    nsys = int(y0.shape[1])
+    if y_out is None:
+        y_out = np.empty_like(y0) if host else y0.new_empty(y0.shape)
+    o = Opts()
+    o.precision, o.mapping, o.block_size, o.max_attempts = precision, mapping, block_size, max_attempts
+    o.io = ODE_IO_HOST if host else ODE_IO_DEVICE
+    o.sync = 1 if sync else 0
+    s = Stats()
+    if counters is not None:
+        s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
+            _ptr(getattr(counters, k)) for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")]
+    if stream is None and not host:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    fn = load().rkck_integrate if method == "rkck" else load().rkc_integrate
+    rc = fn(handle, nsys, _ptr(y0), _ptr(params), float(t0), float(tend), float(rtol), float(atol),
+            C.byref(o), _ptr(y_out), C.byref(s), C.c_void_p(stream) if stream else None)
+    _check(rc)
+    return y_out
+
+
+def counters_like(nsys: int, device=None) -> Counters:
+    """Per-system counter arrays: torch int32 on ``device`` or numpy on host."""
+    if device is None:
+        return Counters(*[np.zeros(nsys, dtype=np.int32) for _ in range(5)])
+    import torch
+    return Counters(*[torch.zeros(nsys, dtype=torch.int32, device=device) for _ in range(5)])
+
+
+def fma_peak(fp64: bool, iters: int = 1 << 16):
+    """Measured FMA-chain throughput of the current device: (GFLOP/s, ms)."""
+    g, ms = C.c_double(0), C.c_double(0)
+    _check(load().bode_fma_peak(1 if fp64 else 0, iters, C.byref(g), C.byref(ms)))
+    return g.value, ms.value
+
+
+def version() -> str:
+    return load().ode_version().decode()

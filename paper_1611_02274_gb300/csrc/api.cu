@@ -1,0 +1,312 @@
+// api.cu -- the C ABI (include/batchode.h): RHS registry, argument
+// validation, workspace, host-buffer staging and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "batchode.h"
+#include "launch.cuh"
+
+using namespace bode;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+std::map<int32_t, RhsEntry> g_reg;
+int32_t g_next_handle = 1;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(ODE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Per-device workspace: a ring of queue cursors and a grow-only staging
+// buffer for host-pointer calls.
+constexpr int kCursorRing = 1024;
+constexpr int kRkcTabMax = 64;  // stage counts with tabulated coefficients
+struct Workspace {
+    unsigned long long* cursors = nullptr;
+    int next_cursor = 0;
+    double* tab64 = nullptr;
+    float4* tab32 = nullptr;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    int sm_count = 0;
+};
+std::map<int, Workspace> g_ws;
+
+int get_workspace(Workspace** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    Workspace& w = g_ws[dev];
+    if (!w.cursors) {
+        e = cudaMalloc(&w.cursors, sizeof(unsigned long long) * kCursorRing);
+        if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "workspace allocation failed: %s", cudaGetErrorString(e));
+        e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        const int entries = rkc_tab_index(kRkcTabMax + 1, 1);
+        e = cudaMalloc(&w.tab64, sizeof(double) * 8 * entries);
+        if (e == cudaSuccess) e = cudaMalloc(&w.tab32, sizeof(float4) * entries);
+        if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "coefficient table allocation failed: %s", cudaGetErrorString(e));
+        e = build_rkc_tables(w.tab64, w.tab32, kRkcTabMax, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "coefficient table build");
+    }
+    *out = &w;
+    return ODE_OK;
+}
+
+int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
+    if (!d) return fail(ODE_ERR_ARG, "desc is NULL");
+    std::memset(r, 0, sizeof(*r));
+    r->kind = d->kind;
+    r->neq = d->neq;
+    r->n_params = d->n_params;
+    if (d->n_params != 1) return fail(ODE_ERR_ARG, "n_params must be 1 for every built-in family (got %d)", d->n_params);
+    switch (d->kind) {
+    case ODE_RHS_VDP:
+        if (d->neq != 2) return fail(ODE_ERR_ARG, "van der Pol has neq 2 (got %d)", d->neq);
+        return ODE_OK;
+    case ODE_RHS_VDP_CHAIN:
+        if (d->neq < 2 || d->neq > 128 || d->neq % 2) return fail(ODE_ERR_ARG, "chain neq must be even in [2, 128]");
+        if (!std::isfinite(d->coupling)) return fail(ODE_ERR_ARG, "coupling must be finite");
+        r->coupling = d->coupling;
+        return ODE_OK;
+    case ODE_RHS_BRUSS1D:
+        if (d->neq < 2 || d->neq > 256 || d->neq % 2) return fail(ODE_ERR_ARG, "Brusselator neq must be even in [2, 256]");
+        r->bruss_A = d->bruss_A;
+        r->bruss_B = d->bruss_B;
+        r->bruss_ubc = d->bruss_ubc;
+        r->bruss_vbc = d->bruss_vbc;
+        return ODE_OK;
+    case ODE_RHS_MASSACTION: {
+        const int S = d->neq, R = d->n_reactions;
+        if (S < 1 || S > kMaxSpecies) return fail(ODE_ERR_ARG, "mass-action species count must be in [1, %d]", kMaxSpecies);
+        if (R < 1 || R > kMaxReactions) return fail(ODE_ERR_ARG, "mass-action reaction count must be in [1, %d]", kMaxReactions);
+        if (!d->n_reac || !d->reac || !d->n_prod || !d->prod || !d->log10A || !d->beta || !d->Ea)
+            return fail(ODE_ERR_ARG, "mass-action network arrays must be non-NULL");
+        if (!(d->kmin > 0.0) || !(d->kmax >= d->kmin)) return fail(ODE_ERR_ARG, "need 0 < kmin <= kmax");
+        MassActionNet& n = r->net;
+        n.n_species = S;
+        n.n_reactions = R;
+        n.kmin = d->kmin;
+        n.kmax = d->kmax;
+        for (int j = 0; j < R; ++j) {
+            const int nr = d->n_reac[j], np = d->n_prod[j];
+            if (nr < 1 || nr > 2 || np < 1 || np > 2) return fail(ODE_ERR_ARG, "reaction %d: 1-2 reactants and products", j);
+            n.n_reac[j] = (int8_t)nr;
+            n.n_prod[j] = (int8_t)np;
+            for (int q = 0; q < 2; ++q) {
+                const int rs = q < nr ? d->reac[2 * j + q] : 0;
+                const int ps = q < np ? d->prod[2 * j + q] : 0;
+                if (rs < 0 || rs >= S || ps < 0 || ps >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
+                n.reac[j][q] = (int8_t)rs;
+                n.prod[j][q] = (int8_t)ps;
+            }
+            if (!std::isfinite(d->log10A[j]) || !std::isfinite(d->beta[j]) || !std::isfinite(d->Ea[j]))
+                return fail(ODE_ERR_ARG, "reaction %d: non-finite Arrhenius parameter", j);
+            n.log10A[j] = d->log10A[j];
+            n.beta[j] = d->beta[j];
+            n.Ea[j] = d->Ea[j];
+        }
+        return ODE_OK;
+    }
+    default:
+        return fail(ODE_ERR_ARG, "unknown rhs kind %d", d->kind);
+    }
+}
+
+enum Method { kRkck = 0, kRkc = 1 };
+
+int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, const double* params, double t0,
+              double tend, double rtol, double atol, const ode_opts* opts_in, double* y_out,
+              const ode_stats* stats_in, void* stream_ptr) {
+    g_err.clear();
+    RhsEntry rhs;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_reg.find(handle);
+        if (it == g_reg.end()) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", handle);
+        rhs = it->second;
+    }
+    ode_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    for (int k = 0; k < 10; ++k)
+        if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
+    if (opts.precision != ODE_PREC_FP64 && opts.precision != ODE_PREC_MIXED)
+        return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
+    if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
+    if (opts.io != ODE_IO_DEVICE && opts.io != ODE_IO_HOST) return fail(ODE_ERR_ARG, "unknown io mode %d", opts.io);
+    if (opts.block_size != 0 && (opts.block_size < 32 || opts.block_size > 256 || opts.block_size % 32))
+        return fail(ODE_ERR_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
+    if (nsys < 0) return fail(ODE_ERR_ARG, "nsys must be >= 0");
+    if (nsys > ((int64_t)1 << 40)) return fail(ODE_ERR_ARG, "nsys too large");
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) return fail(ODE_ERR_ARG, "rtol must be finite and > 0");
+    if (!(atol >= 0.0) || !std::isfinite(atol)) return fail(ODE_ERR_ARG, "atol must be finite and >= 0");
+    if (!std::isfinite(t0) || !std::isfinite(tend) || tend < t0) return fail(ODE_ERR_ARG, "need finite t0 <= tend");
+    if (nsys == 0) return ODE_OK;
+    if (!y0 || !params || !y_out) return fail(ODE_ERR_ARG, "y0, params and y_out must be non-NULL");
+
+    ode_stats stats;
+    std::memset(&stats, 0, sizeof(stats));
+    if (stats_in) stats = *stats_in;
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace* ws = nullptr;
+    int rc = get_workspace(&ws);
+    if (rc) return rc;
+
+    const size_t ny = (size_t)nsys * rhs.neq, np = (size_t)nsys * rhs.n_params;
+    const double* d_y0 = y0;
+    const double* d_p = params;
+    double* d_yout = y_out;
+    ode_stats d_stats = stats;
+    cudaError_t e;
+    int32_t* const* host_cnt[5] = {&stats.n_accept, &stats.n_reject, &stats.n_rhs, &stats.n_specrad_iter, &stats.status};
+    int32_t** dev_cnt[5] = {&d_stats.n_accept, &d_stats.n_reject, &d_stats.n_rhs, &d_stats.n_specrad_iter, &d_stats.status};
+    if (opts.io == ODE_IO_HOST) {
+        const size_t need = sizeof(double) * (2 * ny + np) + sizeof(int32_t) * 5 * (size_t)nsys + 256 * 4;
+        if (ws->stage_bytes < need) {
+            if (ws->stage) cudaFree(ws->stage);
+            ws->stage = nullptr;
+            ws->stage_bytes = 0;
+            e = cudaMalloc(&ws->stage, need);
+            if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "staging allocation of %zu bytes failed", need);
+            ws->stage_bytes = need;
+        }
+        char* p = (char*)ws->stage;
+        auto carve = [&](size_t bytes) {
+            char* q = p;
+            p += (bytes + 255) / 256 * 256;
+            return q;
+        };
+        double* sy0 = (double*)carve(sizeof(double) * ny);
+        double* sp = (double*)carve(sizeof(double) * np);
+        d_yout = (double*)carve(sizeof(double) * ny);
+        for (int k = 0; k < 5; ++k) *dev_cnt[k] = *host_cnt[k] ? (int32_t*)carve(sizeof(int32_t) * nsys) : nullptr;
+        e = cudaMemcpyAsync(sy0, y0, sizeof(double) * ny, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sp, params, sizeof(double) * np, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        d_y0 = sy0;
+        d_p = sp;
+    }
+
+    BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nsys = nsys;
+    a.neq = rhs.neq;
+    a.max_attempts = opts.max_attempts > 0 ? opts.max_attempts : 1000000;
+    a.y0 = d_y0;
+    a.params = d_p;
+    a.y_out = d_yout;
+    a.t0 = t0;
+    a.tend = tend;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.n_accept = d_stats.n_accept;
+    a.n_reject = d_stats.n_reject;
+    a.n_rhs = d_stats.n_rhs;
+    a.n_specrad = d_stats.n_specrad_iter;
+    a.status = d_stats.status;
+    a.cursor = ws->cursors + ws->next_cursor;
+    a.rkc_tab64 = ws->tab64;
+    a.rkc_tab32 = ws->tab32;
+    a.rkc_tab_max = kRkcTabMax;
+    ws->next_cursor = (ws->next_cursor + 1) % kCursorRing;
+
+    LaunchCfg cfg;
+    cfg.mapping = opts.mapping == ODE_MAP_THREAD ? ODE_MAP_THREAD : ODE_MAP_QUEUE;
+    cfg.block = opts.block_size ? opts.block_size : 128;
+    cfg.team = 0;
+    cfg.sm_count = ws->sm_count;
+    cfg.stream = stream;
+    if (cfg.mapping == ODE_MAP_QUEUE) {
+        e = cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cursor reset");
+    }
+    bool supported = true;
+    const int meth = method == kRkck ? kMethodRkck : kMethodRkc;
+    switch (rhs.kind) {
+    case ODE_RHS_VDP: e = launch_vdp(meth, opts.precision, rhs, a, cfg, &supported); break;
+    case ODE_RHS_MASSACTION: e = launch_mass(meth, opts.precision, rhs, a, cfg, &supported); break;
+    case ODE_RHS_BRUSS1D: e = launch_bruss(meth, opts.precision, rhs, a, cfg, &supported); break;
+    case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, opts.precision, rhs, a, cfg, &supported); break;
+    default: supported = false; e = cudaSuccess;
+    }
+    if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built for this method", rhs.kind, rhs.neq);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+
+    if (opts.io == ODE_IO_HOST) {
+        e = cudaMemcpyAsync(y_out, d_yout, sizeof(double) * ny, cudaMemcpyDeviceToHost, stream);
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+            if (*host_cnt[k]) e = cudaMemcpyAsync(*host_cnt[k], *dev_cnt[k], sizeof(int32_t) * nsys, cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    if (opts.io == ODE_IO_HOST || opts.sync) {
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    }
+    return ODE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle) {
+    g_err.clear();
+    if (!rhs_handle) return fail(ODE_ERR_ARG, "rhs_handle is NULL");
+    RhsEntry r;
+    int rc = validate_desc(desc, &r);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int32_t h = g_next_handle++;
+    g_reg[h] = r;
+    *rhs_handle = h;
+    return ODE_OK;
+}
+
+int ode_rhs_release(int32_t rhs_handle) {
+    g_err.clear();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_reg.erase(rhs_handle) == 0) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    return ODE_OK;
+}
+
+int rkck_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0, double tend,
+                   double rtol, double atol, const ode_opts* opts, double* y_out, const ode_stats* stats,
+                   void* stream) {
+    return integrate(kRkck, rhs, nsys, y0, params, t0, tend, rtol, atol, opts, y_out, stats, stream);
+}
+
+int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0, double tend,
+                  double rtol, double atol, const ode_opts* opts, double* y_out, const ode_stats* stats,
+                  void* stream) {
+    return integrate(kRkc, rhs, nsys, y0, params, t0, tend, rtol, atol, opts, y_out, stats, stream);
+}
+
+const char* ode_last_error(void) { return g_err.c_str(); }
+
+const char* ode_version(void) { return "batchode 0.1 (sm_103a)"; }
+
+}  // extern "C"

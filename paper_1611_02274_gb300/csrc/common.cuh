@@ -1,0 +1,70 @@
+// common.cuh -- shared device definitions of the batched integrators.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "batchode.h"
+
+namespace bode {
+
+// Constants of the paper's listings (Section 3.1 constants, Section 3.2).
+constexpr double kUround = 2.22e-16;
+constexpr double kSafety = 0.9;
+constexpr double kPgrow = -0.2;
+constexpr double kPshrnk = -0.25;
+constexpr double kErrcon = 1.89e-4;
+constexpr double kTiny = 1.0e-30;
+constexpr double kP1 = 0.1;  // factor-of-ten limit on step decreases (P1 of the listings)
+constexpr int kSpecradItmax = 50;
+constexpr int kSpecradEvery = 25;
+
+constexpr int kMaxReactions = 64;
+constexpr int kMaxSpecies = 32;
+
+// One registered mass-action network, passed to kernels by value (lives in
+// the kernel-parameter constant bank, so warp-uniform reads broadcast).
+struct MassActionNet {
+    int32_t n_species;
+    int32_t n_reactions;
+    double kmin, kmax;
+    int8_t n_reac[kMaxReactions];
+    int8_t n_prod[kMaxReactions];
+    int8_t reac[kMaxReactions][2];
+    int8_t prod[kMaxReactions][2];
+    double log10A[kMaxReactions];
+    double beta[kMaxReactions];
+    double Ea[kMaxReactions];
+};
+
+struct BrussConst {
+    double A, B, ubc, vbc;
+};
+
+// Everything one batched launch needs besides the model.
+struct BatchArgs {
+    int64_t nsys;
+    int32_t neq;
+    int32_t max_attempts;
+    const double* y0;
+    const double* params;
+    double* y_out;
+    double t0, tend, rtol, atol;
+    int32_t* n_accept;
+    int32_t* n_reject;
+    int32_t* n_rhs;
+    int32_t* n_specrad;
+    int32_t* status;
+    // persistent mapping: work-queue cursor (zeroed before the launch)
+    unsigned long long* cursor;
+    // RKC stage coefficients for m = 2..rkc_tab_max (entry (m, j), j = 1..m,
+    // at index m (m - 1) / 2 - 1 + j - 1): FP64 {1 - mu - nu, mu, nu, mu~,
+    // gamma~, c, 0, 0} and FP32 {mu, nu, mu~, gamma~}
+    const double* rkc_tab64;
+    const float4* rkc_tab32;
+    int32_t rkc_tab_max;
+};
+
+__host__ __device__ inline int rkc_tab_index(int m, int j) { return m * (m - 1) / 2 - 1 + (j - 1); }
+
+}  // namespace bode

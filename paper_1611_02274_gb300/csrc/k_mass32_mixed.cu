@@ -1,0 +1,16 @@
+// k_mass32_mixed.cu -- mass-action kernels for networks of <= 32 species and <= 64 reactions
+// (one thread per system, reaction loop not unrolled);
+// mixed FP32/FP64 form.
+#include "run_model.cuh"
+
+namespace bode {
+
+cudaError_t launch_mass32_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+    *ok = true;
+    (void)r;
+    if (true) return run_model_prec<MassActionModel<32, 64>, ODE_PREC_MIXED>(method, a, r.net, c);
+    *ok = false;
+    return cudaSuccess;
+}
+
+}  // namespace bode

@@ -1,0 +1,15 @@
+// k_vdp_f64.cu -- van der Pol kernels (one thread per system);
+// plain FP64 form; compiled without multiply-add contraction.
+#include "run_model.cuh"
+
+namespace bode {
+
+cudaError_t launch_vdp_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+    *ok = true;
+    (void)r;
+    if (true) return run_model_prec<VdpModel, ODE_PREC_FP64>(method, a, NoCtx{}, c);
+    *ok = false;
+    return cudaSuccess;
+}
+
+}  // namespace bode

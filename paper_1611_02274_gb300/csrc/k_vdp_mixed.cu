@@ -1,0 +1,15 @@
+// k_vdp_mixed.cu -- van der Pol kernels (one thread per system);
+// mixed FP32/FP64 form.
+#include "run_model.cuh"
+
+namespace bode {
+
+cudaError_t launch_vdp_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+    *ok = true;
+    (void)r;
+    if (true) return run_model_prec<VdpModel, ODE_PREC_MIXED>(method, a, NoCtx{}, c);
+    *ok = false;
+    return cudaSuccess;
+}
+
+}  // namespace bode

@@ -1,0 +1,280 @@
+// rhs.cuh -- device right-hand sides f(t, y; g) of the registered families.
+//
+// A Model fixes the team width W (lanes per system) and PER (state slots
+// per lane).  Its Sys<R> holds one system's parameters in registers
+// (R = double for the plain form, float for the mixed form) and provides
+//   comp(team, s)  component index held in slot s by this lane (-1 = unused)
+//   rhs(team, t, y, f)  f = f(t, y) on this lane's slots.
+// Grid families (Brusselator, oscillator chain) place grid point
+// g = q W + lane in slots 2q (u or x) and 2q + 1 (v), so stencil neighbours
+// are one lane away and come from shuffles.  Evaluation orders follow the
+// defining formulas left to right (the compiler may fuse a multiply-add).
+#pragma once
+#include <cmath>
+
+#include "common.cuh"
+#include "team.cuh"
+#include "xmath.cuh"
+
+namespace bode {
+
+struct NoCtx {};
+
+// van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1.  params [mu].
+struct VdpModel {
+    static constexpr int W = 1, PER = 2;
+    using Ctx = NoCtx;
+    template <class R>
+    struct Sys {
+        R mu;
+        int n;
+        __device__ void load(const Ctx&, const Team<W>&, double param, int neq) {
+            mu = (R)param;
+            n = neq;
+        }
+        __device__ int comp(const Team<W>&, int s) const { return s; }
+        // sum over components in component order (the plain form's norms)
+        template <class T>
+        __device__ T ordered_sum(const Team<W>&, const T* x) const {
+            T acc = T(0);
+            acc = acc + x[0];
+            acc = acc + x[1];
+            return acc;
+        }
+        __device__ void rhs(const Team<W>&, R, const R* y, R* f) const {
+            f[0] = y[1];
+            f[1] = mu * (R(1) - y[0] * y[0]) * y[1] - y[0];
+        }
+    };
+};
+
+struct GridCtx {
+    double A, B, ubc, vbc;  // Brusselator constants
+    double coupling;        // chain coupling
+};
+
+// Chain of n van der Pol oscillators, state [x_1..x_n, v_1..v_n]:
+// x_i' = v_i, v_i' = mu (1 - x_i^2) v_i - x_i + c ((x_{i-1} - x_i) + (x_{i+1} - x_i)),
+// neighbour terms dropped at the free ends.  params [mu].
+template <int W_, int G>
+struct ChainModel {
+    static constexpr int W = W_, PER = 2 * G;
+    using Ctx = GridCtx;
+    template <class R>
+    struct Sys {
+        R mu, c;
+        int n, npts;
+        __device__ void load(const Ctx& ctx, const Team<W>&, double param, int neq) {
+            mu = (R)param;
+            c = (R)ctx.coupling;
+            n = neq;
+            npts = neq / 2;
+        }
+        __device__ int comp(const Team<W>& tm, int s) const {
+            const int g = (s >> 1) * W + tm.lane;
+            return g < npts ? ((s & 1) ? npts + g : g) : -1;
+        }
+        // sum over components in component order, first field then second
+        // (the plain form's norms, reproducing a sequential loop)
+        template <class T>
+        __device__ T ordered_sum(const Team<W>& tm, const T* x) const {
+            T acc = T(0);
+#pragma unroll
+            for (int fld = 0; fld < 2; ++fld)
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+#pragma unroll
+                    for (int l = 0; l < W; ++l) {
+                        const T v = tm.bcast(x[2 * q + fld], l);
+                        if (q * W + l < npts) acc = acc + v;
+                    }
+            return acc;
+        }
+        __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int g = q * W + tm.lane;
+                const R x = y[2 * q];
+                R xl = tm.from_left(x);
+                if (q > 0) {
+                    const R w = tm.bcast(y[2 * q - 2], W - 1);
+                    if (tm.lane == 0) xl = w;
+                }
+                R xr = tm.from_right(x);
+                if (q < G - 1) {
+                    const R w = tm.bcast(y[2 * q + 2], 0);
+                    if (tm.lane == W - 1) xr = w;
+                }
+                R coup = R(0);
+                if (g > 0) coup = coup + (xl - x);
+                if (g + 1 < npts) coup = coup + (xr - x);
+                const R v = y[2 * q + 1];
+                f[2 * q] = v;
+                f[2 * q + 1] = mu * (R(1) - x * x) * v - x + c * coup;
+            }
+        }
+    };
+};
+
+// 1D Brusselator on n interior points, state [u_1..u_n, v_1..v_n]:
+// u' = A + u^2 v - (B + 1) u + D (u_{k-1} - 2 u_k + u_{k+1}),
+// v' = B u - u^2 v + D (v_{k-1} - 2 v_k + v_{k+1}),
+// D = a / dx^2, dx = 1/(n+1), ghosts u = ubc, v = vbc.  params [a].
+template <int W_, int G>
+struct BrussModel {
+    static constexpr int W = W_, PER = 2 * G;
+    using Ctx = GridCtx;
+    template <class R>
+    struct Sys {
+        R D, A, B1, B, ubc, vbc;
+        int n, npts;
+        __device__ void load(const Ctx& ctx, const Team<W>&, double a, int neq) {
+            n = neq;
+            npts = neq / 2;
+            const double dx = 1.0 / (double)(npts + 1);
+            D = (R)(a / (dx * dx));
+            A = (R)ctx.A;
+            B = (R)ctx.B;
+            B1 = (R)(ctx.B + 1.0);
+            ubc = (R)ctx.ubc;
+            vbc = (R)ctx.vbc;
+        }
+        __device__ int comp(const Team<W>& tm, int s) const {
+            const int g = (s >> 1) * W + tm.lane;
+            return g < npts ? ((s & 1) ? npts + g : g) : -1;
+        }
+        // sum over components in component order, first field then second
+        // (the plain form's norms, reproducing a sequential loop)
+        template <class T>
+        __device__ T ordered_sum(const Team<W>& tm, const T* x) const {
+            T acc = T(0);
+#pragma unroll
+            for (int fld = 0; fld < 2; ++fld)
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+#pragma unroll
+                    for (int l = 0; l < W; ++l) {
+                        const T v = tm.bcast(x[2 * q + fld], l);
+                        if (q * W + l < npts) acc = acc + v;
+                    }
+            return acc;
+        }
+        __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int g = q * W + tm.lane;
+                const R u = y[2 * q], v = y[2 * q + 1];
+                R ul = tm.from_left(u), vl = tm.from_left(v);
+                if (q > 0) {
+                    const R uw = tm.bcast(y[2 * q - 2], W - 1), vw = tm.bcast(y[2 * q - 1], W - 1);
+                    if (tm.lane == 0) {
+                        ul = uw;
+                        vl = vw;
+                    }
+                }
+                R ur = tm.from_right(u), vr = tm.from_right(v);
+                if (q < G - 1) {
+                    const R uw = tm.bcast(y[2 * q + 2], 0), vw = tm.bcast(y[2 * q + 3], 0);
+                    if (tm.lane == W - 1) {
+                        ur = uw;
+                        vr = vw;
+                    }
+                }
+                if (g == 0) {
+                    ul = ubc;
+                    vl = vbc;
+                }
+                if (g + 1 >= npts) {
+                    ur = ubc;
+                    vr = vbc;
+                }
+                const R uuv = u * u * v;
+                f[2 * q] = A + uuv - B1 * u + D * (ul - R(2) * u + ur);
+                f[2 * q + 1] = B * u - uuv + D * (vl - R(2) * v + vr);
+            }
+        }
+    };
+};
+
+// Mass-action kinetics with a registered network (Section 4.2 omega_i at
+// constant T): r_j = k_j prod_{reactants} C, C_s' = sum_j (nu''_sj - nu'_sj) r_j,
+// accumulated over reactions in order, reactants then products.  params [T].
+// The rate constants (step a2: Arrhenius, clipped) are computed once per
+// system and kept in registers.  One thread per system.
+template <int NS, int NR>
+struct MassActionModel {
+    static constexpr int W = 1, PER = NS;
+    using Ctx = MassActionNet;
+    template <class R>
+    struct Sys {
+        const MassActionNet* net;
+        R k[NR];
+        int n;
+        __device__ void load(const Ctx& ctx, const Team<W>&, double T, int neq) {
+            net = &ctx;
+            n = neq;
+            // mixed form: log2 k in FP64 (a few operations per reaction), then
+            // the fractional power of two in FP32 (accurate to an FP32 ulp)
+            const double lnT = (sizeof(R) == 8) ? 0.0 : log(T);
+            const double lnT64 = (sizeof(R) == 8) ? xm::log_series(T) : 0.0;
+            const double invT = (sizeof(R) == 8) ? 0.0 : 1.0 / T;
+#pragma unroll(NR <= 32 ? NR : 1)
+            for (int j = 0; j < NR; ++j) {
+                if (j < ctx.n_reactions) {
+                    double kk;
+                    if constexpr (sizeof(R) == 8) {
+                        // A T^b exp(-Ea/T) with A = 10^log10A, as one series exponential
+                        kk = xm::exp_series(xm::kLn10 * ctx.log10A[j] + ctx.beta[j] * lnT64 - ctx.Ea[j] / T);
+                    } else {
+                        const double l2 = (2.302585092994046 * ctx.log10A[j] + ctx.beta[j] * lnT - ctx.Ea[j] * invT) *
+                                          1.4426950408889634;
+                        const double li = floor(l2);
+                        kk = (double)ldexpf(exp2f((float)(l2 - li)), (int)li);
+                    }
+                    kk = fmin(fmax(kk, ctx.kmin), ctx.kmax);
+                    k[j] = (R)kk;
+                } else {
+                    k[j] = R(0);
+                }
+            }
+        }
+        __device__ int comp(const Team<W>&, int s) const { return s < n ? s : -1; }
+        template <class T>
+        __device__ T ordered_sum(const Team<W>&, const T* x) const {
+            T acc = T(0);
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                if (s < n) acc = acc + x[s];
+            return acc;
+        }
+        __device__ void rhs(const Team<W>&, R, const R* y, R* f) const {
+            // gathers and scatters by species index go through small local arrays
+            R c[NS], acc[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                c[s] = y[s];
+                acc[s] = R(0);
+            }
+            const MassActionNet& nt = *net;
+            // small networks: fully unrolled (rate constants stay in registers)
+#pragma unroll(NR <= 32 ? NR : 1)
+            for (int j = 0; j < NR; ++j) {
+                if (j < nt.n_reactions) {
+                    const int r0 = nt.reac[j][0];
+                    R r = k[j] * c[r0];
+                    const bool two = nt.n_reac[j] == 2;
+                    const int r1 = nt.reac[j][1];
+                    if (two) r = r * c[r1];
+                    acc[r0] -= r;
+                    if (two) acc[r1] -= r;
+                    acc[nt.prod[j][0]] += r;
+                    if (nt.n_prod[j] == 2) acc[nt.prod[j][1]] += r;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) f[s] = acc[s];
+        }
+    };
+};
+
+}  // namespace bode

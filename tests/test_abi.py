@@ -1,0 +1,77 @@
+"""The C ABI library builds, loads and exports every declared entry point;
+host-side validation answers without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1611_02274_gb300 import binding as B
+from paper_1611_02274_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\([^;]*\)\s*;", text, flags=re.M)
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    names = declared_functions()
+    assert set(B.EXPORTED) <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert "sm_103a" in B.version()
+
+
+def test_register_validation():
+    with pytest.raises(B.BatchOdeError) as e:
+        B.register(99, 2)
+    assert e.value.code == B.ODE_ERR_ARG
+    with pytest.raises(B.BatchOdeError):
+        B.register(B.ODE_RHS_VDP, 3)
+    with pytest.raises(B.BatchOdeError):
+        B.register(B.ODE_RHS_BRUSS1D, 7)
+    net = W.make_network(0)
+    bad = W.Network(net.n_species, net.n_reac, net.reac.copy(), net.n_prod, net.prod, net.log10A,
+                    net.beta, net.Ea)
+    bad.reac[0, 0] = 13
+    with pytest.raises(B.BatchOdeError):
+        B.register(B.ODE_RHS_MASSACTION, 13, network=bad)
+    h = B.register(B.ODE_RHS_MASSACTION, 13, network=net)
+    assert h > 0
+    B.release(h)
+    with pytest.raises(B.BatchOdeError) as e:
+        B.release(h)
+    assert e.value.code == B.ODE_ERR_HANDLE
+
+
+def test_integrate_argument_errors_before_any_launch():
+    h = B.register(B.ODE_RHS_VDP, 2)
+    y = np.zeros((2, 4))
+    p = np.ones((1, 4))
+    for kw, code in [(dict(rtol=0.0), B.ODE_ERR_ARG), (dict(atol=-1.0), B.ODE_ERR_ARG),
+                     (dict(t0=1.0, tend=0.0), B.ODE_ERR_ARG)]:
+        args = dict(t0=0.0, tend=1.0, rtol=1e-6, atol=1e-9)
+        args.update(kw)
+        with pytest.raises(B.BatchOdeError) as e:
+            B.integrate("rkck", h, y, p, **args)
+        assert e.value.code == code
+    with pytest.raises(B.BatchOdeError) as e:
+        B.integrate("rkc", h + 1000, y, p, 0.0, 1.0, 1e-6, 1e-9)
+    assert e.value.code == B.ODE_ERR_HANDLE
+    # an empty batch is a successful no-op
+    B.integrate("rkck", h, np.zeros((2, 0)), np.zeros((1, 0)), 0.0, 1.0, 1e-6, 1e-9)
+    o = B.Opts()
+    o.reserved[3] = 1
+    rc = B.load().rkck_integrate(h, 4, C.c_void_p(y.ctypes.data), C.c_void_p(p.ctypes.data), 0.0, 1.0,
+                                 1e-6, 1e-9, C.byref(o), C.c_void_p(y.ctypes.data), None, None)
+    assert rc == B.ODE_ERR_ARG
+    B.release(h)

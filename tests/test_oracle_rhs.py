@@ -125,3 +125,18 @@ def test_vdp_chain_is_coupled_harmonic_chain_at_mu_zero():
     want = sorted([s * w for w in om for s in (1, -1)])
     np.testing.assert_allclose(sorted(ev.imag), want, atol=1e-8)
     np.testing.assert_allclose(ev.real, 0.0, atol=1e-8)
+
+
+def test_series_log_exp_pow_against_libm():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([10.0 ** rng.uniform(-300, 300, 2000), rng.uniform(0.5, 2.0, 2000), [1.0, 2.0, 0.5]])
+    for x in xs:
+        assert O.series_log(x) == pytest.approx(math.log(x), rel=1e-15, abs=2e-17)
+    for x in np.concatenate([rng.uniform(-700, 700, 2000), rng.uniform(-1, 1, 2000), [0.0, 1.0, -1.0]]):
+        assert O.series_exp(x) == pytest.approx(math.exp(x), rel=8e-16)
+    # the powers the step-size rules and the Arrhenius rate take
+    for e in (-0.25, -0.2, 1.0 / 3.0, 2.0 / 3.0):
+        for x in 10.0 ** rng.uniform(-12, 6, 500):
+            assert O.series_pow(x, e) == pytest.approx(x ** e, rel=4e-15)
+    assert O.series_pow(0.0, 1.0 / 3.0) == 0.0
+    assert O.series_log(1.0) == 0.0 and O.series_exp(0.0) == 1.0
