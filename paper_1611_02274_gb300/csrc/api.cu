@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 // Per-device workspace: a ring of queue cursors and a grow-only staging
 // buffer for host-pointer calls.
 constexpr int kCursorRing = 1024;
-constexpr int kRkcTabMax = 64;  // stage counts with tabulated coefficients
+constexpr int kRkcTabMax = 256;  // stage counts with tabulated coefficients
 struct Workspace {
     unsigned long long* cursors = nullptr;
     int next_cursor = 0;
