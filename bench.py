@@ -154,6 +154,10 @@ def run_ours(args):
         B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
                     precision=prec, mapping=B.ODE_MAP_QUEUE, stream=stream.cuda_stream)
 
+    CHOSEN = B.ODE_PREC_MIXED_CNORM
+    for prec in (CHOSEN, B.ODE_PREC_MIXED, B.ODE_PREC_FP64):
+        B.prepare(h, "rkc", prec)       # generated network kernels compiled before any timing
+
     def timed(prec, steps, warmup):
         for _ in range(warmup):
             step(prec)
@@ -187,14 +191,17 @@ def run_ours(args):
 
     # chosen form: timed with the clock sampler running
     with ClockSampler(gpu_id) as clk:
-        ms_chosen, per_step = timed(B.ODE_PREC_MIXED, args.steps, args.warmup)
+        ms_chosen, per_step = timed(CHOSEN, args.steps, args.warmup)
     clocks = clk.summary()
     # counters of one chosen-form pass (for the flop count) and its output
-    step(B.ODE_PREC_MIXED, cnt)
+    step(CHOSEN, cnt)
     torch.cuda.synchronize()
     c_mixed = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
     y_mixed = yout.cpu().numpy()
     flops_mixed = rkc_flops(w, c_mixed["n_accept"], c_mixed["n_reject"], c_mixed["n_rhs"], c_mixed["n_specrad_iter"])
+
+    # the mixed form with the error norm accumulated in FP64
+    ms_mixed64, _ = timed(B.ODE_PREC_MIXED, args.plain_steps, 1)
 
     # plain FP64 form on the same inputs
     ms_plain, _ = timed(B.ODE_PREC_FP64, args.plain_steps, 1)
@@ -213,7 +220,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
-                    precision=B.ODE_PREC_MIXED, mapping=B.ODE_MAP_QUEUE)
+                    precision=CHOSEN, mapping=B.ODE_MAP_QUEUE)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
@@ -237,7 +244,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded mass-action network and states; no dataset)",
             "config": {"workload": "massaction-13sp-27rx RKC, 1,048,576 systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
-                       "nsys_per_gpu": w.nsys, "method": "rkc", "form": "chosen: FP32 stages + Kahan state, FP64 bookkeeping, persistent queue",
+                       "nsys_per_gpu": w.nsys, "method": "rkc",
+                       "form": "chosen: FP32 stages + Kahan state, FP64 time/step, compensated-FP32 error norm, "
+                               "generated network code, persistent queue",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
             "rhs_evals_per_s": float(np.sum(c_mixed["n_rhs"])) * world / (ms_chosen * 1e-3),
             "plain_fp64": {"value": total_sys / (ms_plain * 1e-3), "ms_per_step": ms_plain,
@@ -245,9 +254,10 @@ def run_ours(args):
                            "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
                            "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
             "speedup_chosen_vs_plain": ms_plain / ms_chosen,
+            "mixed_fp64_norm": {"value": total_sys / (ms_mixed64 * 1e-3), "ms_per_step": ms_mixed64},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_queue<RkcMixed<MassActionModel<16,32>>>",
+                         "kernel": "k_queue<RkcMixed<JitMass, false>> (generated network code)",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                          "peak_measured_fma": peak32 / 1e3, "frac_of_measured": achieved / (peak32 / 1e3),
                          "flops_per_launch": flops_mixed},

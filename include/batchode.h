@@ -75,6 +75,10 @@ extern "C" {
 #define ODE_PREC_MIXED 1     /* FP32 RHS and stage arithmetic with Kahan-compensated FP32 state;
                                 FP64 time, step size, error-norm accumulation and Chebyshev
                                 coefficients */
+#define ODE_PREC_MIXED_CNORM 2 /* as ODE_PREC_MIXED, but the RKC error norm is accumulated in FP32
+                                with compensated (two-sum) summation instead of FP64: the same
+                                accuracy as one rounding, without FP64 instructions (the FP64
+                                pipe of this GPU runs at 1/64 of the FP32 rate) */
 
 /* how systems map onto the GPU */
 #define ODE_MAP_AUTO 0       /* autotuned choice (cached per rhs / method / precision) */
@@ -84,6 +88,12 @@ extern "C" {
 
 #define ODE_IO_DEVICE 0
 #define ODE_IO_HOST 1
+
+/* right-hand-side code generation (mass-action networks) */
+#define ODE_CODEGEN_AUTO 0   /* compile the network into straight-line device code at first use
+                                (NVRTC), falling back to the generic kernels if NVRTC is absent */
+#define ODE_CODEGEN_OFF 1    /* generic kernels that read the network from kernel parameters */
+#define ODE_CODEGEN_ON 2     /* generated code or ODE_ERR_UNSUPPORTED */
 
 typedef struct {
     int32_t kind;         /* ODE_RHS_* */
@@ -116,7 +126,8 @@ typedef struct {
     int32_t block_size;    /* threads per block; 0 = tuned/default */
     int32_t io;            /* ODE_IO_DEVICE or ODE_IO_HOST */
     int32_t sync;          /* nonzero: synchronise the stream before returning */
-    int32_t reserved[10];  /* must be zero */
+    int32_t codegen;       /* ODE_CODEGEN_* (default AUTO) */
+    int32_t reserved[9];   /* must be zero */
 } ode_opts;
 
 /* Per-system outputs, each an array of nsys int32 (device pointers unless
@@ -141,6 +152,17 @@ int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle);
 
 /* Release a handle.  ODE_ERR_HANDLE if it is not registered. */
 int ode_rhs_release(int32_t rhs_handle);
+
+/* Compile ahead of time the generated kernels of a registered mass-action
+ * network for one method (0 = RKCK, 1 = RKC) and precision (ODE_PREC_*),
+ * so that the first integrate call (or a CUDA graph capture) does not pay
+ * the compilation.  Kernels are cached in memory per device and as cubins
+ * on disk (directory BATCHODE_CACHE_DIR, else $HOME/.cache/batchode).
+ * Without a visible device only the compilation (and disk cache) happens.
+ * Other families need no preparation and return ODE_OK.  Errors:
+ * ODE_ERR_HANDLE, ODE_ERR_ARG, ODE_ERR_UNSUPPORTED (NVRTC missing or the
+ * compilation failed; ode_last_error has the log), ODE_ERR_CUDA. */
+int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision);
 
 /* Integrate nsys systems from t0 to tend with the adaptive RKCK method.
  * y0, params: [neq][nsys] and [n_params][nsys] FP64; y_out: [neq][nsys].

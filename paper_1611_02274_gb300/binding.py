@@ -21,11 +21,12 @@ ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM = 
 ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 3
 ODE_ST_SPECRAD_NOCONV = 256
 ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION = 1, 2, 3, 4
-ODE_PREC_FP64, ODE_PREC_MIXED = 0, 1
+ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_CNORM = 0, 1, 2
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
 ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
+ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
 
-EXPORTED = ["ode_rhs_register", "ode_rhs_release", "rkck_integrate", "rkc_integrate",
+EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_integrate", "rkc_integrate",
             "ode_last_error", "ode_version", "bode_fma_peak"]
 
 
@@ -44,7 +45,7 @@ class RhsDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("codegen", C.c_int32), ("reserved", C.c_int32 * 9)]
 
 
 class Stats(C.Structure):
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
     P = C.c_void_p
     L.ode_rhs_register.argtypes = [C.POINTER(RhsDesc), C.POINTER(C.c_int32)]
     L.ode_rhs_release.argtypes = [C.c_int32]
+    L.ode_rhs_prepare.argtypes = [C.c_int32, C.c_int32, C.c_int32]
     for name in ("rkck_integrate", "rkc_integrate"):
         fn = getattr(L, name)
         fn.argtypes = [C.c_int32, C.c_int64, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -130,6 +132,11 @@ def register_workload(w: W.Workload) -> int:
     return register(w.kind, w.neq, network=w.network)
 
 
+def prepare(handle: int, method: str, precision: int = ODE_PREC_FP64):
+    """ode_rhs_prepare: compile a mass-action network's generated kernels ahead of time."""
+    _check(load().ode_rhs_prepare(handle, 0 if method == "rkck" else 1, precision))
+
+
 def release(handle: int):
     _check(load().ode_rhs_release(handle))
 
@@ -154,7 +161,7 @@ class Counters:
 def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
-              stream=None, sync: bool = False):
+              stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
     tensor for device io, numpy array for host io); returns y_out."""
     host = isinstance(y0, np.ndarray)
@@ -165,6 +172,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.precision, o.mapping, o.block_size, o.max_attempts = precision, mapping, block_size, max_attempts
     o.io = ODE_IO_HOST if host else ODE_IO_DEVICE
     o.sync = 1 if sync else 0
+    o.codegen = codegen
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [

@@ -23,7 +23,39 @@ LIB = os.path.join(PKG, "libbatchode.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
+# device headers compiled again at run time (NVRTC) for generated right-hand sides
+JIT_HEADERS = [os.path.join(CSRC, h) for h in (
+    "common.cuh", "team.cuh", "xmath.cuh", "rkc_coef.cuh", "integrators.cuh", "kernels.cuh", "rhs.cuh")]
+
+
+def write_jit_sources() -> None:
+    """Embed the device headers as string literals for the run-time compiler."""
+    delim = "BODEJIT"
+    names, bodies = [], []
+    for path in JIT_HEADERS:
+        text = open(path).read()
+        assert ")" + delim + "\"" not in text
+        names.append(os.path.basename(path))
+        bodies.append(text)
+    # the public header's constants (its function declarations are host code)
+    import re
+    consts = ["#define %s %s" % m.groups() for m in
+              re.finditer(r"^#define (ODE_\w+)\s+(\(?-?\w+\)?)", open(os.path.join(INCLUDE, "batchode.h")).read(), re.M)]
+    names.insert(0, "batchode.h")
+    bodies.insert(0, "#pragma once\n" + "\n".join(consts) + "\n")
+    out = ["// generated by build.py: device headers for the run-time compiler"]
+    out.append("static const char* const kJitHeaderNames[] = {" + ", ".join('"%s"' % n for n in names) + "};")
+    out.append("static const char* const kJitHeaderSources[] = {")
+    for b in bodies:
+        out.append('R"%s(%s)%s",' % (delim, b, delim))
+    out.append("};")
+    out.append("static const int kJitHeaderCount = %d;" % len(names))
+    text = "\n".join(out) + "\n"
+    path = os.path.join(BUILD, "jit_sources.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
 
 
 def nvcc() -> str:
@@ -58,6 +90,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if fh.read() == stamp:
                 return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_sources()
     cc = nvcc()
 
     def compile_one(src):

@@ -11,6 +11,7 @@
 #include <string>
 
 #include "batchode.h"
+#include "jit.h"
 #include "launch.cuh"
 
 using namespace bode;
@@ -150,9 +151,10 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     ode_opts opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    for (int k = 0; k < 10; ++k)
+    for (int k = 0; k < 9; ++k)
         if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
-    if (opts.precision != ODE_PREC_FP64 && opts.precision != ODE_PREC_MIXED)
+    if (opts.codegen < ODE_CODEGEN_AUTO || opts.codegen > ODE_CODEGEN_ON) return fail(ODE_ERR_ARG, "unknown codegen mode %d", opts.codegen);
+    if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_CNORM)
         return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
     if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
     if (opts.io != ODE_IO_DEVICE && opts.io != ODE_IO_HOST) return fail(ODE_ERR_ARG, "unknown io mode %d", opts.io);
@@ -248,7 +250,16 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     const int meth = method == kRkck ? kMethodRkck : kMethodRkc;
     switch (rhs.kind) {
     case ODE_RHS_VDP: e = launch_vdp(meth, opts.precision, rhs, a, cfg, &supported); break;
-    case ODE_RHS_MASSACTION: e = launch_mass(meth, opts.precision, rhs, a, cfg, &supported); break;
+    case ODE_RHS_MASSACTION:
+        if (opts.codegen == ODE_CODEGEN_ON || (opts.codegen == ODE_CODEGEN_AUTO && jit_available())) {
+            std::string why;
+            rc = jit_launch(rhs, meth, opts.precision, a, cfg, &why);
+            if (rc) return fail(rc, "%s", why.c_str());
+            e = cudaSuccess;
+        } else {
+            e = launch_mass(meth, opts.precision, rhs, a, cfg, &supported);
+        }
+        break;
     case ODE_RHS_BRUSS1D: e = launch_bruss(meth, opts.precision, rhs, a, cfg, &supported); break;
     case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, opts.precision, rhs, a, cfg, &supported); break;
     default: supported = false; e = cudaSuccess;
@@ -290,6 +301,24 @@ int ode_rhs_release(int32_t rhs_handle) {
     g_err.clear();
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_reg.erase(rhs_handle) == 0) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    return ODE_OK;
+}
+
+int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision) {
+    g_err.clear();
+    if (method != 0 && method != 1) return fail(ODE_ERR_ARG, "method must be 0 (RKCK) or 1 (RKC)");
+    if (precision < ODE_PREC_FP64 || precision > ODE_PREC_MIXED_CNORM) return fail(ODE_ERR_ARG, "unknown precision %d", precision);
+    RhsEntry r;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_reg.find(rhs_handle);
+        if (it == g_reg.end()) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+        r = it->second;
+    }
+    if (r.kind != ODE_RHS_MASSACTION) return ODE_OK;
+    std::string why;
+    const int rc = jit_prepare(r, method == 0 ? kMethodRkck : kMethodRkc, precision, &why);
+    if (rc) return fail(rc, "%s", why.c_str());
     return ODE_OK;
 }
 

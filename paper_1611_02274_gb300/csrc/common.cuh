@@ -37,6 +37,9 @@ struct MassActionNet {
     double Ea[kMaxReactions];
 };
 
+// Kernel context of right-hand sides that need none.
+struct NoCtx {};
+
 struct BrussConst {
     double A, B, ubc, vbc;
 };

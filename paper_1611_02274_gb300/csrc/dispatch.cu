@@ -4,36 +4,36 @@
 namespace bode {
 
 cudaError_t launch_vdp_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
-cudaError_t launch_vdp_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_vdp_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_mass16_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
-cudaError_t launch_mass16_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_mass16_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_mass32_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
-cudaError_t launch_mass32_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_mass32_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_bruss_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
-cudaError_t launch_bruss_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_bruss_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
-cudaError_t launch_chain_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_chain_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 namespace {
 inline bool f64(int prec) { return prec == ODE_PREC_FP64; }
 }  // namespace
 
 cudaError_t launch_vdp(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
-    return f64(prec) ? launch_vdp_f64(method, r, a, c, ok) : launch_vdp_mixed(method, r, a, c, ok);
+    return f64(prec) ? launch_vdp_f64(method, r, a, c, ok) : launch_vdp_mixed(method, prec, r, a, c, ok);
 }
 
 cudaError_t launch_mass(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     if (r.net.n_species <= 16 && r.net.n_reactions <= 32)
-        return f64(prec) ? launch_mass16_f64(method, r, a, c, ok) : launch_mass16_mixed(method, r, a, c, ok);
-    return f64(prec) ? launch_mass32_f64(method, r, a, c, ok) : launch_mass32_mixed(method, r, a, c, ok);
+        return f64(prec) ? launch_mass16_f64(method, r, a, c, ok) : launch_mass16_mixed(method, prec, r, a, c, ok);
+    return f64(prec) ? launch_mass32_f64(method, r, a, c, ok) : launch_mass32_mixed(method, prec, r, a, c, ok);
 }
 
 cudaError_t launch_bruss(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
-    return f64(prec) ? launch_bruss_f64(method, r, a, c, ok) : launch_bruss_mixed(method, r, a, c, ok);
+    return f64(prec) ? launch_bruss_f64(method, r, a, c, ok) : launch_bruss_mixed(method, prec, r, a, c, ok);
 }
 
 cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
-    return f64(prec) ? launch_chain_f64(method, r, a, c, ok) : launch_chain_mixed(method, r, a, c, ok);
+    return f64(prec) ? launch_chain_f64(method, r, a, c, ok) : launch_chain_mixed(method, prec, r, a, c, ok);
 }
 
 }  // namespace bode

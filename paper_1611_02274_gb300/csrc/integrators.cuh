@@ -696,7 +696,21 @@ struct RkckMixed {
 
 // =============================================================== RKC mixed
 
-template <class Model>
+// Compensated FP32 accumulation (Knuth's two-sum): the rounding error of each
+// addition is collected in c, so s + c carries the sum to about one rounding.
+struct SumF2 {
+    float s = 0.0f, c = 0.0f;
+    __device__ void add(float x) {
+        const float t = s + x;
+        const float bb = t - s;
+        c += (s - (t - bb)) + (x - bb);
+        s = t;
+    }
+};
+
+// NORM64: accumulate the weighted error norm in FP64 (ODE_PREC_MIXED); else
+// in compensated FP32 (ODE_PREC_MIXED_CNORM).
+template <class Model, bool NORM64 = true>
 struct RkcMixed {
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
@@ -704,7 +718,7 @@ struct RkcMixed {
     typename Model::template Sys<float> sys;
     float yh[P], yl[P], Fn[P], v[P], d1[P], d2[P];  // d_j = w_j - y_n (d_0 = 0)
     double t, tend, hmax, hmin, h, h_old, sigma, inv_n;
-    float rtolf, atolf, err_old, hf, dynrm, sig;
+    float rtolf, atolf, err_old, hf, dynrm, sig, inv_nf;
     float4 cur;  // (mu_j, nu_j, mu~_j, gamma~_j) of the current stage
     CoefSource cs;
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
@@ -715,6 +729,7 @@ struct RkcMixed {
         sys.load(ctx, tm, a.params[i], a.neq);
         n = a.neq;
         inv_n = 1.0 / (double)n;
+        inv_nf = (float)inv_n;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
@@ -889,14 +904,27 @@ struct RkcMixed {
 
     __device__ void trial_consume(const BatchArgs& a, const TM& tm, const float* f) {
         n_rhs += 1;
-        double acc = 0.0;
+        double ssq;
+        if constexpr (NORM64) {
+            double acc = 0.0;
 #pragma unroll
-        for (int s = 0; s < P; ++s)
-            if (sys.comp(tm, s) >= 0) {
-                const float e = (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
-                acc = fma((double)e, (double)e, acc);
-            }
-        const double est = h * sqrt(tm.sum(acc) * inv_n);
+            for (int s = 0; s < P; ++s)
+                if (sys.comp(tm, s) >= 0) {
+                    const float e = (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
+                    acc = fma((double)e, (double)e, acc);
+                }
+            ssq = tm.sum(acc);
+        } else {
+            SumF2 acc;
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+                if (sys.comp(tm, s) >= 0) {
+                    const float e = (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
+                    acc.add(e * e);
+                }
+            ssq = (double)(tm.sum(acc.s) + tm.sum(acc.c));
+        }
+        const double est = h * sqrt(ssq * inv_n);
         if (kP1 * h < hmax * sqrt(est))
             h = fmax(kP1 * h / sqrt(est), hmin);
         else
@@ -942,24 +970,43 @@ struct RkcMixed {
     __device__ void final_consume(const BatchArgs& a, const TM& tm, const float* f) {
         n_rhs += m;
         const float h04 = 0.4f * hf;
-        double acc = 0.0;
+        bool reject, bad_err;
+        float err;
+        if constexpr (NORM64) {
+            double acc = 0.0;
 #pragma unroll
-        for (int s = 0; s < P; ++s)
-            if (sys.comp(tm, s) >= 0) {
-                const float wm = yh[s] + (yl[s] + d1[s]);
-                const float e = (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(wm), fabsf(yh[s])));
-                acc = fma((double)e, (double)e, acc);
-            }
-        const double ms = tm.sum(acc) * inv_n;  // err^2
-        if (isnan(ms)) {
+            for (int s = 0; s < P; ++s)
+                if (sys.comp(tm, s) >= 0) {
+                    const float wm = yh[s] + (yl[s] + d1[s]);
+                    const float e = (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(wm), fabsf(yh[s])));
+                    acc = fma((double)e, (double)e, acc);
+                }
+            const double ms = tm.sum(acc) * inv_n;  // err^2
+            bad_err = isnan(ms);
+            reject = ms > 1.0;
+            err = sqrtf((float)ms);
+        } else {
+            SumF2 acc;
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+                if (sys.comp(tm, s) >= 0) {
+                    const float wm = yh[s] + (yl[s] + d1[s]);
+                    const float e = (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(wm), fabsf(yh[s])));
+                    acc.add(e * e);
+                }
+            const float ms = (tm.sum(acc.s) + tm.sum(acc.c)) * inv_nf;  // err^2
+            bad_err = isnan(ms);
+            reject = ms > 1.0f;
+            err = sqrtf(ms);
+        }
+        if (bad_err) {
             n_rej += 1;
             status |= ODE_ST_NONFINITE;
             phase = PH_DONE;
             return;
         }
-        const float err = sqrtf((float)ms);
         const float c3 = cbrtf(err);
-        if (ms > 1.0) {
+        if (reject) {
             n_rej += 1;
             h = h * (double)(0.8f / c3);
             rejected = true;

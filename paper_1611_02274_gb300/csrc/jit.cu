@@ -1,0 +1,417 @@
+// jit.cu -- run-time specialisation of the integrator kernels for a
+// registered mass-action network.
+//
+// The generic mass-action kernels read the network from kernel parameters,
+// so every species index is a run-time value and the state vector must be
+// addressed through local memory.  Here the network is written out as
+// straight-line device code (one statement per rate product and per
+// accumulation, in the order the reactions list them), compiled with NVRTC
+// together with the integrator templates, and loaded as a CUDA library:
+// every index is then a compile-time constant and the state stays in
+// registers.  NVRTC is resolved with dlopen at first use, so the library
+// has no link-time dependency on it; compiled kernels are cached per device
+// in memory and as cubins on disk (BATCHODE_CACHE_DIR, else
+// $HOME/.cache/batchode).
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "jit.h"
+
+namespace bode {
+namespace {
+
+#include "jit_sources.inc"  // kJitHeaderNames / kJitHeaderSources / kJitHeaderCount (generated)
+
+// Stand-ins for the host headers the device headers include.
+const char* const kStubNames[] = {"cstdint", "stdint.h", "cmath", "cuda_runtime.h"};
+const char* const kStubSources[] = {
+    "#pragma once\ntypedef signed char int8_t; typedef short int16_t; typedef int int32_t;\n"
+    "typedef long long int64_t; typedef unsigned char uint8_t; typedef unsigned short uint16_t;\n"
+    "typedef unsigned int uint32_t; typedef unsigned long long uint64_t;\n",
+    "#pragma once\n#include <cstdint>\n",
+    "#pragma once\n#define INFINITY (__int_as_float(0x7f800000))\n#define NAN (__int_as_float(0x7fffffff))\n",
+    "#pragma once\n",
+};
+
+struct Nvrtc {
+    bool ok = false;
+    std::string why;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcAddNameExpression) add_name = nullptr;
+    decltype(&nvrtcGetLoweredName) lowered = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    decltype(&nvrtcGetErrorString) errstr = nullptr;
+};
+
+Nvrtc load_nvrtc() {
+    Nvrtc n;
+    std::vector<std::string> names = {"libnvrtc.so.13", "libnvrtc.so"};
+    for (const char* env : {"CUDA_HOME", "CUDA_PATH"}) {
+        const char* p = getenv(env);
+        if (p) names.push_back(std::string(p) + "/lib64/libnvrtc.so.13");
+    }
+    names.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+    void* h = nullptr;
+    for (const auto& name : names)
+        if ((h = dlopen(name.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+        n.why = "libnvrtc.so.13 not found";
+        return n;
+    }
+#define BODE_SYM(field, sym)                                          \
+    n.field = reinterpret_cast<decltype(n.field)>(dlsym(h, #sym));    \
+    if (!n.field) {                                                   \
+        n.why = "missing symbol " #sym;                               \
+        return n;                                                     \
+    }
+    BODE_SYM(create, nvrtcCreateProgram)
+    BODE_SYM(compile, nvrtcCompileProgram)
+    BODE_SYM(log_size, nvrtcGetProgramLogSize)
+    BODE_SYM(log, nvrtcGetProgramLog)
+    BODE_SYM(cubin_size, nvrtcGetCUBINSize)
+    BODE_SYM(cubin, nvrtcGetCUBIN)
+    BODE_SYM(add_name, nvrtcAddNameExpression)
+    BODE_SYM(lowered, nvrtcGetLoweredName)
+    BODE_SYM(destroy, nvrtcDestroyProgram)
+    BODE_SYM(errstr, nvrtcGetErrorString)
+#undef BODE_SYM
+    n.ok = true;
+    return n;
+}
+
+Nvrtc& nvrtc() {
+    static Nvrtc n = load_nvrtc();
+    return n;
+}
+
+std::string lit(double x) {
+    char buf[64];
+    snprintf(buf, sizeof(buf), "%.17g", x);
+    std::string s(buf);
+    if (s.find_first_of(".eEn") == std::string::npos) s += ".0";
+    return "(" + s + ")";
+}
+
+// The network as a Model (see rhs.cuh for the interface): rate constants in
+// registers, f written as straight-line code whose per-species accumulation
+// order is the reaction order (reactants, then products).
+std::string model_source(const RhsEntry& r) {
+    const MassActionNet& net = r.net;
+    const int S = net.n_species, NR = net.n_reactions;
+    std::ostringstream o;
+    o << "struct JitMass {\n"
+      << "  static constexpr int W = 1, PER = " << S << ";\n"
+      << "  using Ctx = bode::NoCtx;\n"
+      << "  template <class R> struct Sys {\n"
+      << "    R k[" << NR << "];\n"
+      << "    int n;\n"
+      << "    __device__ static double clip(double k) { return fmin(fmax(k, " << lit(net.kmin) << "), " << lit(net.kmax)
+      << "); }\n"
+      << "    __device__ void load(const Ctx&, const bode::Team<1>&, double T, int neq) {\n"
+      << "      n = neq;\n"
+      << "      if constexpr (sizeof(R) == 8) {\n"
+      << "        const double lnT = bode::xm::log_series(T);\n";
+    for (int j = 0; j < NR; ++j)
+        o << "        k[" << j << "] = clip(bode::xm::exp_series(bode::xm::kLn10 * " << lit(net.log10A[j]) << " + "
+          << lit(net.beta[j]) << " * lnT - " << lit(net.Ea[j]) << " / T));\n";
+    o << "      } else {\n"
+      << "        const double lnT = log(T), invT = 1.0 / T;\n";
+    for (int j = 0; j < NR; ++j)
+        o << "        { const double l2 = (2.302585092994046 * " << lit(net.log10A[j]) << " + " << lit(net.beta[j])
+          << " * lnT - " << lit(net.Ea[j]) << " * invT) * 1.4426950408889634; const double li = floor(l2);"
+          << " k[" << j << "] = (R)clip((double)ldexpf(exp2f((float)(l2 - li)), (int)li)); }\n";
+    o << "      }\n"
+      << "    }\n"
+      << "    __device__ int comp(const bode::Team<1>&, int s) const { return s; }\n"
+      << "    template <class T> __device__ T ordered_sum(const bode::Team<1>&, const T* x) const {\n"
+      << "      T acc = T(0);\n";
+    for (int s = 0; s < S; ++s) o << "      acc = acc + x[" << s << "];\n";
+    o << "      return acc;\n"
+      << "    }\n"
+      << "    __device__ void rhs(const bode::Team<1>&, R, const R* y, R* f) const {\n";
+    for (int s = 0; s < S; ++s) o << "      R a" << s << " = R(0);\n";
+    for (int j = 0; j < NR; ++j) {
+        o << "      { R r = k[" << j << "];";
+        for (int q = 0; q < net.n_reac[j]; ++q) o << " r = r * y[" << (int)net.reac[j][q] << "];";
+        for (int q = 0; q < net.n_reac[j]; ++q) o << " a" << (int)net.reac[j][q] << " = a" << (int)net.reac[j][q] << " - r;";
+        for (int q = 0; q < net.n_prod[j]; ++q) o << " a" << (int)net.prod[j][q] << " = a" << (int)net.prod[j][q] << " + r;";
+        o << " }\n";
+    }
+    for (int s = 0; s < S; ++s) o << "      f[" << s << "] = a" << s << ";\n";
+    o << "    }\n"
+      << "  };\n"
+      << "};\n";
+    return o.str();
+}
+
+uint64_t fnv1a(const std::string& s) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string cache_dir() {
+    const char* d = getenv("BATCHODE_CACHE_DIR");
+    if (d && *d) return d;
+    const char* home = getenv("HOME");
+    if (!home || !*home) return "";
+    std::string base = std::string(home) + "/.cache";
+    mkdir(base.c_str(), 0755);
+    return base + "/batchode";
+}
+
+bool read_file(const std::string& path, std::vector<char>* out) {
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return false;
+    out->assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+    return !out->empty();
+}
+
+void write_file(const std::string& dir, const std::string& path, const std::vector<char>& data) {
+    if (dir.empty()) return;
+    mkdir(dir.c_str(), 0755);
+    const std::string tmp = path + ".tmp" + std::to_string(getpid());
+    {
+        std::ofstream f(tmp, std::ios::binary);
+        if (!f) return;
+        f.write(data.data(), (std::streamsize)data.size());
+    }
+    rename(tmp.c_str(), path.c_str());
+}
+
+struct JitKernels {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kstatic = nullptr, kqueue = nullptr;
+};
+
+std::mutex g_jit_mu;
+std::map<std::string, JitKernels> g_cache;  // key: device + source hash + form
+
+std::string method_type(int method, int prec) {
+    if (method == kMethodRkck) return prec == ODE_PREC_FP64 ? "bode::RkckF64<JitMass>" : "bode::RkckMixed<JitMass>";
+    if (prec == ODE_PREC_FP64) return "bode::RkcF64<JitMass>";
+    return prec == ODE_PREC_MIXED ? "bode::RkcMixed<JitMass, true>" : "bode::RkcMixed<JitMass, false>";
+}
+
+struct JitImage {
+    std::string low_static, low_queue;
+    std::vector<char> cubin;
+};
+
+int compile_image(const RhsEntry& r, int method, int prec, JitImage* img, std::string* err) {
+    const std::string model = model_source(r);
+    const std::string meth = method_type(method, prec);
+    const std::string nstatic = "bode::k_static<" + meth + ", bode::NoCtx>";
+    const std::string nqueue = "bode::k_queue<" + meth + ", bode::NoCtx>";
+    // the two kernels are instantiated through their name expressions
+    std::string src = "#include \"rhs.cuh\"\n#include \"integrators.cuh\"\n#include \"kernels.cuh\"\n" + model;
+    std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
+                                     prec == ODE_PREC_FP64 ? "--fmad=false" : "--fmad=true"};
+    const char* maxrreg = getenv("BATCHODE_JIT_MAXRREG");  // register cap (occupancy tuning)
+    if (maxrreg && atoi(maxrreg) > 0) opts.push_back(std::string("--maxrregcount=") + std::to_string(atoi(maxrreg)));
+    const char* verbose = getenv("BATCHODE_JIT_VERBOSE");  // print the ptxas resource report
+    if (verbose && *verbose == '1') opts.push_back("-Xptxas=-v");
+    std::string key_text = src + "\n" + nstatic + "\n" + nqueue;
+    for (const auto& o : opts) key_text += "\n" + o;
+    for (int k = 0; k < kJitHeaderCount; ++k) key_text += kJitHeaderSources[k];
+    char hash[32];
+    snprintf(hash, sizeof(hash), "%016llx", (unsigned long long)fnv1a(key_text));
+    const std::string dir = cache_dir();
+    const std::string path = dir.empty() ? "" : dir + "/jit_" + hash + ".bin";
+
+    // cached cubin: the two lowered names, then the image
+    std::vector<char> blob;
+    std::string& low_static = img->low_static;
+    std::string& low_queue = img->low_queue;
+    std::vector<char>& cubin = img->cubin;
+    if (!path.empty() && read_file(path, &blob)) {
+        const char* p = blob.data();
+        const size_t n = blob.size();
+        const size_t a = strnlen(p, n);
+        if (a < n) {
+            const size_t b = strnlen(p + a + 1, n - a - 1);
+            if (a + 1 + b < n) {
+                low_static.assign(p, a);
+                low_queue.assign(p + a + 1, b);
+                cubin.assign(p + a + b + 2, p + n);
+            }
+        }
+    }
+    if (cubin.empty()) {
+        Nvrtc& nv = nvrtc();
+        if (!nv.ok) {
+            *err = "NVRTC unavailable: " + nv.why;
+            return ODE_ERR_UNSUPPORTED;
+        }
+        std::vector<const char*> hnames, hsrcs;
+        for (int k = 0; k < kJitHeaderCount; ++k) {
+            hnames.push_back(kJitHeaderNames[k]);
+            hsrcs.push_back(kJitHeaderSources[k]);
+        }
+        for (int k = 0; k < 4; ++k) {
+            hnames.push_back(kStubNames[k]);
+            hsrcs.push_back(kStubSources[k]);
+        }
+        nvrtcProgram prog;
+        nvrtcResult rc = nv.create(&prog, src.c_str(), "jit_mass.cu", (int)hnames.size(), hsrcs.data(), hnames.data());
+        if (rc != NVRTC_SUCCESS) {
+            *err = std::string("nvrtcCreateProgram: ") + nv.errstr(rc);
+            return ODE_ERR_UNSUPPORTED;
+        }
+        nv.add_name(prog, nstatic.c_str());
+        nv.add_name(prog, nqueue.c_str());
+        std::vector<const char*> copts;
+        for (const auto& o : opts) copts.push_back(o.c_str());
+        rc = nv.compile(prog, (int)copts.size(), copts.data());
+        if (rc != NVRTC_SUCCESS) {
+            size_t ls = 0;
+            nv.log_size(prog, &ls);
+            std::string logtxt(ls, '\0');
+            nv.log(prog, &logtxt[0]);
+            nv.destroy(&prog);
+            *err = "NVRTC compile failed: " + logtxt.substr(0, 2000);
+            return ODE_ERR_UNSUPPORTED;
+        }
+        if (verbose && *verbose == '1') {
+            size_t ls = 0;
+            nv.log_size(prog, &ls);
+            std::string logtxt(ls, '\0');
+            nv.log(prog, &logtxt[0]);
+            fprintf(stderr, "%s\n", logtxt.c_str());
+        }
+        const char* l1 = nullptr;
+        const char* l2 = nullptr;
+        nv.lowered(prog, nstatic.c_str(), &l1);
+        nv.lowered(prog, nqueue.c_str(), &l2);
+        low_static = l1 ? l1 : "";
+        low_queue = l2 ? l2 : "";
+        size_t cs = 0;
+        nv.cubin_size(prog, &cs);
+        cubin.resize(cs);
+        nv.cubin(prog, cubin.data());
+        nv.destroy(&prog);
+        if (!path.empty()) {
+            std::vector<char> out(low_static.begin(), low_static.end());
+            out.push_back('\0');
+            out.insert(out.end(), low_queue.begin(), low_queue.end());
+            out.push_back('\0');
+            out.insert(out.end(), cubin.begin(), cubin.end());
+            write_file(dir, path, out);
+        }
+    }
+    return ODE_OK;
+}
+
+int load_image(const JitImage& img, JitKernels* out, std::string* err) {
+    cudaError_t e = cudaLibraryLoadData(&out->lib, img.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kstatic, out->lib, img.low_static.c_str());
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kqueue, out->lib, img.low_queue.c_str());
+    if (e != cudaSuccess) {
+        *err = std::string("loading generated kernels: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    return ODE_OK;
+}
+
+std::string cache_key(const RhsEntry& r, int method, int prec, int dev) {
+    char key[96];
+    const char* maxrreg = getenv("BATCHODE_JIT_MAXRREG");
+    snprintf(key, sizeof(key), "%d/%d/%d/%016llx/%s", dev, method, prec, (unsigned long long)fnv1a(model_source(r)),
+             maxrreg ? maxrreg : "");
+    return key;
+}
+
+// kernels for the current device, built and loaded at first use
+int get_kernels(const RhsEntry& r, int method, int prec, JitKernels* k, std::string* err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    const std::string key = cache_key(r, method, prec, dev);
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *k = it->second;
+        return ODE_OK;
+    }
+    JitImage img;
+    int rc = compile_image(r, method, prec, &img, err);
+    if (rc == ODE_OK) rc = load_image(img, k, err);
+    if (rc == ODE_OK) g_cache[key] = *k;
+    return rc;
+}
+
+}  // namespace
+
+bool jit_available() { return nvrtc().ok; }
+
+int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();  // clear the no-device error
+        JitImage img;
+        return compile_image(r, method, prec, &img, err);
+    }
+    JitKernels k;
+    return get_kernels(r, method, prec, &k, err);
+}
+
+int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, const LaunchCfg& c, std::string* err) {
+    JitKernels k;
+    int rc = get_kernels(r, method, prec, &k, err);
+    if (rc) return rc;
+    NoCtx ctx;
+    BatchArgs args = a;
+    void* params[] = {&args, &ctx};
+    const int block = c.block;
+    const int64_t threads = a.nsys;  // one thread per system
+    cudaError_t e;
+    if (c.mapping == ODE_MAP_QUEUE) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.kqueue, block, 0);
+        if (e != cudaSuccess) {
+            *err = std::string("occupancy query: ") + cudaGetErrorString(e);
+            return ODE_ERR_CUDA;
+        }
+        if (per_sm < 1) per_sm = 1;
+        int64_t grid = (int64_t)per_sm * c.sm_count;
+        const int64_t need = (threads + block - 1) / block;
+        if (grid > need) grid = need;
+        e = cudaLaunchKernel((const void*)k.kqueue, dim3((unsigned)grid), dim3(block), params, 0, c.stream);
+    } else {
+        const int64_t grid = (threads + block - 1) / block;
+        e = cudaLaunchKernel((const void*)k.kstatic, dim3((unsigned)grid), dim3(block), params, 0, c.stream);
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("generated kernel launch: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    return ODE_OK;
+}
+
+std::string jit_model_source(const RhsEntry& r) { return model_source(r); }
+
+}  // namespace bode

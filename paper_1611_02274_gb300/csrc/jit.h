@@ -1,0 +1,23 @@
+// jit.h -- run-time specialised kernels for registered mass-action networks.
+#pragma once
+#include <string>
+
+#include "launch.cuh"
+
+namespace bode {
+
+// True when NVRTC could be loaded.
+bool jit_available();
+
+// Launch the generated kernels of network r for (method, precision), building
+// and caching them at first use.  Returns ODE_OK or an ODE_ERR_* code with a
+// description in *err.
+int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, const LaunchCfg& c, std::string* err);
+
+// Compile (and, with a device present, load) the generated kernels of r.
+int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err);
+
+// The generated model source of network r (for inspection).
+std::string jit_model_source(const RhsEntry& r);
+
+}  // namespace bode

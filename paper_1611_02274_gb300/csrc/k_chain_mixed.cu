@@ -4,11 +4,11 @@
 
 namespace bode {
 
-cudaError_t launch_chain_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+cudaError_t launch_chain_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
     (void)r;
-    if (r.neq <= 64) return run_model_prec<ChainModel<32, 1>, ODE_PREC_MIXED>(method, a, grid_ctx(r), c);
-    if (r.neq <= 128) return run_model_prec<ChainModel<32, 2>, ODE_PREC_MIXED>(method, a, grid_ctx(r), c);
+    if (r.neq <= 64) return run_model_mixed<ChainModel<32, 1>>(method, prec, a, grid_ctx(r), c);
+    if (r.neq <= 128) return run_model_mixed<ChainModel<32, 2>>(method, prec, a, grid_ctx(r), c);
     *ok = false;
     return cudaSuccess;
 }

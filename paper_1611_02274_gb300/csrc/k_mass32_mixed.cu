@@ -5,10 +5,10 @@
 
 namespace bode {
 
-cudaError_t launch_mass32_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+cudaError_t launch_mass32_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
     (void)r;
-    if (true) return run_model_prec<MassActionModel<32, 64>, ODE_PREC_MIXED>(method, a, r.net, c);
+    if (true) return run_model_mixed<MassActionModel<32, 64>>(method, prec, a, r.net, c);
     *ok = false;
     return cudaSuccess;
 }

@@ -4,10 +4,10 @@
 
 namespace bode {
 
-cudaError_t launch_vdp_mixed(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+cudaError_t launch_vdp_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
     (void)r;
-    if (true) return run_model_prec<VdpModel, ODE_PREC_MIXED>(method, a, NoCtx{}, c);
+    if (true) return run_model_mixed<VdpModel>(method, prec, a, NoCtx{}, c);
     *ok = false;
     return cudaSuccess;
 }

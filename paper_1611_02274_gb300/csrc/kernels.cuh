@@ -1,0 +1,74 @@
+// kernels.cuh -- the batched kernels that drive the per-system integrators
+// (device code only; also compiled at run time for generated right-hand sides).
+#pragma once
+#include "common.cuh"
+#include "team.cuh"
+
+namespace bode {
+
+// One system per team, one launch over the batch (the paper's intDriver
+// mapping when the team is one thread), grid rounded up.  Each iteration
+// evaluates the right-hand side once, at the point the system's phase needs.
+template <class Method, class Ctx>
+__global__ void __launch_bounds__(256) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+    constexpr int W = Method::W, P = Method::P;
+    using R = typename Method::R;
+    const Team<W> tm = Team<W>::make();
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+    if (i >= a.nsys) return;  // team-uniform
+    Method m;
+    m.init(a, ctx, tm, i);
+    R x[P], f[P];
+    while (!m.done()) {
+        R tx;
+        m.point(x, tx);
+        m.sys.rhs(tm, tx, x, f);
+        m.consume(a, tm, f);
+    }
+    m.store(a, tm, i);
+}
+
+// Persistent kernel: each team pulls a system index from the queue cursor;
+// every iteration of the loop evaluates the right-hand side once for every
+// live team of the warp, at one call site, whatever phase each system is
+// in.  A team whose system finishes stores it and pulls the next one before
+// the next evaluation, so no lane idles while a slow neighbour finishes
+// (the divergence tail of the static mapping).  The only inter-thread
+// interaction is the atomic cursor.
+template <class Method, class Ctx>
+__global__ void __launch_bounds__(256) k_queue(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+    constexpr int W = Method::W, P = Method::P;
+    using R = typename Method::R;
+    const Team<W> tm = Team<W>::make();
+    Method m;
+    int64_t i = 0;
+    bool live = false;
+    // pull systems until one needs work (a zero-length interval finishes at init)
+    auto next = [&]() {
+        for (;;) {
+            unsigned long long v = 0;
+            if (tm.lane == 0) v = atomicAdd(a.cursor, 1ull);
+            i = (int64_t)tm.bcast(v, 0);
+            live = i < a.nsys;
+            if (!live) return;
+            m.init(a, ctx, tm, i);
+            if (!m.done()) return;
+            m.store(a, tm, i);
+        }
+    };
+    next();
+    R x[P], f[P];
+    while (__any_sync(0xffffffffu, live)) {
+        if (live) {
+            R tx;
+            m.point(x, tx);
+            m.sys.rhs(tm, tx, x, f);
+            if (m.consume(a, tm, f)) {
+                m.store(a, tm, i);
+                next();
+            }
+        }
+    }
+}
+
+}  // namespace bode

@@ -18,8 +18,6 @@
 
 namespace bode {
 
-struct NoCtx {};
-
 // van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1.  params [mu].
 struct VdpModel {
     static constexpr int W = 1, PER = 2;

@@ -9,7 +9,7 @@ from paper_1611_02274_gb300 import workloads as W
 
 
 def run_gpu(w: W.Workload, precision=B.ODE_PREC_FP64, mapping=B.ODE_MAP_AUTO, method=None,
-            max_attempts=0, block_size=0):
+            max_attempts=0, block_size=0, codegen=B.ODE_CODEGEN_AUTO):
     import torch
     dev = torch.device("cuda:0")
     h = B.register_workload(w)
@@ -19,7 +19,8 @@ def run_gpu(w: W.Workload, precision=B.ODE_PREC_FP64, mapping=B.ODE_MAP_AUTO, me
         cnt = B.counters_like(w.nsys, dev)
         m = method or ("rkck" if w.method == W.METHOD_RKCK else "rkc")
         y = B.integrate(m, h, y0, p, w.t0, w.tend, w.rtol, w.atol, counters=cnt, precision=precision,
-                        mapping=mapping, max_attempts=max_attempts, block_size=block_size, sync=True)
+                        mapping=mapping, max_attempts=max_attempts, block_size=block_size, sync=True,
+                        codegen=codegen)
         torch.cuda.synchronize()
         out = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
         out["y"] = y.cpu().numpy()

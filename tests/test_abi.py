@@ -75,3 +75,24 @@ def test_integrate_argument_errors_before_any_launch():
                                  1e-6, 1e-9, C.byref(o), C.c_void_p(y.ctypes.data), None, None)
     assert rc == B.ODE_ERR_ARG
     B.release(h)
+
+
+def test_generated_network_kernels_compile():
+    """ode_rhs_prepare compiles the straight-line network kernels (NVRTC);
+    without a device this is a compile-only check."""
+    import ctypes
+    try:
+        ctypes.CDLL("libnvrtc.so.13")
+    except OSError:
+        pytest.skip("NVRTC not installed")
+    w = W.massaction(8)
+    h = B.register_workload(w)
+    for m in ("rkc", "rkck"):
+        for p in (B.ODE_PREC_FP64, B.ODE_PREC_MIXED):
+            B.prepare(h, m, p)
+    assert B.load().ode_rhs_prepare(h, 7, 0) == B.ODE_ERR_ARG
+    B.release(h)
+    # other families need no preparation
+    h = B.register(B.ODE_RHS_VDP, 2)
+    B.prepare(h, "rkck")
+    B.release(h)

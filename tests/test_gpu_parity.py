@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-9
 
 
-def check_fp64(w, mapping=B.ODE_MAP_AUTO, method=None):
+def check_fp64(w, mapping=B.ODE_MAP_AUTO, method=None, codegen=B.ODE_CODEGEN_AUTO):
     ref = O.integrate_workload(w) if method is None else O.integrate(
         O.model_for(w), 0 if method == "rkck" else 1, w.y0, w.params, w.t0, w.tend, w.rtol, w.atol)
-    g = run_gpu(w, mapping=mapping, method=method)
+    g = run_gpu(w, mapping=mapping, method=method, codegen=codegen)
     s = summary(g, ref, w.atol)
     same = same_counts(g, ref)
     assert same.mean() >= 0.999, s
@@ -51,15 +51,34 @@ def test_vdp_rkc_fp64():
     check_fp64(w, method="rkc")
 
 
+CODEGENS = [B.ODE_CODEGEN_ON, B.ODE_CODEGEN_OFF]
+
+
+@pytest.mark.parametrize("codegen", CODEGENS)
 @pytest.mark.parametrize("mapping", [B.ODE_MAP_QUEUE, B.ODE_MAP_THREAD])
-def test_massaction_rkc_fp64(mapping):
-    check_fp64(W.massaction(1500, seed=1), mapping)
+def test_massaction_rkc_fp64(mapping, codegen):
+    # generated (straight-line network) and generic kernels both reproduce the oracle
+    check_fp64(W.massaction(1500, seed=1), mapping, codegen=codegen)
 
 
-def test_massaction_rkck_fp64():
+@pytest.mark.parametrize("codegen", CODEGENS)
+def test_massaction_rkck_fp64(codegen):
     # RKCK on the stiff network: many steps, so a shorter interval
     w = W.massaction(300, seed=2, tend=2e-6)
-    check_fp64(w, method="rkck")
+    check_fp64(w, method="rkck", codegen=codegen)
+
+
+def test_massaction_other_network_sizes():
+    # a 20-species, 40-reaction network exercises the larger generic kernels
+    net = W.make_network(5, n_species=20, n_reactions=40)
+    base = W.massaction(200, seed=6)
+    rng = np.random.default_rng(6)
+    c = rng.uniform(0.01, 1.0, (20, 200))
+    c /= c.sum(axis=0)
+    w = W.Workload("massaction20", W.RHS_MASSACTION, W.METHOD_RKC, 200, 20, c, base.params, 0.0, 2e-5,
+                   1e-6, 1e-12, network=net)
+    for cg in CODEGENS:
+        check_fp64(w, codegen=cg)
 
 
 @pytest.mark.parametrize("n", [32, 1, 5, 33, 100, 128])
@@ -150,15 +169,28 @@ MIXED_CASES = {
 }
 
 
+@pytest.mark.parametrize("method", ["rkc", "rkck"])
+def test_mixed_generated_matches_generic(method):
+    # the generated network code and the generic kernels compute the same
+    # FP32 arithmetic up to evaluation order: both stay close to the oracle
+    w = W.massaction(1024, seed=24, tend=1e-4 if method == "rkc" else 2e-6)
+    ref = O.integrate(O.model_for(w), 0 if method == "rkck" else 1, w.y0, w.params, w.t0, w.tend, w.rtol, w.atol)
+    for cg in CODEGENS:
+        g = run_gpu(w, precision=B.ODE_PREC_MIXED, method=method, codegen=cg)
+        assert (g["status"] & 0xFF == 0).all()
+        assert np.quantile(rel_err(g["y"], ref.y, w.atol), 0.99) < 1e-3
+
+
+@pytest.mark.parametrize("prec", [B.ODE_PREC_MIXED, B.ODE_PREC_MIXED_CNORM])
 @pytest.mark.parametrize("name", sorted(MIXED_CASES))
-def test_mixed_form_error_against_fp64_oracle(name, record_property):
+def test_mixed_form_error_against_fp64_oracle(name, prec, record_property):
     make, bound = MIXED_CASES[name]
     w = make()
     ref = O.integrate_workload(w)
-    g = run_gpu(w, precision=B.ODE_PREC_MIXED)
+    g = run_gpu(w, precision=prec)
     assert (g["status"] & 0xFF == 0).all()
     e = rel_err(g["y"], ref.y, w.atol)
     record_property("max_err", float(e.max()))
     record_property("p999_err", float(np.quantile(e, 0.999)))
-    print(name, "mixed error vs oracle: max", e.max(), "p99.9", np.quantile(e, 0.999), "median", np.median(e))
+    print(name, prec, "mixed error vs oracle: max", e.max(), "p99.9", np.quantile(e, 0.999), "median", np.median(e))
     assert np.quantile(e, 0.999) < bound
