@@ -180,6 +180,43 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
                   double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
                   const ode_stats* stats, void* stream);
 
+/* RKC integration for callers that cannot allocate GPU memory.
+ *
+ * Some callers may not call cudaMalloc at all: code running inside another
+ * framework's memory pool or a fixed memory budget, hosts that forbid
+ * growing the device footprint after start-up, or code that must not fail
+ * on an allocation halfway through a job.  rkc_integrate allocates a
+ * workspace on first use (and grows a staging buffer for host arrays);
+ * this entry point allocates nothing.  Its scratch -- the work-queue
+ * cursor, an RKC coefficient table for stage counts up to 32 and the
+ * staging area for the caller's arrays -- lives in one statically sized
+ * device array of ODE_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which
+ * loads this library holds until the process exits.  The paper has no
+ * counterpart; it is a packaging of the same integrator.
+ *
+ * Same arguments and results as rkc_integrate, except: y0, params, y_out
+ * and the stats arrays are HOST pointers (pinned memory gives asynchronous
+ * copies; y_out may alias y0); opts->io and opts->codegen are ignored (the
+ * built-in kernels are used, never run-time generated ones, since loading
+ * generated code allocates).  A batch whose staged arrays need more than the
+ * scratch offers -- nsys * 8 * (neq + n_params) bytes plus 4 * nsys per
+ * requested counter array, each rounded up to 256 bytes, against 16 MiB
+ * minus the cursor and table -- is rejected with ODE_ERR_ARG before any GPU
+ * work; split such a batch into several calls.
+ *
+ * The first call on each device does the set-up (looks up the array's
+ * device address with the device current and builds the coefficient table
+ * into it, then synchronises), so make that first call before any stream
+ * capture.  Every call shares the array and finds the previous call's
+ * contents there: the cursor is cleared on every call, and every staged or
+ * output element is rewritten.  Calls that overlapped on the GPU would race
+ * on the array; this entry point serialises its own calls with a process-wide
+ * lock and synchronises the stream before returning. */
+#define ODE_NOALLOC_SCRATCH_BYTES 16777216 /* 16 MiB */
+int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
+                          double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
+                          const ode_stats* stats, void* stream);
+
 /* Description of the last error on this thread ("" if none). */
 const char* ode_last_error(void);
 

@@ -27,7 +27,8 @@ ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
 ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
 
 EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_integrate", "rkc_integrate",
-            "ode_last_error", "ode_version", "bode_fma_peak"]
+            "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak"]
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class RhsDesc(C.Structure):
@@ -82,7 +83,7 @@ def load(build_if_missing: bool = True):
     L.ode_rhs_register.argtypes = [C.POINTER(RhsDesc), C.POINTER(C.c_int32)]
     L.ode_rhs_release.argtypes = [C.c_int32]
     L.ode_rhs_prepare.argtypes = [C.c_int32, C.c_int32, C.c_int32]
-    for name in ("rkck_integrate", "rkc_integrate"):
+    for name in ("rkck_integrate", "rkc_integrate", "rkc_integrate_noalloc"):
         fn = getattr(L, name)
         fn.argtypes = [C.c_int32, C.c_int64, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
                        C.POINTER(Opts), P, C.POINTER(Stats), P]
@@ -183,6 +184,28 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     fn = load().rkck_integrate if method == "rkck" else load().rkc_integrate
     rc = fn(handle, nsys, _ptr(y0), _ptr(params), float(t0), float(tend), float(rtol), float(atol),
             C.byref(o), _ptr(y_out), C.byref(s), C.c_void_p(stream) if stream else None)
+    _check(rc)
+    return y_out
+
+
+def integrate_noalloc(handle: int, y0: np.ndarray, params: np.ndarray, t0: float, tend: float, rtol: float,
+                      atol: float, y_out: np.ndarray | None = None, counters: Counters | None = None,
+                      precision: int = ODE_PREC_FP64, mapping: int = ODE_MAP_AUTO, block_size: int = 0,
+                      max_attempts: int = 0, stream=None) -> np.ndarray:
+    """rkc_integrate_noalloc on host (numpy) arrays: RKC through a static
+    device scratch, with no GPU memory allocated by the library."""
+    nsys = int(y0.shape[1])
+    if y_out is None:
+        y_out = np.empty_like(y0)
+    o = Opts()
+    o.precision, o.mapping, o.block_size, o.max_attempts = precision, mapping, block_size, max_attempts
+    s = Stats()
+    if counters is not None:
+        s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
+            _ptr(getattr(counters, k)) for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")]
+    rc = load().rkc_integrate_noalloc(handle, nsys, _ptr(y0), _ptr(params), float(t0), float(tend), float(rtol),
+                                      float(atol), C.byref(o), _ptr(y_out), C.byref(s),
+                                      C.c_void_p(stream) if stream else None)
     _check(rc)
     return y_out
 

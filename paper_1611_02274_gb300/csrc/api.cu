@@ -282,6 +282,27 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
 
 }  // namespace
 
+namespace bode {
+
+// Registry and error-string access for the allocation-free entry point
+// (noalloc.cu).
+bool registry_lookup(int32_t handle, RhsEntry* out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(handle);
+    if (it == g_reg.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+int set_last_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+
+void clear_last_error() { g_err.clear(); }
+
+}  // namespace bode
+
 extern "C" {
 
 int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle) {
