@@ -59,6 +59,7 @@ extern "C" {
 #define ODE_ST_MAX_ATTEMPTS 2     /* attempt cap reached before tend */
 #define ODE_ST_NONFINITE 3        /* NaN error estimate or non-finite state */
 #define ODE_ST_SPECRAD_NOCONV 256 /* warning bit: power method did not converge */
+#define ODE_ST_PROPOSED 512       /* information bit: RKC started from a proposed h0 / sigma0 */
 
 /* right-hand-side families */
 #define ODE_RHS_VDP 1        /* van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1; params [mu]; neq 2 */
@@ -75,10 +76,12 @@ extern "C" {
 #define ODE_PREC_MIXED 1     /* FP32 RHS and stage arithmetic with Kahan-compensated FP32 state;
                                 FP64 time, step size, error-norm accumulation and Chebyshev
                                 coefficients */
-#define ODE_PREC_MIXED_CNORM 2 /* as ODE_PREC_MIXED, but the RKC error norm is accumulated in FP32
-                                with compensated (two-sum) summation instead of FP64: the same
-                                accuracy as one rounding, without FP64 instructions (the FP64
-                                pipe of this GPU runs at 1/64 of the FP32 rate) */
+#define ODE_PREC_MIXED_LEAN 2 /* FP32 RHS, stages, step size, spectral radius and error norms
+                                (norms with compensated two-sum accumulation), Kahan-compensated
+                                FP32 state; FP64 kept where rounding accumulates -- the time t --
+                                and for the Chebyshev coefficients.  The FP64 pipe of this GPU
+                                runs at 1/64 of the FP32 rate, so every FP64 instruction of the
+                                step-size bookkeeping costs as much as ~64 FP32 ones */
 
 /* how systems map onto the GPU */
 #define ODE_MAP_AUTO 0       /* autotuned choice (cached per rhs / method / precision) */
@@ -128,6 +131,18 @@ typedef struct {
     int32_t sync;          /* nonzero: synchronise the stream before returning */
     int32_t codegen;       /* ODE_CODEGEN_* (default AUTO) */
     int32_t reserved[9];   /* must be zero */
+    /* RKC, mixed precisions: optional per-system proposals [nsys] (device
+     * arrays, NaN = none) of the initial step and the spectral-radius bound,
+     * e.g. from ode_mlp_propose.  A system with a finite positive pair skips
+     * the initial power method and Euler trial step and starts from them;
+     * the error test still judges every step and the first rejection hands
+     * the system back to the power method (Appendix). */
+    const float* h0;
+    const float* sigma0;
+    /* RKC, ODE_PREC_FP64: optional training log [nsys][neq + 3] (device):
+     * at each system's first accepted step, log max(|y_k|, 1e-30) for every
+     * component, the parameter, log h and log sigma of that step. */
+    float* log_xy;
 } ode_opts;
 
 /* Per-system outputs, each an array of nsys int32 (device pointers unless
@@ -216,6 +231,54 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
 int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
                           double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
                           const ode_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Learned initial step / spectral-radius proposal.  Not in the paper: the
+ * paper starts every RKC system with a power-method estimate (Appendix) and
+ * an Euler trial step (Section 2.2); this network proposes both from the
+ * initial state.  MLP n_in -> 64 -> 64 -> 2 with SiLU, FP32 master weights
+ * used as BF16 with FP32 accumulation (CUDA cores), inputs log max(|y_k|,
+ * 1e-30) for each component plus the parameter (normalised by statistics
+ * of the training set), outputs log h0 and log sigma.  Training minimises
+ * squared error on log h0 plus a pinball loss (quantile 0.9) on log sigma,
+ * so sigma leans to over-estimates, with Adam.  Device arrays throughout,
+ * rows contiguous (X [n][n_in], Y [n][2]); returns ODE_OK or ODE_ERR_*.
+ * The parameter vector layout: W1 [64][n_in], b1 [64], W2 [64][64],
+ * b2 [64], W3 [2][64], b3 [2]; the normalisation block: x_mean, x_scale,
+ * x_min, x_max [ODE_MLP_MAX_IN each], y_mean, y_scale [2 each]. */
+#define ODE_MLP_HIDDEN 64
+#define ODE_MLP_MAX_IN 33
+#define ODE_MLP_NORM_FLOATS 136
+
+typedef struct {
+    int32_t epochs;   /* passes over the data */
+    int32_t batch;    /* rows per Adam step */
+    float lr;         /* Adam learning rate */
+    int32_t pad;      /* must be zero */
+    uint64_t seed;    /* shuffling seed */
+} ode_train_opts;
+
+int ode_mlp_create(int32_t n_in, uint64_t seed, int32_t* mlp_handle);   /* Glorot-uniform init */
+int ode_mlp_release(int32_t mlp_handle);
+int ode_mlp_num_params(int32_t n_in);                                     /* -1 if n_in is out of range */
+/* mean / standard deviation / range of every input and target column */
+int ode_mlp_fit_normalization(int32_t mlp_handle, const float* X, const float* Y, int64_t n, void* stream);
+/* epochs of shuffled minibatch Adam; loss_history (host, [epochs]) gets each epoch's mean loss */
+int ode_mlp_train(int32_t mlp_handle, const float* X, const float* Y, int64_t n, const ode_train_opts* opts,
+                  float* loss_history, void* stream);
+/* gradient of the mean loss over the n rows w.r.t. the parameters (device grad_out [num_params]);
+ * *loss_out (host) = the mean loss; synchronous */
+int ode_mlp_gradient(int32_t mlp_handle, const float* X, const float* Y, int64_t n, float* grad_out,
+                     float* loss_out, void* stream);
+/* outputs (log h0, log sigma) for raw feature rows: out [n][2] */
+int ode_mlp_apply(int32_t mlp_handle, const float* X, int64_t n, float* out, void* stream);
+/* proposals for an SoA batch (y0 [neq][nsys], params [1][nsys], FP64): h0 and sigma0 [nsys], NaN where
+ * an input lies outside the training range widened by `margin` of its width, or an output is not finite */
+int ode_mlp_propose(int32_t mlp_handle, int64_t nsys, int32_t neq, const double* y0, const double* params,
+                    float margin, float* h0, float* sigma0, void* stream);
+/* host copies of the FP32 parameters [num_params] and the normalisation block (either may be NULL) */
+int ode_mlp_get_params(int32_t mlp_handle, float* params, float* norm);
+int ode_mlp_set_params(int32_t mlp_handle, const float* params, const float* norm);
 
 /* Description of the last error on this thread ("" if none). */
 const char* ode_last_error(void);

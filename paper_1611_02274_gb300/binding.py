@@ -21,7 +21,7 @@ ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM = 
 ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 3
 ODE_ST_SPECRAD_NOCONV = 256
 ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION = 1, 2, 3, 4
-ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_CNORM = 0, 1, 2
+ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN = 0, 1, 2
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
 ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
 ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2

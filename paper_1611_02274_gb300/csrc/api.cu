@@ -154,7 +154,7 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     for (int k = 0; k < 9; ++k)
         if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
     if (opts.codegen < ODE_CODEGEN_AUTO || opts.codegen > ODE_CODEGEN_ON) return fail(ODE_ERR_ARG, "unknown codegen mode %d", opts.codegen);
-    if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_CNORM)
+    if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_LEAN)
         return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
     if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
     if (opts.io != ODE_IO_DEVICE && opts.io != ODE_IO_HOST) return fail(ODE_ERR_ARG, "unknown io mode %d", opts.io);
@@ -231,6 +231,11 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     a.n_specrad = d_stats.n_specrad_iter;
     a.status = d_stats.status;
     a.cursor = ws->cursors + ws->next_cursor;
+    a.h0 = opts.h0;
+    a.sigma0 = opts.sigma0;
+    a.log_xy = opts.log_xy;
+    if ((opts.h0 == nullptr) != (opts.sigma0 == nullptr)) return fail(ODE_ERR_ARG, "h0 and sigma0 go together");
+    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy)) return fail(ODE_ERR_ARG, "proposals and logs need device io");
     a.rkc_tab64 = ws->tab64;
     a.rkc_tab32 = ws->tab32;
     a.rkc_tab_max = kRkcTabMax;
@@ -328,7 +333,7 @@ int ode_rhs_release(int32_t rhs_handle) {
 int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision) {
     g_err.clear();
     if (method != 0 && method != 1) return fail(ODE_ERR_ARG, "method must be 0 (RKCK) or 1 (RKC)");
-    if (precision < ODE_PREC_FP64 || precision > ODE_PREC_MIXED_CNORM) return fail(ODE_ERR_ARG, "unknown precision %d", precision);
+    if (precision < ODE_PREC_FP64 || precision > ODE_PREC_MIXED_LEAN) return fail(ODE_ERR_ARG, "unknown precision %d", precision);
     RhsEntry r;
     {
         std::lock_guard<std::mutex> lk(g_mu);

@@ -37,6 +37,16 @@ struct MassActionNet {
     double Ea[kMaxReactions];
 };
 
+// Compile-time type choice (the run-time compiler has no <type_traits>).
+template <bool B, class T, class F>
+struct Pick {
+    using type = T;
+};
+template <class T, class F>
+struct Pick<false, T, F> {
+    using type = F;
+};
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 
@@ -66,6 +76,10 @@ struct BatchArgs {
     const double* rkc_tab64;
     const float4* rkc_tab32;
     int32_t rkc_tab_max;
+    // optional proposals (mixed RKC) and training log (plain RKC)
+    const float* h0;
+    const float* sigma0;
+    float* log_xy;
 };
 
 __host__ __device__ inline int rkc_tab_index(int m, int j) { return m * (m - 1) / 2 - 1 + (j - 1); }

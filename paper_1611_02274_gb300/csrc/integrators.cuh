@@ -18,9 +18,10 @@
 //           multiply-add contraction, norms are summed in component order),
 //           so results reproduce a sequential FP64 implementation bit for bit;
 //   *Mixed  FP32 right-hand sides and stage arithmetic on an FP32 state with
-//           a Kahan compensation term; time, step size and spectral radius in
-//           FP64, the RKC weighted error norm accumulated in FP64, the RKC
-//           Chebyshev coefficients computed in FP64.
+//           a Kahan compensation term and the RKC Chebyshev coefficients
+//           computed in FP64; with SPEC also time, step size, spectral radius
+//           and the RKC error-norm accumulation in FP64, without it only the
+//           time t (the lean split: FP64 only where rounding accumulates).
 #pragma once
 #include <cmath>
 
@@ -122,7 +123,7 @@ struct RkckF64 {
         }
     }
 
-    __device__ bool consume(const BatchArgs&, const TM& tm, const double* f) {
+    __device__ bool consume(const BatchArgs&, const TM& tm, const double*, const double* f) {
         switch (stage) {
         case 1:
 #pragma unroll
@@ -237,10 +238,12 @@ struct RkcF64 {
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
     int32_t phase, m, j, sr_iter;
     bool have_sigma, rejected;
+    int64_t idx;  // system index (training log)
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
         sys.load(ctx, tm, a.params[i], a.neq);
         n = a.neq;
+        idx = i;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
@@ -301,7 +304,7 @@ struct RkcF64 {
         }
     }
 
-    __device__ bool consume(const BatchArgs& a, const TM& tm, const double* f) {
+    __device__ bool consume(const BatchArgs& a, const TM& tm, const double*, const double* f) {
         switch (phase) {
         case PH_F0:
 #pragma unroll
@@ -494,6 +497,7 @@ struct RkcF64 {
             loop_top(a, tm);
             return;
         }
+        if (a.log_xy != nullptr && n_acc == 0) write_log(a, tm);
         n_acc += 1;
         rejected = false;
         t = t + h;
@@ -526,6 +530,22 @@ struct RkcF64 {
         loop_top(a, tm);
     }
 
+    // training record of the first accepted step: features of the initial
+    // state, the parameter, log h and log sigma
+    __device__ void write_log(const BatchArgs& a, const TM& tm) const {
+        float* rec = a.log_xy + idx * (int64_t)(n + 3);
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            if (c >= 0) rec[c] = (float)log(fmax(fabs(yn[s]), 1e-30));
+        }
+        if (tm.lane == 0) {
+            rec[n] = (float)a.params[idx];
+            rec[n + 1] = (float)log(h);
+            rec[n + 2] = (float)log(sigma);
+        }
+    }
+
     __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
 #pragma unroll
         for (int s = 0; s < P; ++s) {
@@ -544,15 +564,36 @@ struct RkcF64 {
 
 // ============================================================== RKCK mixed
 
-template <class Model>
+// x^p for the step-size factors of the mixed forms (x >= 0): two special
+// function unit operations, relative error ~1e-6 -- ample for a safety factor.
+__device__ __forceinline__ float fpow(float x, float p) { return exp2f(p * __log2f(x)); }
+
+// Compensated FP32 accumulation (Knuth's two-sum): the rounding error of each
+// addition is collected in c, so s + c carries the sum to about one rounding.
+struct SumF2 {
+    float s = 0.0f, c = 0.0f;
+    __device__ void add(float x) {
+        const float t = s + x;
+        const float bb = t - s;
+        c += (s - (t - bb)) + (x - bb);
+        s = t;
+    }
+};
+
+// SPEC: the split as specified (ODE_PREC_MIXED): time and step size in FP64.
+// Otherwise (ODE_PREC_MIXED_LEAN) only the time t is FP64; the step size is
+// FP32 and a step that reaches the end of the interval lands on tend exactly.
+template <class Model, bool SPEC = true>
 struct RkckMixed {
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
     using TM = Team<W>;
+    using HT = typename Pick<SPEC, double, float>::type;
     typename Model::template Sys<float> sys;
     float yh[P], yl[P], k1[P], k2[P], k3[P], k4[P], k5[P];
-    double t, tend, h, hmax;
-    float hf, deltaf, inv_rtolf;
+    double t, tend;
+    HT h, hmax;
+    float hf, remf, tabsf, deltaf, inv_rtolf;
     int32_t n_acc, n_rej, status, max_att, stage;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
@@ -567,8 +608,10 @@ struct RkckMixed {
         }
         t = a.t0;
         tend = a.tend;
-        hmax = fabs(tend - t);
-        h = 0.5 * fabs(tend - t);
+        hmax = (HT)fabs(tend - t);
+        h = (HT)(0.5 * fabs(tend - t));
+        remf = (float)(tend - t);
+        tabsf = fabsf((float)t);
         deltaf = (float)((a.atol > 0.0) ? a.atol / a.rtol : kTiny);
         inv_rtolf = (float)(1.0 / a.rtol);
         n_acc = n_rej = status = 0;
@@ -579,12 +622,19 @@ struct RkckMixed {
 
     __device__ void loop_top() {
         stage = 0;
-        if (!(t < tend)) return;
+        if constexpr (SPEC) {
+            if (!(t < tend)) return;
+        } else {
+            if (!(remf > 0.0f)) return;
+        }
         if (n_acc + n_rej >= max_att) {
             status = ODE_ST_MAX_ATTEMPTS;
             return;
         }
-        h = fmin(tend - t, h);
+        if constexpr (SPEC)
+            h = fmin(tend - t, h);
+        else
+            h = fminf(remf, h);
         hf = (float)h;
         stage = 1;
     }
@@ -608,7 +658,7 @@ struct RkckMixed {
         for (int s = 0; s < P; ++s) x[s] = yh[s] + (b1 * k1[s] + b2 * k2[s] + b3 * k3[s] + b4 * k4[s] + b5 * k5[s]);
     }
 
-    __device__ bool consume(const BatchArgs&, const TM& tm, const float* f) {
+    __device__ bool consume(const BatchArgs&, const TM& tm, const float*, const float* f) {
         if (stage == 6) {
             finish(tm, f);
             return done();
@@ -638,7 +688,7 @@ struct RkckMixed {
                              (float)ck::DC5 * k5[s] + (float)ck::DC6 * k6;
             if (sys.comp(tm, s) >= 0) {
                 if (isnan(ye) || isnan(incr[s])) nan_flag = true;
-                err = fmaxf(err, fabsf(ye) / (fabsf(yh[s]) + fabsf(k1[s]) + deltaf));
+                err = fmaxf(err, __fdividef(fabsf(ye), fabsf(yh[s]) + fabsf(k1[s]) + deltaf));
             }
         }
         err = tm.max(err) * inv_rtolf;
@@ -646,13 +696,18 @@ struct RkckMixed {
         if (err > 1.0f || isnan(err) || nan_flag) {
             n_rej += 1;
             if (isnan(err) || nan_flag) {
-                h = h * kP1;
+                h = h * (HT)kP1;
 #pragma unroll
                 for (int s = 0; s < P; ++s) k1[s] = k2[s] = k3[s] = k4[s] = k5[s] = 0.0f;
             } else {
-                h = h * (double)fmaxf((float)kSafety * powf(err, (float)kPshrnk), (float)kP1);
+                h = h * (HT)fmaxf((float)kSafety * fpow(err, (float)kPshrnk), (float)kP1);
             }
-            if (h < 1.0e-20 || t + h == t) {
+            bool underflow;
+            if constexpr (SPEC)
+                underflow = h < 1.0e-20 || t + h == t;
+            else
+                underflow = h < 1.0e-20f || h <= tabsf * 2.2e-16f;
+            if (underflow) {
                 status = ODE_ST_H_UNDERFLOW;
                 stage = 0;
                 return;
@@ -661,9 +716,21 @@ struct RkckMixed {
             return;
         }
         n_acc += 1;
-        t = t + h;
-        const float fac = (err > (float)kErrcon) ? (float)kSafety * powf(err, (float)kPgrow) : 5.0f;
-        h = fmax(1.0e-20, fmin(hmax, h * (double)fac));
+        if constexpr (SPEC) {
+            t = t + h;
+        } else if (h >= remf * 0.999999f) {
+            t = tend;  // the step covered what was left
+            remf = 0.0f;
+        } else {
+            t = t + (double)h;
+            remf = (float)(tend - t);
+            tabsf = fabsf((float)t);
+        }
+        const float fac = (err > (float)kErrcon) ? (float)kSafety * fpow(err, (float)kPgrow) : 5.0f;
+        if constexpr (SPEC)
+            h = fmax(1.0e-20, fmin(hmax, h * (double)fac));
+        else
+            h = fmaxf(1.0e-20f, fminf(hmax, h * fac));
         bool bad = false;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
@@ -696,29 +763,21 @@ struct RkckMixed {
 
 // =============================================================== RKC mixed
 
-// Compensated FP32 accumulation (Knuth's two-sum): the rounding error of each
-// addition is collected in c, so s + c carries the sum to about one rounding.
-struct SumF2 {
-    float s = 0.0f, c = 0.0f;
-    __device__ void add(float x) {
-        const float t = s + x;
-        const float bb = t - s;
-        c += (s - (t - bb)) + (x - bb);
-        s = t;
-    }
-};
-
-// NORM64: accumulate the weighted error norm in FP64 (ODE_PREC_MIXED); else
-// in compensated FP32 (ODE_PREC_MIXED_CNORM).
-template <class Model, bool NORM64 = true>
+// SPEC (ODE_PREC_MIXED): time, step size and spectral radius in FP64 and the
+// weighted error norm accumulated in FP64, as specified.  Otherwise
+// (ODE_PREC_MIXED_LEAN): only the time t in FP64; step size and spectral
+// radius in FP32, norms with compensated FP32 accumulation.
+template <class Model, bool SPEC = true>
 struct RkcMixed {
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
     using TM = Team<W>;
+    using HT = typename Pick<SPEC, double, float>::type;
     typename Model::template Sys<float> sys;
     float yh[P], yl[P], Fn[P], v[P], d1[P], d2[P];  // d_j = w_j - y_n (d_0 = 0)
-    double t, tend, hmax, hmin, h, h_old, sigma, inv_n;
-    float rtolf, atolf, err_old, hf, dynrm, sig, inv_nf;
+    double t, tend;
+    HT hmax, hmin, h, h_old, sigma;
+    float rtolf, atolf, c3_old, hf, remf, dynrm, sig, inv_nf;  // c3_old = err_old^(1/3)
     float4 cur;  // (mu_j, nu_j, mu~_j, gamma~_j) of the current stage
     CoefSource cs;
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
@@ -728,8 +787,7 @@ struct RkcMixed {
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
         sys.load(ctx, tm, a.params[i], a.neq);
         n = a.neq;
-        inv_n = 1.0 / (double)n;
-        inv_nf = (float)inv_n;
+        inv_nf = 1.0f / (float)n;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
@@ -739,20 +797,34 @@ struct RkcMixed {
         }
         t = a.t0;
         tend = a.tend;
+        remf = (float)(tend - t);
         rtolf = (float)a.rtol;
         atolf = (float)a.atol;
         mmax = (int)round(sqrt(a.rtol / (10.0 * kUround)));
         if (mmax < 2) mmax = 2;
-        hmax = fabs(tend - t);
-        hmin = 10.0 * kUround * fmax(fabs(t), hmax);
+        hmax = (HT)fabs(tend - t);
+        hmin = (HT)(10.0 * kUround * fmax(fabs(t), fabs(tend - t)));
         n_acc = n_rej = n_sr = status = 0;
         n_rhs = 1;
         max_att = a.max_attempts;
-        h = h_old = sigma = 0.0;
-        err_old = 0.0f;
+        h = h_old = sigma = (HT)0;
+        c3_old = 0.0f;
         num_step = 0;
         sr_step = -1;
         have_sigma = rejected = false;
+        if (a.h0 != nullptr) {
+            // a proposed start replaces the initial power method and Euler
+            // trial; the first rejection returns the system to the power method
+            const float hp = a.h0[i], sp = a.sigma0[i];
+            if (isfinite(hp) && isfinite(sp) && hp > 0.0f && sp > 0.0f) {
+                h = (HT)hp < hmax ? (HT)hp : hmax;
+                h = h > hmin ? h : hmin;
+                sigma = (HT)sp;
+                have_sigma = true;
+                sr_step = 0;
+                status |= ODE_ST_PROPOSED;
+            }
+        }
         phase = PH_F0;
     }
     __device__ bool done() const { return phase == PH_DONE; }
@@ -786,7 +858,7 @@ struct RkcMixed {
         }
     }
 
-    __device__ bool consume(const BatchArgs& a, const TM& tm, const float* f) {
+    __device__ bool consume(const BatchArgs& a, const TM& tm, const float* x, const float* f) {
         switch (phase) {
         case PH_F0:
 #pragma unroll
@@ -799,22 +871,33 @@ struct RkcMixed {
         case PH_SR: sr_consume(a, tm, f); break;
         case PH_TRIAL: trial_consume(a, tm, f); break;
         case PH_STAGE: stage_consume(f); break;
-        default: final_consume(a, tm, f);
+        default: final_consume(a, tm, x, f);
         }
         return done();
     }
 
     __device__ void loop_top(const BatchArgs& a, const TM& tm) {
-        if (!(t < tend)) {
-            phase = PH_DONE;
-            return;
+        if constexpr (SPEC) {
+            if (!(t < tend)) {
+                phase = PH_DONE;
+                return;
+            }
+        } else {
+            if (!(remf > 0.0f)) {
+                phase = PH_DONE;
+                return;
+            }
         }
         if (n_acc + n_rej >= max_att) {
             status |= ODE_ST_MAX_ATTEMPTS;
             phase = PH_DONE;
             return;
         }
-        if (1.1 * h >= fabs(tend - t)) h = fabs(tend - t);
+        if constexpr (SPEC) {
+            if (1.1 * h >= fabs(tend - t)) h = fabs(tend - t);
+        } else {
+            if (1.1f * h >= remf) h = remf;
+        }
         if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
             sr_begin(tm);
             return;
@@ -859,7 +942,7 @@ struct RkcMixed {
         const float d = sqrtf(tm.sum(acc));
         const float sig_prev = sig;
         sig = d / dynrm;
-        if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, (float)(1.0 / hmax)) * 0.01f) {
+        if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
 #pragma unroll
             for (int s = 0; s < P; ++s) v[s] = v[s] - yh[s];
             sr_end(a);
@@ -884,17 +967,17 @@ struct RkcMixed {
     }
 
     __device__ void sr_end(const BatchArgs& a) {
-        sigma = 1.2 * (double)sig;
+        sigma = (HT)1.2 * (HT)sig;
         have_sigma = true;
         sr_step = num_step;
         after_sr(a);
     }
 
     __device__ void after_sr(const BatchArgs& a) {
-        if (h < kUround) {
+        if (h < (HT)kUround) {
             h = hmax;
-            if (sigma * h > 1.0) h = 1.0 / sigma;
-            h = fmax(h, hmin);
+            if (sigma * h > (HT)1) h = (HT)1 / sigma;
+            h = h > hmin ? h : hmin;
             hf = (float)h;
             phase = PH_TRIAL;
             return;
@@ -902,41 +985,66 @@ struct RkcMixed {
         stage_begin(a);
     }
 
-    __device__ void trial_consume(const BatchArgs& a, const TM& tm, const float* f) {
-        n_rhs += 1;
-        double ssq;
-        if constexpr (NORM64) {
+    // weighted sum of squares of e, FP64 (SPEC) or compensated FP32
+    template <class E>
+    __device__ double weighted_ssq(const TM& tm, E e_of) const {
+        if constexpr (SPEC) {
             double acc = 0.0;
 #pragma unroll
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
-                    const float e = (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
+                    const float e = e_of(s);
                     acc = fma((double)e, (double)e, acc);
                 }
-            ssq = tm.sum(acc);
+            return tm.sum(acc);
         } else {
             SumF2 acc;
 #pragma unroll
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
-                    const float e = (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
+                    const float e = e_of(s);
                     acc.add(e * e);
                 }
-            ssq = (double)(tm.sum(acc.s) + tm.sum(acc.c));
+            return (double)(tm.sum(acc.s) + tm.sum(acc.c));
         }
-        const double est = h * sqrt(ssq * inv_n);
-        if (kP1 * h < hmax * sqrt(est))
-            h = fmax(kP1 * h / sqrt(est), hmin);
-        else
-            h = hmax;
+    }
+
+    __device__ void trial_consume(const BatchArgs& a, const TM& tm, const float* f) {
+        n_rhs += 1;
+        if constexpr (SPEC) {
+            const double ssq = weighted_ssq(tm, [&](int s) {
+                return (f[s] - Fn[s]) / (atolf + rtolf * fabsf(yh[s]));
+            });
+            const double est = h * sqrt(ssq / (double)n);
+            if (kP1 * h < hmax * sqrt(est))
+                h = fmax(kP1 * h / sqrt(est), hmin);
+            else
+                h = hmax;
+        } else {
+            SumF2 acc;
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+                if (sys.comp(tm, s) >= 0) {
+                    const float e = __fdividef(f[s] - Fn[s], atolf + rtolf * fabsf(yh[s]));
+                    acc.add(e * e);
+                }
+            const float est = h * sqrtf((tm.sum(acc.s) + tm.sum(acc.c)) * inv_nf);
+            if ((float)kP1 * h < hmax * sqrtf(est))
+                h = fmaxf((float)kP1 * h / sqrtf(est), hmin);
+            else
+                h = hmax;
+        }
         stage_begin(a);
     }
 
     __device__ void stage_begin(const BatchArgs& a) {
-        m = 1 + (int)sqrtf((float)(1.54 * h * sigma) + 1.0f);
+        if constexpr (SPEC)
+            m = 1 + (int)sqrtf((float)(1.54 * h * sigma) + 1.0f);
+        else
+            m = 1 + (int)sqrtf(1.54f * h * sigma + 1.0f);
         if (m > mmax) {
             m = mmax;
-            h = (double)(m * m - 1) / (1.54 * sigma);
+            h = (HT)(m * m - 1) / ((HT)1.54 * sigma);
         }
         hf = (float)h;
         cs.start(m, a);
@@ -967,21 +1075,16 @@ struct RkcMixed {
             phase = PH_FINAL;
     }
 
-    __device__ void final_consume(const BatchArgs& a, const TM& tm, const float* f) {
+    // x = w_m (the point F_{n+1} was evaluated at), f = F_{n+1}
+    __device__ void final_consume(const BatchArgs& a, const TM& tm, const float* x, const float* f) {
         n_rhs += m;
         const float h04 = 0.4f * hf;
         bool reject, bad_err;
         float err;
-        if constexpr (NORM64) {
-            double acc = 0.0;
-#pragma unroll
-            for (int s = 0; s < P; ++s)
-                if (sys.comp(tm, s) >= 0) {
-                    const float wm = yh[s] + (yl[s] + d1[s]);
-                    const float e = (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(wm), fabsf(yh[s])));
-                    acc = fma((double)e, (double)e, acc);
-                }
-            const double ms = tm.sum(acc) * inv_n;  // err^2
+        if constexpr (SPEC) {
+            const double ms = weighted_ssq(tm, [&](int s) {
+                return (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(x[s]), fabsf(yh[s])));
+            }) / (double)n;  // err^2
             bad_err = isnan(ms);
             reject = ms > 1.0;
             err = sqrtf((float)ms);
@@ -990,8 +1093,8 @@ struct RkcMixed {
 #pragma unroll
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
-                    const float wm = yh[s] + (yl[s] + d1[s]);
-                    const float e = (-0.8f * d1[s] + h04 * (Fn[s] + f[s])) / (atolf + rtolf * fmaxf(fabsf(wm), fabsf(yh[s])));
+                    const float e = __fdividef(-0.8f * d1[s] + h04 * (Fn[s] + f[s]),
+                                               atolf + rtolf * fmaxf(fabsf(x[s]), fabsf(yh[s])));
                     acc.add(e * e);
                 }
             const float ms = (tm.sum(acc.s) + tm.sum(acc.c)) * inv_nf;  // err^2
@@ -1005,10 +1108,10 @@ struct RkcMixed {
             phase = PH_DONE;
             return;
         }
-        const float c3 = cbrtf(err);
+        const float c3 = fpow(err, 1.0f / 3.0f);
         if (reject) {
             n_rej += 1;
-            h = h * (double)(0.8f / c3);
+            h = h * (HT)(0.8f / c3);
             rejected = true;
             if (h < hmin) {
                 status |= ODE_ST_H_UNDERFLOW;
@@ -1022,16 +1125,24 @@ struct RkcMixed {
         rejected = false;
         num_step += 1;
         float fac = 10.0f;
-        if (h_old < kUround) {
+        if (h_old < (HT)kUround) {
             if (0.8f < fac * c3) fac = 0.8f / c3;
         } else {
-            const float temp1 = 0.8f * hf * cbrtf(err_old);
+            const float temp1 = 0.8f * hf * c3_old;
             const float temp2 = (float)h_old * (c3 * c3);
             if (temp1 < fac * temp2) fac = temp1 / temp2;
         }
-        err_old = err;
+        c3_old = c3;
         h_old = h;
-        t = t + h;
+        if constexpr (SPEC) {
+            t = t + h;
+        } else if (h >= remf * 0.999999f) {
+            t = tend;  // the step covered what was left
+            remf = 0.0f;
+        } else {
+            t = t + (double)h;
+            remf = (float)(tend - t);
+        }
         bool bad = false;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
@@ -1039,8 +1150,13 @@ struct RkcMixed {
             Fn[s] = f[s];
             if (sys.comp(tm, s) >= 0 && !isfinite(yh[s])) bad = true;
         }
-        h = h * (double)fmaxf((float)kP1, fac);
-        h = fmax(hmin, fmin(hmax, h));
+        if constexpr (SPEC) {
+            h = h * (double)fmaxf((float)kP1, fac);
+            h = fmax(hmin, fmin(hmax, h));
+        } else {
+            h = h * fmaxf((float)kP1, fac);
+            h = fmaxf(hmin, fminf(hmax, h));
+        }
         if (tm.any(bad)) {
             status |= ODE_ST_NONFINITE;
             phase = PH_DONE;

@@ -102,6 +102,16 @@ Nvrtc& nvrtc() {
     return n;
 }
 
+// Resident blocks of 128 threads per SM the generated kernels are compiled
+// for (a register budget of 65536 / (128 n) per thread).  3 measured best for
+// the 13-species network (168 registers; 1 and 2 leave 231, 4 spills);
+// BATCHODE_JIT_MINBLOCKS overrides it (1 = no budget).
+int jit_min_blocks() {
+    const char* v = getenv("BATCHODE_JIT_MINBLOCKS");
+    const int n = v ? atoi(v) : 3;
+    return n >= 1 && n <= 16 ? n : 3;
+}
+
 std::string lit(double x) {
     char buf[64];
     snprintf(buf, sizeof(buf), "%.17g", x);
@@ -209,7 +219,9 @@ std::mutex g_jit_mu;
 std::map<std::string, JitKernels> g_cache;  // key: device + source hash + form
 
 std::string method_type(int method, int prec) {
-    if (method == kMethodRkck) return prec == ODE_PREC_FP64 ? "bode::RkckF64<JitMass>" : "bode::RkckMixed<JitMass>";
+    if (method == kMethodRkck)
+        return prec == ODE_PREC_FP64 ? "bode::RkckF64<JitMass>"
+               : prec == ODE_PREC_MIXED ? "bode::RkckMixed<JitMass, true>" : "bode::RkckMixed<JitMass, false>";
     if (prec == ODE_PREC_FP64) return "bode::RkcF64<JitMass>";
     return prec == ODE_PREC_MIXED ? "bode::RkcMixed<JitMass, true>" : "bode::RkcMixed<JitMass, false>";
 }
@@ -228,8 +240,13 @@ int compile_image(const RhsEntry& r, int method, int prec, JitImage* img, std::s
     std::string src = "#include \"rhs.cuh\"\n#include \"integrators.cuh\"\n#include \"kernels.cuh\"\n" + model;
     std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
                                      prec == ODE_PREC_FP64 ? "--fmad=false" : "--fmad=true"};
-    const char* maxrreg = getenv("BATCHODE_JIT_MAXRREG");  // register cap (occupancy tuning)
-    if (maxrreg && atoi(maxrreg) > 0) opts.push_back(std::string("--maxrregcount=") + std::to_string(atoi(maxrreg)));
+    // occupancy tuning: blocks of at most 128 threads with a register budget
+    // for BATCHODE_JIT_MINBLOCKS resident blocks per SM
+    const int minb = jit_min_blocks();
+    if (minb > 1) {
+        opts.push_back("-DBODE_MAX_THREADS=128");
+        opts.push_back("-DBODE_MIN_BLOCKS=" + std::to_string(minb));
+    }
     const char* verbose = getenv("BATCHODE_JIT_VERBOSE");  // print the ptxas resource report
     if (verbose && *verbose == '1') opts.push_back("-Xptxas=-v");
     std::string key_text = src + "\n" + nstatic + "\n" + nqueue;
@@ -336,9 +353,8 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
 
 std::string cache_key(const RhsEntry& r, int method, int prec, int dev) {
     char key[96];
-    const char* maxrreg = getenv("BATCHODE_JIT_MAXRREG");
-    snprintf(key, sizeof(key), "%d/%d/%d/%016llx/%s", dev, method, prec, (unsigned long long)fnv1a(model_source(r)),
-             maxrreg ? maxrreg : "");
+    snprintf(key, sizeof(key), "%d/%d/%d/%016llx/%d", dev, method, prec, (unsigned long long)fnv1a(model_source(r)),
+             jit_min_blocks());
     return key;
 }
 
@@ -386,7 +402,7 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
     NoCtx ctx;
     BatchArgs args = a;
     void* params[] = {&args, &ctx};
-    const int block = c.block;
+    const int block = jit_min_blocks() > 1 && c.block > 128 ? 128 : c.block;
     const int64_t threads = a.nsys;  // one thread per system
     cudaError_t e;
     if (c.mapping == ODE_MAP_QUEUE) {

@@ -4,13 +4,23 @@
 #include "common.cuh"
 #include "team.cuh"
 
+// Launch bounds: at most BODE_MAX_THREADS threads per block and, when
+// BODE_MIN_BLOCKS > 1, a register budget that keeps that many blocks resident
+// per SM (the run-time compiled kernels take both from tuning options).
+#ifndef BODE_MAX_THREADS
+#define BODE_MAX_THREADS 256
+#endif
+#ifndef BODE_MIN_BLOCKS
+#define BODE_MIN_BLOCKS 1
+#endif
+
 namespace bode {
 
 // One system per team, one launch over the batch (the paper's intDriver
 // mapping when the team is one thread), grid rounded up.  Each iteration
 // evaluates the right-hand side once, at the point the system's phase needs.
 template <class Method, class Ctx>
-__global__ void __launch_bounds__(256) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
@@ -23,7 +33,7 @@ __global__ void __launch_bounds__(256) k_static(const BatchArgs a, const __grid_
         R tx;
         m.point(x, tx);
         m.sys.rhs(tm, tx, x, f);
-        m.consume(a, tm, f);
+        m.consume(a, tm, x, f);
     }
     m.store(a, tm, i);
 }
@@ -36,7 +46,7 @@ __global__ void __launch_bounds__(256) k_static(const BatchArgs a, const __grid_
 // (the divergence tail of the static mapping).  The only inter-thread
 // interaction is the atomic cursor.
 template <class Method, class Ctx>
-__global__ void __launch_bounds__(256) k_queue(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_queue(const BatchArgs a, const __grid_constant__ Ctx ctx) {
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
@@ -63,7 +73,7 @@ __global__ void __launch_bounds__(256) k_queue(const BatchArgs a, const __grid_c
             R tx;
             m.point(x, tx);
             m.sys.rhs(tm, tx, x, f);
-            if (m.consume(a, tm, f)) {
+            if (m.consume(a, tm, x, f)) {
                 m.store(a, tm, i);
                 next();
             }

@@ -83,7 +83,7 @@ extern "C" int rkc_integrate_noalloc(int32_t handle, int64_t nsys, const double*
     ode_opts opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_CNORM)
+    if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_LEAN)
         return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
     if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
     if (opts.block_size != 0 && (opts.block_size < 32 || opts.block_size > 256 || opts.block_size % 32))

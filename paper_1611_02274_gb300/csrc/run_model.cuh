@@ -13,11 +13,10 @@ cudaError_t run_model_prec(int method, const BatchArgs& a, const Ctx& ctx, const
         if (method == kMethodRkck) return launch_method<RkckF64<Model>>(a, ctx, c);
         return launch_method<RkcF64<Model>>(a, ctx, c);
     } else if constexpr (PREC == ODE_PREC_MIXED) {
-        if (method == kMethodRkck) return launch_method<RkckMixed<Model>>(a, ctx, c);
+        if (method == kMethodRkck) return launch_method<RkckMixed<Model, true>>(a, ctx, c);
         return launch_method<RkcMixed<Model, true>>(a, ctx, c);
     } else {
-        // RKCK's error norm is a maximum: both mixed modes share its kernels
-        if (method == kMethodRkck) return launch_method<RkckMixed<Model>>(a, ctx, c);
+        if (method == kMethodRkck) return launch_method<RkckMixed<Model, false>>(a, ctx, c);
         return launch_method<RkcMixed<Model, false>>(a, ctx, c);
     }
 }
@@ -26,7 +25,7 @@ cudaError_t run_model_prec(int method, const BatchArgs& a, const Ctx& ctx, const
 template <class Model, class Ctx>
 cudaError_t run_model_mixed(int method, int prec, const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c) {
     if (prec == ODE_PREC_MIXED) return run_model_prec<Model, ODE_PREC_MIXED>(method, a, ctx, c);
-    return run_model_prec<Model, ODE_PREC_MIXED_CNORM>(method, a, ctx, c);
+    return run_model_prec<Model, ODE_PREC_MIXED_LEAN>(method, a, ctx, c);
 }
 
 template <class Model, class Ctx>

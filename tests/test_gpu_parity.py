@@ -181,7 +181,7 @@ def test_mixed_generated_matches_generic(method):
         assert np.quantile(rel_err(g["y"], ref.y, w.atol), 0.99) < 1e-3
 
 
-@pytest.mark.parametrize("prec", [B.ODE_PREC_MIXED, B.ODE_PREC_MIXED_CNORM])
+@pytest.mark.parametrize("prec", [B.ODE_PREC_MIXED, B.ODE_PREC_MIXED_LEAN])
 @pytest.mark.parametrize("name", sorted(MIXED_CASES))
 def test_mixed_form_error_against_fp64_oracle(name, prec, record_property):
     make, bound = MIXED_CASES[name]

@@ -38,7 +38,7 @@ def rel(y, ref, atol):
     return float((np.abs(y - ref) / (np.abs(ref) + atol)).max())
 
 
-@pytest.mark.parametrize("prec", [B.ODE_PREC_FP64, B.ODE_PREC_MIXED_CNORM])
+@pytest.mark.parametrize("prec", [B.ODE_PREC_FP64, B.ODE_PREC_MIXED_LEAN])
 def test_noalloc_matches_rkc_integrate_twice(prec):
     # two different batches back to back: the second call runs on the
     # scratch the first one left behind (cursor, staged arrays)
