@@ -235,6 +235,7 @@ def run_ours(args):
     achieved = flops_mixed / (ms_chosen * 1e-3) / 1e12
     achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12
 
+    out = {}
     if rank == 0:
         peak32, _ = B.fma_peak(False, 1 << 20)
         peak64, _ = B.fma_peak(True, 1 << 14)
@@ -272,10 +273,136 @@ def run_ours(args):
         if not args.no_cpu:
             out["cpu_baseline"], acc = cpu_baseline(w, args, y_mixed, y_plain, c_plain)
             out["accuracy_vs_oracle"] = acc
+    if args.proposal_nsys > 0:
+        prop = proposal_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["learned_proposal"] = prop
+    if args.mixed_nsys > 0:
+        mixed = mixed_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["mixed_batch"] = mixed
+    if rank == 0:
         print(json.dumps(out), flush=True)
     B.release(h)
     if world > 1:
         dist.destroy_process_group()
+
+
+def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The learned initial-step / spectral-radius proposal on the 4,194,304-
+    system mass-action batch: trained on pairs the plain FP64 solver logs on
+    held-out seeds, then the chosen form timed with and without it (the
+    proposal pass is inside the timed step)."""
+    import oracle as O
+    t_start = time.perf_counter()
+    wt = W.massaction(nsys=args.proposal_train, seed=1000 + rank)
+    ht = B.register_workload(wt)
+    log = torch.full((wt.nsys, wt.neq + 3), float("nan"), dtype=torch.float32, device=dev)
+    B.integrate("rkc", ht, torch.from_numpy(wt.y0).to(dev), torch.from_numpy(wt.params).to(dev), wt.t0, wt.tend,
+                wt.rtol, wt.atol, precision=B.ODE_PREC_FP64, log_xy=log, sync=True)
+    B.release(ht)
+    ok = torch.isfinite(log).all(dim=1)
+    X, Y = log[ok, :wt.neq + 1].contiguous(), log[ok, wt.neq + 1:].contiguous()
+    net = B.MLP(wt.neq + 1, seed=0)
+    net.fit_normalization(X, Y)
+    hist = net.train(X, Y, epochs=8, batch=4096, lr=2e-3, seed=0)
+    t_train = time.perf_counter() - t_start
+    del log, X, Y
+
+    w = W.massaction(nsys=args.proposal_nsys, seed=4 + rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    yout = torch.empty_like(y0)
+    CH = B.ODE_PREC_MIXED_LEAN
+    B.prepare(h, "rkc", CH)
+
+    def step(use, counters=None):
+        kw = {}
+        if use:
+            h0, s0 = net.propose(y0, p, stream=stream.cuda_stream)
+            kw = dict(h0=h0, sigma0=s0)
+        B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters, precision=CH,
+                    mapping=B.ODE_MAP_QUEUE, stream=stream.cuda_stream, **kw)
+
+    res = {}
+    for use in (False, True):
+        for _ in range(args.warmup):
+            step(use)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.proposal_steps):
+            step(use)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.proposal_steps
+        cnt = B.counters_like(w.nsys, dev)
+        step(use, cnt)
+        torch.cuda.synchronize()
+        c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+        res["with_proposal" if use else "without"] = {
+            "systems_per_s": w.nsys * world / (ms * 1e-3), "ms_per_step": ms,
+            "reject_rate": float(np.sum(c["n_reject"]) / np.sum(c["n_accept"] + c["n_reject"])),
+            "mean_rhs": float(np.mean(c["n_rhs"])), "mean_power_iterations": float(np.mean(c["n_specrad_iter"])),
+            "proposal_used": float(np.mean((c["status"] & B.ODE_ST_PROPOSED) != 0)),
+            "y_sample": yout[:, :2048].cpu().numpy()}
+    B.release(h)
+    net.release()
+    ref = O.integrate_workload(W.subset(w, np.arange(2048)))
+    for r in res.values():
+        e = (np.abs(r.pop("y_sample") - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+        r["err_vs_fp64_oracle_max"] = float(e.max())
+        r["err_vs_fp64_oracle_p999"] = float(np.quantile(e, 0.999))
+    res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": int(ok.sum().item()), "train_seeds": "1000+rank",
+                     "eval_seed": "4+rank", "epochs": 8, "batch": 4096, "final_train_loss": float(hist[-1]),
+                     "train_seconds_incl_logging": t_train,
+                     "network": "14 -> 64 -> 64 -> 2 SiLU, BF16 weights, FP32 accumulate"}
+    res["speedup_with_proposal"] = res["without"]["ms_per_step"] / res["with_proposal"]["ms_per_step"]
+    return res
+
+
+def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The ragged batch: 262,144 systems, half Brusselator grids of 1-128
+    points (RKC, rtol 1e-5), half van der Pol chains of 1-64 oscillators
+    (RKCK, rtol 1e-6), in one graph-captured plan; the autotuned shapes
+    against the paper's fixed one-thread-per-system mapping."""
+    b = W.mixed(nsys=args.mixed_nsys, seed=rank)
+    hb = B.register(B.ODE_RHS_BRUSS1D, 256)
+    hc = B.register(B.ODE_RHS_VDP_CHAIN, 128, coupling=b.coupling)
+    handles = np.where(b.kind == B.ODE_RHS_BRUSS1D, hb, hc)
+    devt = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    y0, prm = devt(b.y0), devt(b.param)
+    t0, tend, rtol, atol = devt(b.t0), devt(b.tend), devt(b.rtol), devt(b.atol)
+    y = torch.empty_like(y0)
+    res = {}
+    for name, mapping in (("autotuned", B.ODE_MAP_AUTO), ("fixed_thread_per_system", B.ODE_MAP_THREAD)):
+        plan = B.RaggedPlan(handles, b.method, b.neq, b.offset[:-1], y0, prm, t0, tend, rtol, atol, y_out=y,
+                            precision=B.ODE_PREC_MIXED_LEAN, mapping=mapping, stream=stream.cuda_stream)
+        for _ in range(1):
+            plan.launch(stream.cuda_stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.mixed_steps):
+            plan.launch(stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.mixed_steps
+        res[name] = {"systems_per_s": b.nsys * world / (ms * 1e-3), "ms_per_step": ms,
+                     "buckets": [{k: d[k] for k in ("family", "method", "size_class", "systems", "lanes",
+                                                     "points_per_lane", "block")} for d in plan.info()]}
+        plan.destroy()
+    B.release(hb)
+    B.release(hc)
+    res["speedup_autotuned_vs_fixed"] = res["fixed_thread_per_system"]["ms_per_step"] / res["autotuned"]["ms_per_step"]
+    res["config"] = {"nsys_per_gpu": b.nsys, "unknowns_total": int(b.offset[-1]), "precision": "mixed lean",
+                     "graph": "one CUDA graph launch per step (all buckets on parallel branches)"}
+    return res
 
 
 def cpu_baseline(w, args, y_mixed, y_plain, c_plain):
@@ -363,6 +490,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--proposal-nsys", type=int, default=1 << 22, help="0 skips the learned-proposal leg")
+    ap.add_argument("--proposal-train", type=int, default=1 << 20)
+    ap.add_argument("--proposal-steps", type=int, default=3)
+    ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
+    ap.add_argument("--mixed-steps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -233,6 +233,50 @@ int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const dou
                           const ode_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Ragged batches: systems of different sizes, families and methods in one
+ * call (independent systems, Section 2, Eq. ode).  A plan buckets the
+ * systems by family, method and size class (8, 16, 32, 64, 128, 256
+ * unknowns), orders each bucket largest-first, chooses each bucket's kernel
+ * shape (lanes per system, grid points per lane, block size) and captures all
+ * buckets' persistent-queue kernels, on parallel branches, in one CUDA graph;
+ * ode_ragged_plan_launch replays it (in place when y_out == y0, so a plan can
+ * integrate the same buffers again and again).  opts->mapping: ODE_MAP_AUTO
+ * times the candidate shapes on a sample of each bucket (results cached per
+ * family / method / precision / size class), ODE_MAP_THREAD is the paper's
+ * one-thread-per-system mapping with 64-thread blocks, ODE_MAP_QUEUE the
+ * default warp-per-system shape.  Families: Brusselator and oscillator
+ * chains (register each family once with its largest neq).  Layout: system
+ * i's components are contiguous from offset[i]. */
+typedef struct {
+    int64_t nsys;
+    const int32_t* rhs;     /* HOST [nsys]: registered handle of each system's family */
+    const int32_t* method;  /* HOST [nsys]: 0 = RKCK, 1 = RKC */
+    const int32_t* neq;     /* HOST [nsys]: unknowns of each system (even, <= the handle's neq) */
+    const int64_t* offset;  /* HOST [nsys]: start of each system in y0 / y_out */
+    const double* y0;       /* DEVICE [sum neq] */
+    const double* params;   /* DEVICE [nsys]: one parameter per system */
+    const double* t0;       /* DEVICE [nsys] */
+    const double* tend;     /* DEVICE [nsys] */
+    const double* rtol;     /* DEVICE [nsys] */
+    const double* atol;     /* DEVICE [nsys] */
+} ode_ragged_batch;
+
+/* Builds a plan (tuning runs real integrations of samples on `stream`, then
+ * the graph is captured); *plan receives its handle.  Arrays and y_out /
+ * stats (device, indexed by system) must stay valid while the plan is used.
+ * Errors: ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM,
+ * ODE_ERR_CUDA. */
+int ode_ragged_plan_create(const ode_ragged_batch* batch, const ode_opts* opts, double* y_out,
+                           const ode_stats* stats, void* stream, int64_t* plan);
+/* Integrates the whole batch once (asynchronous on stream). */
+int ode_ragged_plan_launch(int64_t plan, void* stream);
+/* Bucket descriptions: 8 int32 per bucket (family, method, size class,
+ * systems, lanes per system, grid points per lane (0 = by size), block size,
+ * mapping), up to `capacity` buckets; *n_buckets gets the count. */
+int ode_ragged_plan_info(int64_t plan, int32_t* n_buckets, int32_t* desc, int32_t capacity);
+int ode_ragged_plan_destroy(int64_t plan);
+
+/* ---------------------------------------------------------------------
  * Learned initial step / spectral-radius proposal.  Not in the paper: the
  * paper starts every RKC system with a power-method estimate (Appendix) and
  * an Euler trial step (Section 2.2); this network proposes both from the

@@ -20,6 +20,8 @@ ODE_OK = 0
 ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM = -1, -2, -3, -4, -5
 ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 3
 ODE_ST_SPECRAD_NOCONV = 256
+ODE_ST_PROPOSED = 512
+MLP_HIDDEN, MLP_MAX_IN, MLP_NORM_FLOATS = 64, 33, 136
 ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION = 1, 2, 3, 4
 ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN = 0, 1, 2
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
@@ -27,7 +29,11 @@ ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
 ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
 
 EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_integrate", "rkc_integrate",
-            "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak"]
+            "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak",
+            "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
+            "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
+            "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
+            "ode_ragged_plan_destroy"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -46,7 +52,19 @@ class RhsDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
-                ("codegen", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("codegen", C.c_int32), ("reserved", C.c_int32 * 9),
+                ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p)]
+
+
+class RaggedBatch(C.Structure):
+    _fields_ = [("nsys", C.c_int64), ("rhs", C.c_void_p), ("method", C.c_void_p), ("neq", C.c_void_p),
+                ("offset", C.c_void_p), ("y0", C.c_void_p), ("params", C.c_void_p), ("t0", C.c_void_p),
+                ("tend", C.c_void_p), ("rtol", C.c_void_p), ("atol", C.c_void_p)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("pad", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -90,6 +108,21 @@ def load(build_if_missing: bool = True):
     L.ode_last_error.restype = C.c_char_p
     L.ode_version.restype = C.c_char_p
     L.bode_fma_peak.argtypes = [C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.ode_ragged_plan_create.argtypes = [C.POINTER(RaggedBatch), C.POINTER(Opts), P, C.POINTER(Stats), P,
+                                         C.POINTER(C.c_int64)]
+    L.ode_ragged_plan_launch.argtypes = [C.c_int64, P]
+    L.ode_ragged_plan_info.argtypes = [C.c_int64, C.POINTER(C.c_int32), P, C.c_int32]
+    L.ode_ragged_plan_destroy.argtypes = [C.c_int64]
+    L.ode_mlp_create.argtypes = [C.c_int32, C.c_uint64, C.POINTER(C.c_int32)]
+    L.ode_mlp_release.argtypes = [C.c_int32]
+    L.ode_mlp_num_params.argtypes = [C.c_int32]
+    L.ode_mlp_fit_normalization.argtypes = [C.c_int32, P, P, C.c_int64, P]
+    L.ode_mlp_train.argtypes = [C.c_int32, P, P, C.c_int64, C.POINTER(TrainOpts), P, P]
+    L.ode_mlp_gradient.argtypes = [C.c_int32, P, P, C.c_int64, P, C.POINTER(C.c_float), P]
+    L.ode_mlp_apply.argtypes = [C.c_int32, P, C.c_int64, P, P]
+    L.ode_mlp_propose.argtypes = [C.c_int32, C.c_int64, C.c_int32, P, P, C.c_float, P, P, P]
+    L.ode_mlp_get_params.argtypes = [C.c_int32, P, P]
+    L.ode_mlp_set_params.argtypes = [C.c_int32, P, P]
     _lib = L
     return L
 
@@ -162,7 +195,8 @@ class Counters:
 def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
-              stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO):
+              stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO, h0=None, sigma0=None,
+              log_xy=None):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
     tensor for device io, numpy array for host io); returns y_out."""
     host = isinstance(y0, np.ndarray)
@@ -174,6 +208,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.io = ODE_IO_HOST if host else ODE_IO_DEVICE
     o.sync = 1 if sync else 0
     o.codegen = codegen
+    o.h0, o.sigma0, o.log_xy = _ptr(h0), _ptr(sigma0), _ptr(log_xy)
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
@@ -223,6 +258,115 @@ def fma_peak(fp64: bool, iters: int = 1 << 16):
     g, ms = C.c_double(0), C.c_double(0)
     _check(load().bode_fma_peak(1 if fp64 else 0, iters, C.byref(g), C.byref(ms)))
     return g.value, ms.value
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class MLP:
+    """The learned h0 / sigma proposal (ode_mlp_*): inputs are torch CUDA
+    tensors, float32, rows contiguous."""
+
+    def __init__(self, n_in: int, seed: int = 0):
+        h = C.c_int32(0)
+        _check(load().ode_mlp_create(n_in, seed, C.byref(h)))
+        self.handle, self.n_in = int(h.value), n_in
+        self.n_params = int(load().ode_mlp_num_params(n_in))
+
+    def release(self):
+        if self.handle:
+            _check(load().ode_mlp_release(self.handle))
+            self.handle = 0
+
+    def fit_normalization(self, X, Y, stream=None):
+        _check(load().ode_mlp_fit_normalization(self.handle, _ptr(X), _ptr(Y), int(X.shape[0]), _stream(stream)))
+
+    def train(self, X, Y, epochs: int = 10, batch: int = 4096, lr: float = 1e-3, seed: int = 0, stream=None):
+        o = TrainOpts(epochs, batch, lr, 0, seed)
+        hist = np.zeros(epochs, dtype=np.float32)
+        _check(load().ode_mlp_train(self.handle, _ptr(X), _ptr(Y), int(X.shape[0]), C.byref(o), _ptr(hist),
+                                    _stream(stream)))
+        return hist
+
+    def gradient(self, X, Y, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = C.c_float(0)
+        _check(load().ode_mlp_gradient(self.handle, _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(g), C.byref(loss),
+                                       _stream(stream)))
+        return g, float(loss.value)
+
+    def apply(self, X, stream=None):
+        import torch
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(load().ode_mlp_apply(self.handle, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def propose(self, y0, params, margin: float = 0.05, stream=None):
+        import torch
+        nsys = int(y0.shape[1])
+        h0 = torch.empty(nsys, dtype=torch.float32, device=y0.device)
+        s0 = torch.empty(nsys, dtype=torch.float32, device=y0.device)
+        _check(load().ode_mlp_propose(self.handle, nsys, int(y0.shape[0]), _ptr(y0), _ptr(params), margin,
+                                      _ptr(h0), _ptr(s0), _stream(stream)))
+        return h0, s0
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        nrm = np.zeros(MLP_NORM_FLOATS, dtype=np.float32)
+        _check(load().ode_mlp_get_params(self.handle, _ptr(p), _ptr(nrm)))
+        return p, nrm
+
+    def set_params(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _check(load().ode_mlp_set_params(self.handle, _ptr(p), _ptr(n)))
+
+
+class RaggedPlan:
+    """ode_ragged_plan_*: a workloads.MixedBatch-like ragged batch integrated by
+    one CUDA graph.  Host metadata (numpy), device data (torch CUDA tensors)."""
+
+    def __init__(self, handles, method, neq, offset, y0, params, t0, tend, rtol, atol, y_out=None,
+                 counters: Counters | None = None, precision: int = ODE_PREC_MIXED_LEAN,
+                 mapping: int = ODE_MAP_AUTO, stream=None):
+        self._keep = [np.ascontiguousarray(handles, dtype=np.int32), np.ascontiguousarray(method, dtype=np.int32),
+                      np.ascontiguousarray(neq, dtype=np.int32), np.ascontiguousarray(offset, dtype=np.int64)]
+        self.y_out = y0 if y_out is None else y_out
+        self._dev = [y0, params, t0, tend, rtol, atol, self.y_out]
+        b = RaggedBatch(len(self._keep[0]), *[_ptr(a) for a in self._keep],
+                        *[_ptr(a) for a in (y0, params, t0, tend, rtol, atol)])
+        o = Opts()
+        o.precision, o.mapping = precision, mapping
+        s = Stats()
+        if counters is not None:
+            self._dev.append(counters)
+            s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
+                _ptr(getattr(counters, k)) for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")]
+        h = C.c_int64(0)
+        _check(load().ode_ragged_plan_create(C.byref(b), C.byref(o), _ptr(self.y_out), C.byref(s), _stream(stream),
+                                             C.byref(h)))
+        self.handle = int(h.value)
+
+    def launch(self, stream=None):
+        _check(load().ode_ragged_plan_launch(self.handle, _stream(stream)))
+
+    def info(self):
+        n = C.c_int32(0)
+        _check(load().ode_ragged_plan_info(self.handle, C.byref(n), None, 0))
+        d = np.zeros((max(n.value, 1), 8), dtype=np.int32)
+        _check(load().ode_ragged_plan_info(self.handle, C.byref(n), _ptr(d), n.value))
+        keys = ("family", "method", "size_class", "systems", "lanes", "points_per_lane", "block", "mapping")
+        return [dict(zip(keys, map(int, row))) for row in d[:n.value]]
+
+    def destroy(self):
+        if self.handle:
+            _check(load().ode_ragged_plan_destroy(self.handle))
+            self.handle = 0
 
 
 def version() -> str:

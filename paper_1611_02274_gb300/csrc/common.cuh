@@ -80,6 +80,24 @@ struct BatchArgs {
     const float* h0;
     const float* sigma0;
     float* log_xy;
+    // ragged batches: the queue holds nsys entries index[k] (global system
+    // numbers); system i's state starts at offset[i] (components contiguous)
+    // and has neq_arr[i] unknowns and its own interval and tolerances.
+    const int32_t* index;
+    const int64_t* offset;
+    const int32_t* neq_arr;
+    const double* t0_arr;
+    const double* tend_arr;
+    const double* rtol_arr;
+    const double* atol_arr;
+
+    __host__ __device__ int64_t sys_of(int64_t k) const { return index ? (int64_t)index[k] : k; }
+    __host__ __device__ int64_t yidx(int64_t i, int c) const { return offset ? offset[i] + c : i + nsys * (int64_t)c; }
+    __host__ __device__ int neq_of(int64_t i) const { return neq_arr ? neq_arr[i] : neq; }
+    __host__ __device__ double t0_of(int64_t i) const { return t0_arr ? t0_arr[i] : t0; }
+    __host__ __device__ double tend_of(int64_t i) const { return tend_arr ? tend_arr[i] : tend; }
+    __host__ __device__ double rtol_of(int64_t i) const { return rtol_arr ? rtol_arr[i] : rtol; }
+    __host__ __device__ double atol_of(int64_t i) const { return atol_arr ? atol_arr[i] : atol; }
 };
 
 __host__ __device__ inline int rkc_tab_index(int m, int j) { return m * (m - 1) / 2 - 1 + (j - 1); }

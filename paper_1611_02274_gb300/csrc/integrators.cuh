@@ -55,18 +55,18 @@ struct RkckF64 {
     int32_t n_acc, n_rej, status, max_att, stage;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
-        sys.load(ctx, tm, a.params[i], a.neq);
-#pragma unroll
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            y[s] = c >= 0 ? a.y0[i + a.nsys * (int64_t)c] : 0.0;
+            y[s] = c >= 0 ? a.y0[a.yidx(i, c)] : 0.0;
         }
-        t = a.t0;
-        tend = a.tend;
-        rtol = a.rtol;
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
+        rtol = a.rtol_of(i);
         hmax = fabs(tend - t);
         h = 0.5 * fabs(tend - t);
-        delta = (a.atol > 0.0) ? a.atol / a.rtol : kTiny;
+        delta = (a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny;
         n_acc = n_rej = status = 0;
         max_att = a.max_attempts;
         loop_top();
@@ -90,33 +90,33 @@ struct RkckF64 {
         switch (stage) {
         case 1:
             tx = t;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = y[s];
             break;
         case 2:
             tx = t + ck::A2 * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = y[s] + ck::B21 * k1[s];
             break;
         case 3:
             tx = t + ck::A3 * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = y[s] + ck::B31 * k1[s] + ck::B32 * k2[s];
             break;
         case 4:
             tx = t + ck::A4 * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = y[s] + ck::B41 * k1[s] + ck::B42 * k2[s] + ck::B43 * k3[s];
             break;
         case 5:
             tx = t + ck::A5 * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 x[s] = y[s] + ck::B51 * k1[s] + ck::B52 * k2[s] + ck::B53 * k3[s] + ck::B54 * k4[s];
             break;
         default:
             tx = t + ck::A6 * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 x[s] = y[s] + ck::B61 * k1[s] + ck::B62 * k2[s] + ck::B63 * k3[s] + ck::B64 * k4[s] +
                        ck::B65 * k5[s];
@@ -126,23 +126,23 @@ struct RkckF64 {
     __device__ bool consume(const BatchArgs&, const TM& tm, const double*, const double* f) {
         switch (stage) {
         case 1:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) k1[s] = h * f[s];
             break;
         case 2:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) k2[s] = h * f[s];
             break;
         case 3:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) k3[s] = h * f[s];
             break;
         case 4:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) k4[s] = h * f[s];
             break;
         case 5:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) k5[s] = h * f[s];
             break;
         default:
@@ -159,7 +159,7 @@ struct RkckF64 {
         double yt[P];
         double err = 0.0;
         bool nan_flag = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const double k6 = h * f[s];
             yt[s] = y[s] + ck::C1 * k1[s] + ck::C3 * k3[s] + ck::C4 * k4[s] + ck::C6 * k6;
@@ -193,7 +193,7 @@ struct RkckF64 {
             h = h * 5.0;
         h = fmax(1.0e-20, fmin(hmax, h));
         bool bad = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             y[s] = yt[s];
             if (sys.comp(tm, s) >= 0 && !isfinite(yt[s])) bad = true;
@@ -207,10 +207,10 @@ struct RkckF64 {
     }
 
     __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            if (c >= 0) a.y_out[i + a.nsys * (int64_t)c] = y[s];
+            if (c >= 0) a.y_out[a.yidx(i, c)] = y[s];
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;
@@ -241,18 +241,18 @@ struct RkcF64 {
     int64_t idx;  // system index (training log)
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
-        sys.load(ctx, tm, a.params[i], a.neq);
-        n = a.neq;
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        n = a.neq_of(i);
         idx = i;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            yn[s] = c >= 0 ? a.y0[i + a.nsys * (int64_t)c] : 0.0;
+            yn[s] = c >= 0 ? a.y0[a.yidx(i, c)] : 0.0;
         }
-        t = a.t0;
-        tend = a.tend;
-        rtol = a.rtol;
-        atol = a.atol;
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
+        rtol = a.rtol_of(i);
+        atol = a.atol_of(i);
         mmax = (int)round(sqrt(rtol / (10.0 * kUround)));
         if (mmax < 2) mmax = 2;
         hmax = fabs(tend - t);
@@ -270,7 +270,7 @@ struct RkcF64 {
 
     __device__ double sumsq(const TM& tm, const double* x) const {
         double sq[P];
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) sq[s] = x[s] * x[s];
         return sys.ordered_sum(tm, sq);
     }
@@ -279,27 +279,27 @@ struct RkcF64 {
         switch (phase) {
         case PH_F0:
             tx = t;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = yn[s];
             break;
         case PH_SR:
             tx = t;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = v[s];
             break;
         case PH_TRIAL:
             tx = t + h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = yn[s] + h * Fn[s];
             break;
         case PH_STAGE:
             tx = t + cur.cprev * h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = w1[s];
             break;
         default:  // PH_FINAL: F_{n+1} at w_m
             tx = t + h;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = w1[s];
         }
     }
@@ -307,7 +307,7 @@ struct RkcF64 {
     __device__ bool consume(const BatchArgs& a, const TM& tm, const double*, const double* f) {
         switch (phase) {
         case PH_F0:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 Fn[s] = f[s];
                 v[s] = f[s];  // first eigenvector guess
@@ -347,19 +347,19 @@ struct RkcF64 {
         const double nrm1 = sqrt(sumsq(tm, yn)), nrm2 = sqrt(sumsq(tm, v));
         if (nrm1 != 0.0 && nrm2 != 0.0) {
             dynrm = nrm1 * sq;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yn[s] + v[s] * (dynrm / nrm2);
         } else if (nrm1 != 0.0) {
             dynrm = nrm1 * sq;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yn[s] * (1.0 + sq);
         } else if (nrm2 != 0.0) {
             dynrm = kUround;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] * (dynrm / nrm2);
         } else {
             dynrm = kUround;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = kUround;
         }
         sig = 0.0;
@@ -371,28 +371,28 @@ struct RkcF64 {
         sr_iter += 1;
         n_sr += 1;
         double sq[P];
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) sq[s] = (Fv[s] - Fn[s]) * (Fv[s] - Fn[s]);
         const double d = sqrt(sys.ordered_sum(tm, sq));
         const double sig_prev = sig;
         sig = d / dynrm;
         if (sr_iter >= 2 && fabs(sig - sig_prev) <= fmax(sig, 1.0 / hmax) * 0.01) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yn[s];
             sr_end(a);
             return;
         }
         if (d != 0.0) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yn[s] + (Fv[s] - Fn[s]) * (dynrm / d);
         } else {
             const int ind = sr_iter % n;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) == ind) v[s] = yn[s] - (v[s] - yn[s]);
         }
         if (sr_iter == kSpecradItmax) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yn[s];
             status |= ODE_ST_SPECRAD_NOCONV;
             sr_end(a);
@@ -421,7 +421,7 @@ struct RkcF64 {
     __device__ void trial_consume(const BatchArgs& a, const TM& tm, const double* f) {
         n_rhs += 1;
         double sq[P];
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const double e = (f[s] - Fn[s]) / (atol + rtol * fabs(yn[s]));
             sq[s] = e * e;
@@ -443,7 +443,7 @@ struct RkcF64 {
         }
         cs.start(m, a);
         const double mut1 = cs.mut1();
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             w2[s] = yn[s];
             w1[s] = yn[s] + mut1 * h * Fn[s];
@@ -455,7 +455,7 @@ struct RkcF64 {
 
     // Eq. E:rkcj with f_{j-1} = f(t + c_{j-1} h, w_{j-1})
     __device__ void stage_consume(const BatchArgs&, const double* f) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const double wj = cur.cy * yn[s] + cur.mu * w1[s] + cur.nu * w2[s] + cur.mut * h * f[s] + cur.gt * h * Fn[s];
             w2[s] = w1[s];
@@ -472,7 +472,7 @@ struct RkcF64 {
     __device__ void final_consume(const BatchArgs& a, const TM& tm, const double* f) {
         n_rhs += m;
         double sq[P];
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             double e = 0.8 * (yn[s] - w1[s]) + 0.4 * h * (Fn[s] + f[s]);
             e = e / (atol + rtol * fmax(fabs(w1[s]), fabs(yn[s])));
@@ -514,7 +514,7 @@ struct RkcF64 {
         err_old = err;
         h_old = h;
         bool bad = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             yn[s] = w1[s];
             Fn[s] = f[s];
@@ -534,7 +534,7 @@ struct RkcF64 {
     // state, the parameter, log h and log sigma
     __device__ void write_log(const BatchArgs& a, const TM& tm) const {
         float* rec = a.log_xy + idx * (int64_t)(n + 3);
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
             if (c >= 0) rec[c] = (float)log(fmax(fabs(yn[s]), 1e-30));
@@ -547,10 +547,10 @@ struct RkcF64 {
     }
 
     __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            if (c >= 0) a.y_out[i + a.nsys * (int64_t)c] = yn[s];
+            if (c >= 0) a.y_out[a.yidx(i, c)] = yn[s];
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;
@@ -597,23 +597,23 @@ struct RkckMixed {
     int32_t n_acc, n_rej, status, max_att, stage;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
-        sys.load(ctx, tm, a.params[i], a.neq);
-#pragma unroll
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            const double y0 = c >= 0 ? a.y0[i + a.nsys * (int64_t)c] : 0.0;
+            const double y0 = c >= 0 ? a.y0[a.yidx(i, c)] : 0.0;
             yh[s] = (float)y0;
             yl[s] = (float)(y0 - (double)yh[s]);
             k1[s] = k2[s] = k3[s] = k4[s] = k5[s] = 0.0f;
         }
-        t = a.t0;
-        tend = a.tend;
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
         hmax = (HT)fabs(tend - t);
         h = (HT)(0.5 * fabs(tend - t));
         remf = (float)(tend - t);
         tabsf = fabsf((float)t);
-        deltaf = (float)((a.atol > 0.0) ? a.atol / a.rtol : kTiny);
-        inv_rtolf = (float)(1.0 / a.rtol);
+        deltaf = (float)((a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny);
+        inv_rtolf = (float)(1.0 / a.rtol_of(i));
         n_acc = n_rej = status = 0;
         max_att = a.max_attempts;
         loop_top();
@@ -654,7 +654,7 @@ struct RkckMixed {
         default: break;
         }
         tx = (float)t;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) x[s] = yh[s] + (b1 * k1[s] + b2 * k2[s] + b3 * k3[s] + b4 * k4[s] + b5 * k5[s]);
     }
 
@@ -663,7 +663,7 @@ struct RkckMixed {
             finish(tm, f);
             return done();
         }
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const float k = hf * f[s];
             k1[s] = stage == 1 ? k : k1[s];
@@ -680,7 +680,7 @@ struct RkckMixed {
         float incr[P];
         float err = 0.0f;
         bool nan_flag = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const float k6 = hf * f[s];
             incr[s] = (float)ck::C1 * k1[s] + (float)ck::C3 * k3[s] + (float)ck::C4 * k4[s] + (float)ck::C6 * k6;
@@ -697,7 +697,7 @@ struct RkckMixed {
             n_rej += 1;
             if (isnan(err) || nan_flag) {
                 h = h * (HT)kP1;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
                 for (int s = 0; s < P; ++s) k1[s] = k2[s] = k3[s] = k4[s] = k5[s] = 0.0f;
             } else {
                 h = h * (HT)fmaxf((float)kSafety * fpow(err, (float)kPshrnk), (float)kP1);
@@ -732,7 +732,7 @@ struct RkckMixed {
         else
             h = fmaxf(1.0e-20f, fminf(hmax, h * fac));
         bool bad = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             kahan_add(yh[s], yl[s], incr[s]);
             if (sys.comp(tm, s) >= 0 && !isfinite(yh[s])) bad = true;
@@ -746,10 +746,10 @@ struct RkckMixed {
     }
 
     __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            if (c >= 0) a.y_out[i + a.nsys * (int64_t)c] = (double)yh[s] + (double)yl[s];
+            if (c >= 0) a.y_out[a.yidx(i, c)] = (double)yh[s] + (double)yl[s];
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;
@@ -785,22 +785,22 @@ struct RkcMixed {
     bool have_sigma, rejected;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
-        sys.load(ctx, tm, a.params[i], a.neq);
-        n = a.neq;
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        n = a.neq_of(i);
         inv_nf = 1.0f / (float)n;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            const double y0 = c >= 0 ? a.y0[i + a.nsys * (int64_t)c] : 0.0;
+            const double y0 = c >= 0 ? a.y0[a.yidx(i, c)] : 0.0;
             yh[s] = (float)y0;
             yl[s] = (float)(y0 - (double)yh[s]);
         }
-        t = a.t0;
-        tend = a.tend;
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
         remf = (float)(tend - t);
-        rtolf = (float)a.rtol;
-        atolf = (float)a.atol;
-        mmax = (int)round(sqrt(a.rtol / (10.0 * kUround)));
+        rtolf = (float)a.rtol_of(i);
+        atolf = (float)a.atol_of(i);
+        mmax = (int)round(sqrt(a.rtol_of(i) / (10.0 * kUround)));
         if (mmax < 2) mmax = 2;
         hmax = (HT)fabs(tend - t);
         hmin = (HT)(10.0 * kUround * fmax(fabs(t), fabs(tend - t)));
@@ -831,7 +831,7 @@ struct RkcMixed {
 
     __device__ float sumsq(const TM& tm, const float* x) const {
         float acc = 0.0f;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s)
             if (sys.comp(tm, s) >= 0) acc = acc + x[s] * x[s];
         return tm.sum(acc);
@@ -841,19 +841,19 @@ struct RkcMixed {
         tx = (float)t;
         switch (phase) {
         case PH_F0:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = yh[s];
             break;
         case PH_SR:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = v[s];
             break;
         case PH_TRIAL:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = yh[s] + hf * Fn[s];
             break;
         default:  // stages and F_{n+1}: w = y_n + d
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) x[s] = yh[s] + (yl[s] + d1[s]);
         }
     }
@@ -861,7 +861,7 @@ struct RkcMixed {
     __device__ bool consume(const BatchArgs& a, const TM& tm, const float* x, const float* f) {
         switch (phase) {
         case PH_F0:
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 Fn[s] = f[s];
                 v[s] = f[s];
@@ -911,20 +911,20 @@ struct RkcMixed {
         if (nrm1 != 0.0f && nrm2 != 0.0f) {
             dynrm = nrm1 * kSqrtUroundF;
             const float sc = dynrm / nrm2;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yh[s] + v[s] * sc;
         } else if (nrm1 != 0.0f) {
             dynrm = nrm1 * kSqrtUroundF;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yh[s] * (1.0f + kSqrtUroundF);
         } else if (nrm2 != 0.0f) {
             dynrm = kSqrtUroundF;
             const float sc = dynrm / nrm2;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] * sc;
         } else {
             dynrm = kSqrtUroundF;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = kSqrtUroundF;
         }
         sig = 0.0f;
@@ -936,30 +936,30 @@ struct RkcMixed {
         sr_iter += 1;
         n_sr += 1;
         float acc = 0.0f;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s)
             if (sys.comp(tm, s) >= 0) acc = acc + (Fv[s] - Fn[s]) * (Fv[s] - Fn[s]);
         const float d = sqrtf(tm.sum(acc));
         const float sig_prev = sig;
         sig = d / dynrm;
         if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yh[s];
             sr_end(a);
             return;
         }
         if (d != 0.0f) {
             const float sc = dynrm / d;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = yh[s] + (Fv[s] - Fn[s]) * sc;
         } else {
             const int ind = sr_iter % n;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) == ind) v[s] = yh[s] - (v[s] - yh[s]);
         }
         if (sr_iter == kSpecradItmax) {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yh[s];
             status |= ODE_ST_SPECRAD_NOCONV;
             sr_end(a);
@@ -990,7 +990,7 @@ struct RkcMixed {
     __device__ double weighted_ssq(const TM& tm, E e_of) const {
         if constexpr (SPEC) {
             double acc = 0.0;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
                     const float e = e_of(s);
@@ -999,7 +999,7 @@ struct RkcMixed {
             return tm.sum(acc);
         } else {
             SumF2 acc;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
                     const float e = e_of(s);
@@ -1022,7 +1022,7 @@ struct RkcMixed {
                 h = hmax;
         } else {
             SumF2 acc;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
                     const float e = __fdividef(f[s] - Fn[s], atolf + rtolf * fabsf(yh[s]));
@@ -1049,7 +1049,7 @@ struct RkcMixed {
         hf = (float)h;
         cs.start(m, a);
         const float mut1h = (float)cs.mut1() * hf;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             d2[s] = 0.0f;
             d1[s] = mut1h * Fn[s];
@@ -1062,7 +1062,7 @@ struct RkcMixed {
     // d_j = mu_j d_{j-1} + nu_j d_{j-2} + mu~_j h f_{j-1} + gamma~_j h F_n
     __device__ void stage_consume(const float* f) {
         const float muth = cur.z * hf, gth = cur.w * hf;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const float dj = cur.x * d1[s] + cur.y * d2[s] + muth * f[s] + gth * Fn[s];
             d2[s] = d1[s];
@@ -1090,7 +1090,7 @@ struct RkcMixed {
             err = sqrtf((float)ms);
         } else {
             SumF2 acc;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
                 if (sys.comp(tm, s) >= 0) {
                     const float e = __fdividef(-0.8f * d1[s] + h04 * (Fn[s] + f[s]),
@@ -1144,7 +1144,7 @@ struct RkcMixed {
             remf = (float)(tend - t);
         }
         bool bad = false;
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             kahan_add(yh[s], yl[s], d1[s]);
             Fn[s] = f[s];
@@ -1166,10 +1166,10 @@ struct RkcMixed {
     }
 
     __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
-#pragma unroll
+#pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            if (c >= 0) a.y_out[i + a.nsys * (int64_t)c] = (double)yh[s] + (double)yl[s];
+            if (c >= 0) a.y_out[a.yidx(i, c)] = (double)yh[s] + (double)yl[s];
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;

@@ -24,8 +24,9 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(co
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-    if (i >= a.nsys) return;  // team-uniform
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+    if (k >= a.nsys) return;  // team-uniform
+    const int64_t i = a.sys_of(k);
     Method m;
     m.init(a, ctx, tm, i);
     R x[P], f[P];
@@ -58,9 +59,10 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_queue(con
         for (;;) {
             unsigned long long v = 0;
             if (tm.lane == 0) v = atomicAdd(a.cursor, 1ull);
-            i = (int64_t)tm.bcast(v, 0);
-            live = i < a.nsys;
+            const int64_t k = (int64_t)tm.bcast(v, 0);
+            live = k < a.nsys;
             if (!live) return;
+            i = a.sys_of(k);
             m.init(a, ctx, tm, i);
             if (!m.done()) return;
             m.store(a, tm, i);

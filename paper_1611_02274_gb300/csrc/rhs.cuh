@@ -79,7 +79,7 @@ struct ChainModel {
             T acc = T(0);
 #pragma unroll
             for (int fld = 0; fld < 2; ++fld)
-#pragma unroll
+#pragma unroll(G <= 32 ? G : 2)
                 for (int q = 0; q < G; ++q)
 #pragma unroll
                     for (int l = 0; l < W; ++l) {
@@ -89,7 +89,7 @@ struct ChainModel {
             return acc;
         }
         __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
-#pragma unroll
+#pragma unroll(G <= 32 ? G : 2)
             for (int q = 0; q < G; ++q) {
                 const int g = q * W + tm.lane;
                 const R x = y[2 * q];
@@ -148,7 +148,7 @@ struct BrussModel {
             T acc = T(0);
 #pragma unroll
             for (int fld = 0; fld < 2; ++fld)
-#pragma unroll
+#pragma unroll(G <= 32 ? G : 2)
                 for (int q = 0; q < G; ++q)
 #pragma unroll
                     for (int l = 0; l < W; ++l) {
@@ -158,7 +158,7 @@ struct BrussModel {
             return acc;
         }
         __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
-#pragma unroll
+#pragma unroll(G <= 32 ? G : 2)
             for (int q = 0; q < G; ++q) {
                 const int g = q * W + tm.lane;
                 const R u = y[2 * q], v = y[2 * q + 1];

@@ -1,0 +1,90 @@
+"""Ragged batches (Brusselator grids and oscillator chains of mixed sizes and
+methods) through one graph-captured plan, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1611_02274_gb300 import binding as B
+from paper_1611_02274_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def ragged_rel_err(y, ref, b):
+    e = np.abs(y - ref) / (np.abs(ref) + np.repeat(b.atol, b.neq))
+    return np.maximum.reduceat(e, b.offset[:-1])
+
+
+def build_plan(b, precision, mapping, counters=True):
+    import torch
+    hb = B.register(B.ODE_RHS_BRUSS1D, 256)
+    hc = B.register(B.ODE_RHS_VDP_CHAIN, 128, coupling=b.coupling)
+    handles = np.where(b.kind == B.ODE_RHS_BRUSS1D, hb, hc)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    y0 = dev(b.y0)
+    y = torch.empty_like(y0)
+    cnt = B.counters_like(b.nsys, "cuda") if counters else None
+    plan = B.RaggedPlan(handles, b.method, b.neq, b.offset[:-1], y0, dev(b.param), dev(b.t0), dev(b.tend),
+                        dev(b.rtol), dev(b.atol), y_out=y, counters=cnt, precision=precision, mapping=mapping)
+    return plan, y, cnt, (hb, hc)
+
+
+def run(b, precision, mapping):
+    import torch
+    plan, y, cnt, hs = build_plan(b, precision, mapping)
+    plan.launch()
+    torch.cuda.synchronize()
+    out = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+    out["y"] = y.cpu().numpy()
+    out["info"] = plan.info()
+    plan.destroy()
+    for h in hs:
+        B.release(h)
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    b = W.mixed(nsys=1200, seed=3)
+    b.tend = np.where(b.kind == B.ODE_RHS_BRUSS1D, 1.0, 2.0)   # shorter intervals keep the oracle quick
+    return b, O.integrate_mixed(b)
+
+
+def test_fp64_plan_reproduces_oracle(batch):
+    b, ref = batch
+    g = run(b, B.ODE_PREC_FP64, B.ODE_MAP_QUEUE)
+    same = (g["n_accept"] == ref.n_accept) & (g["n_reject"] == ref.n_reject)
+    assert same.mean() >= 0.999
+    assert ragged_rel_err(g["y"], ref.y, b)[same].max() <= 1e-9
+    np.testing.assert_array_equal(g["status"], ref.status)
+    assert {d["method"] for d in g["info"]} == {0, 1}
+
+
+@pytest.mark.parametrize("mapping", [B.ODE_MAP_AUTO, B.ODE_MAP_THREAD, B.ODE_MAP_QUEUE])
+def test_lean_plan_error_against_oracle(batch, mapping):
+    b, ref = batch
+    g = run(b, B.ODE_PREC_MIXED_LEAN, mapping)
+    assert ((g["status"] & 0xFF) == 0).all()
+    e = ragged_rel_err(g["y"], ref.y, b)
+    print(mapping, "p99.9", np.quantile(e, 0.999), "median", np.median(e), [(d["size_class"], d["lanes"], d["block"]) for d in g["info"]])
+    assert np.quantile(e, 0.99) < 2e-3
+    if mapping == B.ODE_MAP_THREAD:
+        assert all(d["lanes"] == 1 for d in g["info"])
+        assert all(d["block"] == 64 for d in g["info"])
+
+
+def test_plan_replays_identically(batch):
+    import torch
+    b, _ = batch
+    plan, y, cnt, hs = build_plan(b, B.ODE_PREC_MIXED_LEAN, B.ODE_MAP_AUTO)
+    plan.launch()
+    torch.cuda.synchronize()
+    first = y.cpu().numpy().copy()
+    y.zero_()
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y.cpu().numpy(), first)
+    plan.destroy()
+    for h in hs:
+        B.release(h)

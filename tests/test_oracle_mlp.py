@@ -1,0 +1,65 @@
+"""Pins of the FP64 reference network: its analytic gradient against central
+finite differences (brute force), and special cases fixed by the definition."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+
+def random_case(n_in=5, n=7, seed=0):
+    rng = np.random.default_rng(seed)
+    npar = 64 * n_in + 64 + 64 * 64 + 64 + 2 * 64 + 2
+    params = rng.normal(scale=0.3, size=npar)
+    norm = np.zeros(136)
+    norm[:n_in] = rng.normal(size=n_in)
+    norm[33:33 + n_in] = rng.uniform(0.5, 2.0, size=n_in)
+    norm[132:134] = rng.normal(size=2)
+    norm[134:136] = rng.uniform(0.5, 2.0, size=2)
+    X = rng.normal(size=(n, n_in))
+    Y = rng.normal(size=(n, 2))
+    return params, norm, X, Y
+
+
+def test_gradient_matches_finite_differences():
+    params, norm, X, Y = random_case()
+    loss, g = M.loss_and_grad(params, norm, X, Y)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(params.size, 60, replace=False)
+    eps = 1e-6
+    for k in idx:
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += eps
+        p2[k] -= eps
+        fd = (M.loss_and_grad(p1, norm, X, Y)[0] - M.loss_and_grad(p2, norm, X, Y)[0]) / (2 * eps)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-8), k
+
+
+def test_biases_only_network_outputs_biases():
+    n_in = 3
+    params = np.zeros(64 * n_in + 64 + 4096 + 64 + 128 + 2)
+    params[-2:] = [0.7, -1.3]
+    norm = np.zeros(136)
+    norm[33:36] = 1.0
+    norm[132:134] = [1.0, 2.0]
+    norm[134:136] = [2.0, 3.0]
+    out = M.forward(params, norm, np.ones((4, n_in)))
+    np.testing.assert_allclose(out, [[0.7 * 2 + 1, -1.3 * 3 + 2]] * 4)
+
+
+def test_pinball_loss_prefers_overestimates():
+    # an over-estimate of log sigma by d costs (1 - tau) d, an under-estimate tau d
+    params, norm, X, Y = random_case(n=1)
+    p = M.forward(params, norm, X)
+    ys = norm[134:136]
+    base = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1]]]))[0]
+    up = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] - ys[1]]]))[0]
+    down = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] + ys[1]]]))[0]
+    assert base == pytest.approx(0.0, abs=1e-12)
+    assert up == pytest.approx(1 - M.TAU) and down == pytest.approx(M.TAU)
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.00390625, 1.005859375, -3.14159, 65504.0], dtype=np.float32)
+    r = M.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125   # ties to even, then round up
+    assert abs(r[3] / -3.14159 - 1) < 2 ** -8
