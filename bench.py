@@ -152,7 +152,7 @@ def run_ours(args):
 
     def step(prec, counters=None):
         B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
-                    precision=prec, mapping=B.ODE_MAP_QUEUE, stream=stream.cuda_stream)
+                    precision=prec, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
 
     CHOSEN = B.ODE_PREC_MIXED_LEAN
     for prec in (CHOSEN, B.ODE_PREC_MIXED, B.ODE_PREC_FP64):
@@ -220,7 +220,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
-                    precision=CHOSEN, mapping=B.ODE_MAP_QUEUE)
+                    precision=CHOSEN, mapping=B.ODE_MAP_AUTO)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
@@ -323,7 +323,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
             h0, s0 = net.propose(y0, p, stream=stream.cuda_stream)
             kw = dict(h0=h0, sigma0=s0)
         B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters, precision=CH,
-                    mapping=B.ODE_MAP_QUEUE, stream=stream.cuda_stream, **kw)
+                    mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream, **kw)
 
     res = {}
     for use in (False, True):

@@ -76,15 +76,20 @@ extern "C" {
 #define ODE_PREC_MIXED 1     /* FP32 RHS and stage arithmetic with Kahan-compensated FP32 state;
                                 FP64 time, step size, error-norm accumulation and Chebyshev
                                 coefficients */
-#define ODE_PREC_MIXED_LEAN 2 /* FP32 RHS, stages, step size, spectral radius and error norms
-                                (norms with compensated two-sum accumulation), Kahan-compensated
-                                FP32 state; FP64 kept where rounding accumulates -- the time t --
-                                and for the Chebyshev coefficients.  The FP64 pipe of this GPU
-                                runs at 1/64 of the FP32 rate, so every FP64 instruction of the
-                                step-size bookkeeping costs as much as ~64 FP32 ones */
+#define ODE_PREC_MIXED_LEAN 2 /* FP32 RHS, stages, step size, spectral radius and error norms,
+                                Kahan-compensated FP32 state; FP64 kept where rounding accumulates
+                                -- the time t -- and for the Chebyshev coefficients.  The FP64 pipe
+                                of this GPU runs at 1/64 of the FP32 rate, so every FP64 instruction
+                                of the step-size bookkeeping costs as much as ~64 FP32 ones */
 
 /* how systems map onto the GPU */
-#define ODE_MAP_AUTO 0       /* autotuned choice (cached per rhs / method / precision) */
+#define ODE_MAP_AUTO 0       /* uniform batches: the first call with >= 32768 systems times the
+                                thread and queue mappings at several block sizes on its first
+                                systems (output to scratch; the host waits for these runs), and
+                                the choice is cached per rhs / method / precision / device.
+                                Smaller batches, and calls on a capturing stream, use
+                                ODE_MAP_THREAD with 128-thread blocks.  Ragged plans: see
+                                ode_ragged_plan_create */
 #define ODE_MAP_THREAD 1     /* one thread per system, one launch over the batch (the paper's) */
 #define ODE_MAP_QUEUE 2      /* persistent kernel, one thread per system, systems pulled from a
                                 device work queue one at a time as lanes finish */
@@ -241,8 +246,10 @@ int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const dou
  * buckets' persistent-queue kernels, on parallel branches, in one CUDA graph;
  * ode_ragged_plan_launch replays it (in place when y_out == y0, so a plan can
  * integrate the same buffers again and again).  opts->mapping: ODE_MAP_AUTO
- * times the candidate shapes on a sample of each bucket (results cached per
- * family / method / precision / size class), ODE_MAP_THREAD is the paper's
+ * times the candidate shapes, block sizes and mappings (queue or one launch)
+ * on a sample of each bucket (results cached per family / method /
+ * precision / size class; an in-place plan's sample writes to a temporary
+ * copy of the state), ODE_MAP_THREAD is the paper's
  * one-thread-per-system mapping with 64-thread blocks, ODE_MAP_QUEUE the
  * default warp-per-system shape.  Families: Brusselator and oscillator
  * chains (register each family once with its largest neq).  Layout: system
@@ -323,6 +330,13 @@ int ode_mlp_propose(int32_t mlp_handle, int64_t nsys, int32_t neq, const double*
 /* host copies of the FP32 parameters [num_params] and the normalisation block (either may be NULL) */
 int ode_mlp_get_params(int32_t mlp_handle, float* params, float* norm);
 int ode_mlp_set_params(int32_t mlp_handle, const float* params, const float* norm);
+
+/* Forget every cached ODE_MAP_AUTO timing (uniform calls and ragged plans),
+ * so that the next such call or plan times its candidates again (after a
+ * change of the generated kernels' occupancy setting, say).  No counterpart
+ * in the paper, whose mapping is fixed.  Existing plans keep their shapes.
+ * Always returns ODE_OK. */
+int ode_tuning_reset(void);
 
 /* Description of the last error on this thread ("" if none). */
 const char* ode_last_error(void);

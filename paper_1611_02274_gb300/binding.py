@@ -33,7 +33,7 @@ EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_inte
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
             "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
-            "ode_ragged_plan_destroy"]
+            "ode_ragged_plan_destroy", "ode_tuning_reset"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -367,6 +367,11 @@ class RaggedPlan:
         if self.handle:
             _check(load().ode_ragged_plan_destroy(self.handle))
             self.handle = 0
+
+
+def tuning_reset() -> None:
+    """Forget cached ODE_MAP_AUTO timings (uniform calls and ragged plans)."""
+    _check(load().ode_tuning_reset())
 
 
 def version() -> str:

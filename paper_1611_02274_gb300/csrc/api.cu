@@ -9,6 +9,9 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
+#include <algorithm>
 
 #include "batchode.h"
 #include "jit.h"
@@ -43,8 +46,10 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int kCursorRing = 1024;
 constexpr int kRkcTabMax = 256;  // stage counts with tabulated coefficients
 struct Workspace {
-    unsigned long long* cursors = nullptr;
+    unsigned long long* cursors = nullptr;  // kCursorRing + 1: the last one for tuning runs
     int next_cursor = 0;
+    double* tune_y = nullptr;  // output of mapping-tuning runs, grow-only
+    size_t tune_bytes = 0;
     double* tab64 = nullptr;
     float4* tab32 = nullptr;
     void* stage = nullptr;
@@ -59,7 +64,7 @@ int get_workspace(Workspace** out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     Workspace& w = g_ws[dev];
     if (!w.cursors) {
-        e = cudaMalloc(&w.cursors, sizeof(unsigned long long) * kCursorRing);
+        e = cudaMalloc(&w.cursors, sizeof(unsigned long long) * (kCursorRing + 1));
         if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "workspace allocation failed: %s", cudaGetErrorString(e));
         e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
@@ -136,6 +141,125 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
 }
 
 enum Method { kRkck = 0, kRkc = 1 };
+
+// One launch of the family's kernel (queue cursor reset included).
+int dispatch(const RhsEntry& rhs, int meth, int prec, bool use_jit, const BatchArgs& a, const LaunchCfg& cfg) {
+    cudaError_t e;
+    if (cfg.mapping == ODE_MAP_QUEUE) {
+        e = cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), cfg.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cursor reset");
+    }
+    bool supported = true;
+    switch (rhs.kind) {
+    case ODE_RHS_VDP: e = launch_vdp(meth, prec, rhs, a, cfg, &supported); break;
+    case ODE_RHS_MASSACTION:
+        if (use_jit) {
+            std::string why;
+            const int rc = jit_launch(rhs, meth, prec, a, cfg, &why);
+            if (rc) return fail(rc, "%s", why.c_str());
+            e = cudaSuccess;
+        } else {
+            e = launch_mass(meth, prec, rhs, a, cfg, &supported);
+        }
+        break;
+    case ODE_RHS_BRUSS1D: e = launch_bruss(meth, prec, rhs, a, cfg, &supported); break;
+    case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, prec, rhs, a, cfg, &supported); break;
+    default: supported = false; e = cudaSuccess;
+    }
+    if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built for this method", rhs.kind, rhs.neq);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return ODE_OK;
+}
+
+// ODE_MAP_AUTO: the mapping and block size of a (rhs, method, precision,
+// code path, device) are timed once on a sample of the first batch that is
+// large enough to fill the device, and cached.  Smaller batches, and calls
+// on a capturing stream, take the untuned default.
+constexpr int64_t kTuneMinSystems = 32768;
+std::map<std::tuple<int32_t, int, int, int, int, int>, std::pair<int, int>> g_map_tuned;
+
+// Untuned default: one thread per system, one launch over the batch (lanes
+// of a warp then start their systems together and stay in step longer than
+// the queue's refills let them).
+void default_mapping(LaunchCfg* cfg, int block_req) {
+    cfg->mapping = ODE_MAP_THREAD;
+    cfg->block = block_req ? block_req : 128;
+}
+
+int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, int prec, bool use_jit, int block_req,
+                 const BatchArgs& a, LaunchCfg* cfg) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(handle, meth, prec, (int)use_jit, dev, block_req);
+    auto it = g_map_tuned.find(key);
+    if (it != g_map_tuned.end()) {
+        cfg->mapping = it->second.first;
+        cfg->block = it->second.second;
+        return ODE_OK;
+    }
+    default_mapping(cfg, block_req);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(cfg->stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (a.nsys < kTuneMinSystems || cap != cudaStreamCaptureStatusNone) return ODE_OK;
+
+    // sample: the first systems of the batch, output to a scratch buffer
+    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(65536, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
+    const size_t bytes = sizeof(double) * (size_t)sample * rhs.neq;
+    if (ws->tune_bytes < bytes) {
+        if (ws->tune_y) cudaFree(ws->tune_y);
+        ws->tune_y = nullptr;
+        ws->tune_bytes = 0;
+        if (cudaMalloc(&ws->tune_y, bytes) != cudaSuccess) return ODE_OK;  // untuned
+        ws->tune_bytes = bytes;
+    }
+    BatchArgs t = a;
+    t.nsys = sample;
+    t.ld_in = a.nsys;
+    t.ld_out = sample;
+    t.y_out = ws->tune_y;
+    t.n_accept = t.n_reject = t.n_rhs = t.n_specrad = t.status = nullptr;
+    t.log_xy = nullptr;
+    t.cursor = ws->cursors + kCursorRing;
+    std::vector<std::pair<int, int>> cand;
+    for (int b : {64, 128, 256})
+        if (!block_req || b == block_req) cand.push_back({ODE_MAP_THREAD, b});
+    if (block_req && block_req != 64 && block_req != 128 && block_req != 256) cand.push_back({ODE_MAP_THREAD, block_req});
+    cand.push_back({ODE_MAP_QUEUE, block_req ? block_req : 128});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    float best = 3.0e38f;
+    int rc = ODE_OK;
+    for (size_t k = 0; k <= cand.size() && rc == ODE_OK; ++k) {
+        // k = 0 warms up (code paging, caches) with the first candidate
+        LaunchCfg c = *cfg;
+        c.mapping = cand[k ? k - 1 : 0].first;
+        c.block = cand[k ? k - 1 : 0].second;
+        e = cudaEventRecord(e0, c.stream);
+        if (e == cudaSuccess) rc = dispatch(rhs, meth, prec, use_jit, t, c);
+        if (rc) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "mapping tuning");
+            break;
+        }
+        if (k && ms < best) {
+            best = ms;
+            cfg->mapping = c.mapping;
+            cfg->block = c.block;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    g_map_tuned[key] = {cfg->mapping, cfg->block};
+    return ODE_OK;
+}
 
 int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, const double* params, double t0,
               double tend, double rtol, double atol, const ode_opts* opts_in, double* y_out,
@@ -242,35 +366,20 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     ws->next_cursor = (ws->next_cursor + 1) % kCursorRing;
 
     LaunchCfg cfg;
-    cfg.mapping = opts.mapping == ODE_MAP_THREAD ? ODE_MAP_THREAD : ODE_MAP_QUEUE;
+    cfg.mapping = opts.mapping;
     cfg.block = opts.block_size ? opts.block_size : 128;
     cfg.team = 0;
     cfg.sm_count = ws->sm_count;
     cfg.stream = stream;
-    if (cfg.mapping == ODE_MAP_QUEUE) {
-        e = cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cursor reset");
-    }
-    bool supported = true;
     const int meth = method == kRkck ? kMethodRkck : kMethodRkc;
-    switch (rhs.kind) {
-    case ODE_RHS_VDP: e = launch_vdp(meth, opts.precision, rhs, a, cfg, &supported); break;
-    case ODE_RHS_MASSACTION:
-        if (opts.codegen == ODE_CODEGEN_ON || (opts.codegen == ODE_CODEGEN_AUTO && jit_available())) {
-            std::string why;
-            rc = jit_launch(rhs, meth, opts.precision, a, cfg, &why);
-            if (rc) return fail(rc, "%s", why.c_str());
-            e = cudaSuccess;
-        } else {
-            e = launch_mass(meth, opts.precision, rhs, a, cfg, &supported);
-        }
-        break;
-    case ODE_RHS_BRUSS1D: e = launch_bruss(meth, opts.precision, rhs, a, cfg, &supported); break;
-    case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, opts.precision, rhs, a, cfg, &supported); break;
-    default: supported = false; e = cudaSuccess;
+    const bool use_jit = rhs.kind == ODE_RHS_MASSACTION &&
+                         (opts.codegen == ODE_CODEGEN_ON || (opts.codegen == ODE_CODEGEN_AUTO && jit_available()));
+    if (opts.mapping == ODE_MAP_AUTO) {
+        rc = tune_mapping(ws, handle, rhs, meth, opts.precision, use_jit, opts.block_size, a, &cfg);
+        if (rc) return rc;
     }
-    if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built for this method", rhs.kind, rhs.neq);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    rc = dispatch(rhs, meth, opts.precision, use_jit, a, cfg);
+    if (rc) return rc;
 
     if (opts.io == ODE_IO_HOST) {
         e = cudaMemcpyAsync(y_out, d_yout, sizeof(double) * ny, cudaMemcpyDeviceToHost, stream);
@@ -288,6 +397,8 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
 }  // namespace
 
 namespace bode {
+
+void ragged_tuning_reset();
 
 // Registry and error-string access for the allocation-free entry point
 // (noalloc.cu).
@@ -327,6 +438,8 @@ int ode_rhs_release(int32_t rhs_handle) {
     g_err.clear();
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_reg.erase(rhs_handle) == 0) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    for (auto it = g_map_tuned.begin(); it != g_map_tuned.end();)
+        it = std::get<0>(it->first) == rhs_handle ? g_map_tuned.erase(it) : std::next(it);
     return ODE_OK;
 }
 
@@ -358,6 +471,16 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
                   double rtol, double atol, const ode_opts* opts, double* y_out, const ode_stats* stats,
                   void* stream) {
     return integrate(kRkc, rhs, nsys, y0, params, t0, tend, rtol, atol, opts, y_out, stats, stream);
+}
+
+int ode_tuning_reset(void) {
+    g_err.clear();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_map_tuned.clear();
+    }
+    ragged_tuning_reset();
+    return ODE_OK;
 }
 
 const char* ode_last_error(void) { return g_err.c_str(); }

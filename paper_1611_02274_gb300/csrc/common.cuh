@@ -8,6 +8,15 @@
 
 namespace bode {
 
+// An integer the optimiser cannot see through.  A loop that writes only the
+// element whose index equals a run-time value would otherwise be rewritten
+// as one indexed store, and an indexed store forces the whole per-system
+// state object out of registers into local memory.
+__device__ __forceinline__ int opaque(int x) {
+    asm("" : "+r"(x));
+    return x;
+}
+
 // Constants of the paper's listings (Section 3.1 constants, Section 3.2).
 constexpr double kUround = 2.22e-16;
 constexpr double kSafety = 0.9;
@@ -90,9 +99,19 @@ struct BatchArgs {
     const double* tend_arr;
     const double* rtol_arr;
     const double* atol_arr;
+    // uniform layout: stride between consecutive components of a system in
+    // y0 (ld_in) and y_out (ld_out); 0 means nsys.  A run on the first k
+    // systems of a batch (mapping autotuning) keeps the batch's input stride
+    // and writes a k-system output.
+    int64_t ld_in, ld_out;
 
     __host__ __device__ int64_t sys_of(int64_t k) const { return index ? (int64_t)index[k] : k; }
-    __host__ __device__ int64_t yidx(int64_t i, int c) const { return offset ? offset[i] + c : i + nsys * (int64_t)c; }
+    __host__ __device__ int64_t yidx(int64_t i, int c) const {
+        return offset ? offset[i] + c : i + (ld_in ? ld_in : nsys) * (int64_t)c;
+    }
+    __host__ __device__ int64_t yidx_out(int64_t i, int c) const {
+        return offset ? offset[i] + c : i + (ld_out ? ld_out : nsys) * (int64_t)c;
+    }
     __host__ __device__ int neq_of(int64_t i) const { return neq_arr ? neq_arr[i] : neq; }
     __host__ __device__ double t0_of(int64_t i) const { return t0_arr ? t0_arr[i] : t0; }
     __host__ __device__ double tend_of(int64_t i) const { return tend_arr ? tend_arr[i] : tend; }

@@ -10,8 +10,9 @@
 // launch replays the graph: one call integrates the whole batch, and while
 // one bucket drains its tail the others fill the freed SMs.
 //
-// Shapes: ODE_MAP_AUTO times each candidate shape x block size on a sample
-// of the bucket (cached per family / method / precision / size class);
+// Shapes: ODE_MAP_AUTO times each candidate shape x block size x mapping
+// (persistent queue or one launch over the bucket) on a sample of the
+// bucket (cached per family / method / precision / size class);
 // ODE_MAP_THREAD is the paper's mapping (one thread per system, one
 // launch, 64-thread blocks); ODE_MAP_QUEUE uses the default warp-per-system
 // shape without tuning.
@@ -132,8 +133,12 @@ struct Plan {
 std::mutex g_mu;
 std::map<int64_t, Plan*> g_plans;
 int64_t g_next_plan = 1;
-// tuned (shape, block) per family / method / precision / size class / SM count
-std::map<std::tuple<int, int, int, int, int>, std::pair<Shape, int>> g_tuned;
+// tuned (shape, block, mapping) per family / method / precision / size class / SM count
+struct Tuned {
+    Shape shape;
+    int block, mapping;
+};
+std::map<std::tuple<int, int, int, int, int>, Tuned> g_tuned;
 
 constexpr int kTabMax = 256;
 
@@ -187,6 +192,13 @@ int destroy(Plan* p) {
 }
 
 }  // namespace
+
+namespace bode {
+void ragged_tuning_reset() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned.clear();
+}
+}  // namespace bode
 
 extern "C" {
 
@@ -271,6 +283,7 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
     }
 
     // shapes
+    double* tune_out = nullptr;
     for (auto& b : p->buckets) {
         const int family = b.rhs.kind;
         if (o.mapping == ODE_MAP_THREAD) {
@@ -284,18 +297,29 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
         b.shape = cand.front();
         b.block = 128;
         b.mapping = ODE_MAP_QUEUE;
-        if (o.mapping == ODE_MAP_QUEUE || cand.size() == 1) continue;
+        if (o.mapping == ODE_MAP_QUEUE) continue;
         auto key = std::make_tuple(family, b.method, o.precision, b.cls, sms);
         {
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tuned.find(key);
             if (it != g_tuned.end()) {
-                b.shape = it->second.first;
-                b.block = it->second.second;
+                b.shape = it->second.shape;
+                b.block = it->second.block;
+                b.mapping = it->second.mapping;
                 continue;
             }
         }
-        // time each shape and block size on a sample of this bucket
+        // time each shape, block size and mapping on a sample of this bucket;
+        // the sample's results go to a scratch state when the plan
+        // integrates in place (they would overwrite initial states)
+        if (y_out == rb->y0 && !tune_out) {
+            int64_t ny = 0;
+            for (int64_t i = 0; i < nsys; ++i) ny = std::max<int64_t>(ny, rb->offset[i] + rb->neq[i]);
+            if (cudaMalloc(&tune_out, sizeof(double) * (size_t)ny) != cudaSuccess) {
+                tune_out = nullptr;
+                continue;  // untuned
+            }
+        }
         const int64_t sample = std::min<int64_t>((int64_t)b.sys.size(), 8192);
         float best = 3.0e38f;
         cudaEvent_t e0, e1;
@@ -303,38 +327,44 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
         cudaEventCreate(&e1);
         for (const Shape& sh : cand) {
             for (int blk : {64, 128, 256}) {
-                BatchArgs a;
-                make_args(*p, b, *rb, o, y_out, st, sample, p->d_cursor + 32 * nb, &a);
-                LaunchCfg cfg{ODE_MAP_QUEUE, blk, sh.team, sms, user};
                 bool ok = true;
-                cudaMemsetAsync(a.cursor, 0, 8, user);
-                launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);  // warm-up
+                for (int map : {ODE_MAP_QUEUE, ODE_MAP_THREAD}) {
+                    BatchArgs a;
+                    make_args(*p, b, *rb, o, tune_out ? tune_out : y_out, st, sample, p->d_cursor + 32 * nb, &a);
+                    LaunchCfg cfg{map, blk, sh.team, sms, user};
+                    cudaMemsetAsync(a.cursor, 0, 8, user);
+                    launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);  // warm-up
+                    if (!ok) break;
+                    cudaMemsetAsync(a.cursor, 0, 8, user);
+                    cudaEventRecord(e0, user);
+                    launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);
+                    cudaEventRecord(e1, user);
+                    e = cudaEventSynchronize(e1);
+                    if (e != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        cudaFree(tune_out);
+                        destroy(p);
+                        return cuda_fail(e, "autotuning launch");
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        b.shape = sh;
+                        b.block = blk;
+                        b.mapping = map;
+                    }
+                }
                 if (!ok) break;
-                cudaMemsetAsync(a.cursor, 0, 8, user);
-                cudaEventRecord(e0, user);
-                launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);
-                cudaEventRecord(e1, user);
-                e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    destroy(p);
-                    return cuda_fail(e, "autotuning launch");
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    b.shape = sh;
-                    b.block = blk;
-                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_mu);
-        g_tuned[key] = {b.shape, b.block};
+        g_tuned[key] = {b.shape, b.block, b.mapping};
     }
+    cudaFree(tune_out);
 
     // graph: fork one branch per bucket, join
     cudaStream_t cap;

@@ -15,14 +15,14 @@ def ragged_rel_err(y, ref, b):
     return np.maximum.reduceat(e, b.offset[:-1])
 
 
-def build_plan(b, precision, mapping, counters=True):
+def build_plan(b, precision, mapping, counters=True, in_place=False):
     import torch
     hb = B.register(B.ODE_RHS_BRUSS1D, 256)
     hc = B.register(B.ODE_RHS_VDP_CHAIN, 128, coupling=b.coupling)
     handles = np.where(b.kind == B.ODE_RHS_BRUSS1D, hb, hc)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
     y0 = dev(b.y0)
-    y = torch.empty_like(y0)
+    y = y0 if in_place else torch.empty_like(y0)
     cnt = B.counters_like(b.nsys, "cuda") if counters else None
     plan = B.RaggedPlan(handles, b.method, b.neq, b.offset[:-1], y0, dev(b.param), dev(b.t0), dev(b.tend),
                         dev(b.rtol), dev(b.atol), y_out=y, counters=cnt, precision=precision, mapping=mapping)
