@@ -56,6 +56,11 @@ struct Pick<false, T, F> {
     using type = F;
 };
 
+// Floats of shared memory per thread that the mixed RKC integrator keeps its
+// power-method vector in (one-thread systems of at most 32 unknowns; larger
+// or multi-lane systems keep it in registers).
+__host__ __device__ constexpr int rkc_mixed_smem_floats(int lanes, int per_lane) { return (lanes == 1 && per_lane <= 32) ? per_lane : 0; }
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 

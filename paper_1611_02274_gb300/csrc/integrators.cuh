@@ -42,10 +42,24 @@ __device__ __forceinline__ void kahan_add(float& hi, float& lo, float d) {
     hi = t;
 }
 
+// Double-float subtraction (hi, lo) -= b: Knuth's two-sum of hi and -b gives
+// the rounded difference and its exact error, which joins lo before a
+// renormalisation.  Keeps a time interval to ~48 significant bits with FP32
+// instructions only.
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float b) {
+    const float s = hi - b;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) - (b + bb);
+    const float l = lo + e;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
 // ================================================================ RKCK F64
 
 template <class Model>
 struct RkckF64 {
+    static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
     using TM = Team<W>;
@@ -226,6 +240,7 @@ struct RkckF64 {
 
 template <class Model>
 struct RkcF64 {
+    static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
     using TM = Team<W>;
@@ -585,6 +600,7 @@ struct SumF2 {
 // FP32 and a step that reaches the end of the interval lands on tend exactly.
 template <class Model, bool SPEC = true>
 struct RkckMixed {
+    static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
     using TM = Team<W>;
@@ -593,7 +609,7 @@ struct RkckMixed {
     float yh[P], yl[P], k1[P], k2[P], k3[P], k4[P], k5[P];
     double t, tend;
     HT h, hmax;
-    float hf, remf, tabsf, deltaf, inv_rtolf;
+    float hf, remf, reml, tendf, tabsf, deltaf, inv_rtolf;  // lean: remaining interval remf + reml
     int32_t n_acc, n_rej, status, max_att, stage;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
@@ -611,6 +627,8 @@ struct RkckMixed {
         hmax = (HT)fabs(tend - t);
         h = (HT)(0.5 * fabs(tend - t));
         remf = (float)(tend - t);
+        reml = (float)((tend - t) - (double)remf);
+        tendf = (float)tend;
         tabsf = fabsf((float)t);
         deltaf = (float)((a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny);
         inv_rtolf = (float)(1.0 / a.rtol_of(i));
@@ -653,7 +671,10 @@ struct RkckMixed {
             break;
         default: break;
         }
-        tx = (float)t;
+        if constexpr (SPEC)
+            tx = (float)t;
+        else
+            tx = tendf - remf;
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) x[s] = yh[s] + (b1 * k1[s] + b2 * k2[s] + b3 * k3[s] + b4 * k4[s] + b5 * k5[s]);
     }
@@ -719,12 +740,10 @@ struct RkckMixed {
         if constexpr (SPEC) {
             t = t + h;
         } else if (h >= remf * 0.999999f) {
-            t = tend;  // the step covered what was left
-            remf = 0.0f;
+            remf = reml = 0.0f;  // the step covered what was left
         } else {
-            t = t + (double)h;
-            remf = (float)(tend - t);
-            tabsf = fabsf((float)t);
+            df_sub(remf, reml, h);
+            tabsf = fabsf(tendf - remf);
         }
         const float fac = (err > (float)kErrcon) ? (float)kSafety * fpow(err, (float)kPgrow) : 5.0f;
         if constexpr (SPEC)
@@ -774,10 +793,29 @@ struct RkcMixed {
     using TM = Team<W>;
     using HT = typename Pick<SPEC, double, float>::type;
     typename Model::template Sys<float> sys;
-    float yh[P], yl[P], Fn[P], v[P], d1[P], d2[P];  // d_j = w_j - y_n (d_0 = 0)
+    float yh[P], yl[P], Fn[P], d1[P], d2[P];  // d_j = w_j - y_n (d_0 = 0)
+    // Power-method vector v: touched only in the rare power-method phases,
+    // so for small one-thread systems it lives in shared memory (this
+    // thread's column of a [P][blockDim] array), which frees P registers
+    // for the state the stages use.
+    static constexpr int SMEM_FLOATS = rkc_mixed_smem_floats(W, P);
+    mutable float vreg[SMEM_FLOATS ? 1 : P];
+    float* vs;
+    int vstride;
+    __device__ void bind_smem(float* base, int stride) {
+        vs = base;
+        vstride = stride;
+    }
+    __device__ float& V(int s) const {
+        if constexpr (SMEM_FLOATS > 0)
+            return vs[s * vstride];
+        else
+            return vreg[s];
+    }
     double t, tend;
     HT hmax, hmin, h, h_old, sigma;
     float rtolf, atolf, c3_old, hf, remf, dynrm, sig, inv_nf;  // c3_old = err_old^(1/3)
+    float reml, tendf;  // lean: remaining interval remf + reml, FP32 end time for f(t, y)
     float4 cur;  // (mu_j, nu_j, mu~_j, gamma~_j) of the current stage
     CoefSource cs;
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
@@ -798,6 +836,8 @@ struct RkcMixed {
         t = a.t0_of(i);
         tend = a.tend_of(i);
         remf = (float)(tend - t);
+        reml = (float)((tend - t) - (double)remf);
+        tendf = (float)tend;
         rtolf = (float)a.rtol_of(i);
         atolf = (float)a.atol_of(i);
         mmax = (int)round(sqrt(a.rtol_of(i) / (10.0 * kUround)));
@@ -829,16 +869,20 @@ struct RkcMixed {
     }
     __device__ bool done() const { return phase == PH_DONE; }
 
-    __device__ float sumsq(const TM& tm, const float* x) const {
+    template <class X>
+    __device__ float sumsq(const TM& tm, X x_of) const {
         float acc = 0.0f;
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s)
-            if (sys.comp(tm, s) >= 0) acc = acc + x[s] * x[s];
+            if (sys.comp(tm, s) >= 0) acc = acc + x_of(s) * x_of(s);
         return tm.sum(acc);
     }
 
     __device__ void point(float* x, float& tx) const {
-        tx = (float)t;
+        if constexpr (SPEC)
+            tx = (float)t;
+        else
+            tx = tendf - remf;
         switch (phase) {
         case PH_F0:
 #pragma unroll(P <= 64 ? P : 4)
@@ -846,7 +890,7 @@ struct RkcMixed {
             break;
         case PH_SR:
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) x[s] = v[s];
+            for (int s = 0; s < P; ++s) x[s] = V(s);
             break;
         case PH_TRIAL:
 #pragma unroll(P <= 64 ? P : 4)
@@ -864,7 +908,7 @@ struct RkcMixed {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 Fn[s] = f[s];
-                v[s] = f[s];
+                V(s) = f[s];
             }
             loop_top(a, tm);
             break;
@@ -907,25 +951,26 @@ struct RkcMixed {
 
     // power method in FP32, perturbation scaled by the FP32 sqrt(uround)
     __device__ void sr_begin(const TM& tm) {
-        const float nrm1 = sqrtf(sumsq(tm, yh)), nrm2 = sqrtf(sumsq(tm, v));
+        const float nrm1 = sqrtf(sumsq(tm, [&](int s) { return yh[s]; }));
+        const float nrm2 = sqrtf(sumsq(tm, [&](int s) { return V(s); }));
         if (nrm1 != 0.0f && nrm2 != 0.0f) {
             dynrm = nrm1 * kSqrtUroundF;
             const float sc = dynrm / nrm2;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = yh[s] + v[s] * sc;
+            for (int s = 0; s < P; ++s) V(s) = yh[s] + V(s) * sc;
         } else if (nrm1 != 0.0f) {
             dynrm = nrm1 * kSqrtUroundF;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = yh[s] * (1.0f + kSqrtUroundF);
+            for (int s = 0; s < P; ++s) V(s) = yh[s] * (1.0f + kSqrtUroundF);
         } else if (nrm2 != 0.0f) {
             dynrm = kSqrtUroundF;
             const float sc = dynrm / nrm2;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = v[s] * sc;
+            for (int s = 0; s < P; ++s) V(s) = V(s) * sc;
         } else {
             dynrm = kSqrtUroundF;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = kSqrtUroundF;
+            for (int s = 0; s < P; ++s) V(s) = kSqrtUroundF;
         }
         sig = 0.0f;
         sr_iter = 0;
@@ -944,23 +989,23 @@ struct RkcMixed {
         sig = d / dynrm;
         if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = v[s] - yh[s];
+            for (int s = 0; s < P; ++s) V(s) = V(s) - yh[s];
             sr_end(a);
             return;
         }
         if (d != 0.0f) {
             const float sc = dynrm / d;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = yh[s] + (Fv[s] - Fn[s]) * sc;
+            for (int s = 0; s < P; ++s) V(s) = yh[s] + (Fv[s] - Fn[s]) * sc;
         } else {
             const int ind = sr_iter % n;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
-                if (opaque(sys.comp(tm, s)) == ind) v[s] = yh[s] - (v[s] - yh[s]);
+                if (opaque(sys.comp(tm, s)) == ind) V(s) = yh[s] - (V(s) - yh[s]);
         }
         if (sr_iter == kSpecradItmax) {
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) v[s] = v[s] - yh[s];
+            for (int s = 0; s < P; ++s) V(s) = V(s) - yh[s];
             status |= ODE_ST_SPECRAD_NOCONV;
             sr_end(a);
         }
@@ -1048,7 +1093,11 @@ struct RkcMixed {
         }
         hf = (float)h;
         cs.start(m, a);
-        const float mut1h = (float)cs.mut1() * hf;
+        float mut1h;
+        if constexpr (SPEC)
+            mut1h = (float)cs.mut1() * hf;
+        else
+            mut1h = cs.mut1f() * hf;
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             d2[s] = 0.0f;
@@ -1139,11 +1188,9 @@ struct RkcMixed {
         if constexpr (SPEC) {
             t = t + h;
         } else if (h >= remf * 0.999999f) {
-            t = tend;  // the step covered what was left
-            remf = 0.0f;
+            remf = reml = 0.0f;  // the step covered what was left
         } else {
-            t = t + (double)h;
-            remf = (float)(tend - t);
+            df_sub(remf, reml, h);
         }
         bool bad = false;
         float chk = 0.0f;  // lean form: one finiteness test of a sum per system

@@ -403,11 +403,14 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
     BatchArgs args = a;
     void* params[] = {&args, &ctx};
     const int block = jit_min_blocks() > 1 && c.block > 128 ? 128 : c.block;
+    // the generated model is one thread per system with PER = species count
+    const int smem_floats = method == kMethodRkc && prec != ODE_PREC_FP64 ? rkc_mixed_smem_floats(1, r.net.n_species) : 0;
+    const size_t smem = sizeof(float) * smem_floats * (size_t)block;
     const int64_t threads = a.nsys;  // one thread per system
     cudaError_t e;
     if (c.mapping == ODE_MAP_QUEUE) {
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.kqueue, block, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.kqueue, block, smem);
         if (e != cudaSuccess) {
             *err = std::string("occupancy query: ") + cudaGetErrorString(e);
             return ODE_ERR_CUDA;
@@ -416,10 +419,10 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
         int64_t grid = (int64_t)per_sm * c.sm_count;
         const int64_t need = (threads + block - 1) / block;
         if (grid > need) grid = need;
-        e = cudaLaunchKernel((const void*)k.kqueue, dim3((unsigned)grid), dim3(block), params, 0, c.stream);
+        e = cudaLaunchKernel((const void*)k.kqueue, dim3((unsigned)grid), dim3(block), params, smem, c.stream);
     } else {
         const int64_t grid = (threads + block - 1) / block;
-        e = cudaLaunchKernel((const void*)k.kstatic, dim3((unsigned)grid), dim3(block), params, 0, c.stream);
+        e = cudaLaunchKernel((const void*)k.kstatic, dim3((unsigned)grid), dim3(block), params, smem, c.stream);
     }
     if (e != cudaSuccess) {
         *err = std::string("generated kernel launch: ") + cudaGetErrorString(e);

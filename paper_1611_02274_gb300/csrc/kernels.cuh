@@ -16,6 +16,16 @@
 
 namespace bode {
 
+// Per-thread shared-memory columns of the methods that keep rarely used
+// vectors there (Method::SMEM_FLOATS floats per thread, launched with
+// SMEM_FLOATS * blockDim floats of dynamic shared memory).
+extern __shared__ float bode_dyn_smem[];
+
+template <class Method>
+__device__ __forceinline__ void bind_method_smem(Method& m) {
+    if constexpr (Method::SMEM_FLOATS > 0) m.bind_smem(bode_dyn_smem + threadIdx.x, (int)blockDim.x);
+}
+
 // One system per team, one launch over the batch (the paper's intDriver
 // mapping when the team is one thread), grid rounded up.  Each iteration
 // evaluates the right-hand side once, at the point the system's phase needs.
@@ -28,6 +38,7 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(co
     if (k >= a.nsys) return;  // team-uniform
     const int64_t i = a.sys_of(k);
     Method m;
+    bind_method_smem(m);
     m.init(a, ctx, tm, i);
     R x[P], f[P];
     while (!m.done()) {
@@ -52,6 +63,7 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_queue(con
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
     Method m;
+    bind_method_smem(m);
     int64_t i = 0;
     bool live = false;
     // pull systems until one needs work (a zero-length interval finishes at init)

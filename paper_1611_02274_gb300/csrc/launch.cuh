@@ -32,19 +32,20 @@ template <class Method, class Ctx>
 cudaError_t launch_method(const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c) {
     constexpr int W = Method::W;
     const int block = c.block;
+    const size_t smem = sizeof(float) * Method::SMEM_FLOATS * (size_t)block;
     const int64_t threads = a.nsys * W;
     if (c.mapping == ODE_MAP_QUEUE) {
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue<Method, Ctx>, block, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue<Method, Ctx>, block, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         int64_t grid = (int64_t)per_sm * c.sm_count;
         const int64_t need = (threads + block - 1) / block;
         if (grid > need) grid = need;
-        k_queue<Method, Ctx><<<(unsigned)grid, block, 0, c.stream>>>(a, ctx);
+        k_queue<Method, Ctx><<<(unsigned)grid, block, smem, c.stream>>>(a, ctx);
     } else {
         const int64_t grid = (threads + block - 1) / block;
-        k_static<Method, Ctx><<<(unsigned)grid, block, 0, c.stream>>>(a, ctx);
+        k_static<Method, Ctx><<<(unsigned)grid, block, smem, c.stream>>>(a, ctx);
     }
     return cudaGetLastError();
 }

@@ -128,6 +128,12 @@ struct CoefSource {
         g.start(m);
         return g.mut1;
     }
+    __device__ float mut1f() const {
+        if (e32) return __ldg(e32).z;
+        RkcStageGen g;
+        g.start(m);
+        return (float)g.mut1;
+    }
     __device__ StageCoef recompute(int j) const {
         RkcStageGen g;
         g.start(m);
