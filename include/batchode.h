@@ -144,10 +144,22 @@ typedef struct {
      * the system back to the power method (Appendix). */
     const float* h0;
     const float* sigma0;
-    /* RKC, ODE_PREC_FP64: optional training log [nsys][neq + 3] (device):
+    /* RKC, ODE_PREC_FP64: optional training log [nsys][neq + 4] (device):
      * at each system's first accepted step, log max(|y_k|, 1e-30) for every
-     * component, the parameter, log h and log sigma of that step. */
+     * component, the parameter, log h and log sigma of that step; when the
+     * system finishes, log of its right-hand-side evaluations (n_rhs). */
     float* log_xy;
+    /* Optional per-system cost estimates [nsys] (device, io DEVICE only;
+     * larger = more work, e.g. the previous call's n_rhs or the cost that
+     * ode_mlp_propose predicts; NaN or <= 0 counts as cheapest).  When
+     * given, the systems are taken longest-first: the library sorts them
+     * into 65536 classes spread about log-uniformly over the batch's range
+     * of costs, with its own kernels, and the integration kernel reads them
+     * through that order.  Results do not
+     * depend on the order; only the time does (lanes of a warp then hold
+     * systems of similar cost, and the long ones start first).  Not in the
+     * paper, whose mapping takes the systems in index order. */
+    const float* cost;
 } ode_opts;
 
 /* Per-system outputs, each an array of nsys int32 (device pointers unless
@@ -218,7 +230,7 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
  * and the stats arrays are HOST pointers (pinned memory gives asynchronous
  * copies; y_out may alias y0); opts->io and opts->codegen are ignored (the
  * built-in kernels are used, never run-time generated ones, since loading
- * generated code allocates).  A batch whose staged arrays need more than the
+ * generated code allocates), and so are opts->h0, sigma0, log_xy and cost.  A batch whose staged arrays need more than the
  * scratch offers -- nsys * 8 * (neq + n_params) bytes plus 4 * nsys per
  * requested counter array, each rounded up to 256 bytes, against 16 MiB
  * minus the cursor and table -- is rejected with ODE_ERR_ARG before any GPU
@@ -251,7 +263,8 @@ int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const dou
  * precision / size class; an in-place plan's sample writes to a temporary
  * copy of the state), ODE_MAP_THREAD is the paper's
  * one-thread-per-system mapping with 64-thread blocks, ODE_MAP_QUEUE the
- * default warp-per-system shape.  Families: Brusselator and oscillator
+ * default warp-per-system shape; opts->h0, sigma0, log_xy and cost are
+ * ignored (a plan orders each bucket by system size).  Families: Brusselator and oscillator
  * chains (register each family once with its largest neq).  Layout: system
  * i's components are contiguous from offset[i]. */
 typedef struct {
@@ -284,22 +297,26 @@ int ode_ragged_plan_info(int64_t plan, int32_t* n_buckets, int32_t* desc, int32_
 int ode_ragged_plan_destroy(int64_t plan);
 
 /* ---------------------------------------------------------------------
- * Learned initial step / spectral-radius proposal.  Not in the paper: the
- * paper starts every RKC system with a power-method estimate (Appendix) and
- * an Euler trial step (Section 2.2); this network proposes both from the
- * initial state.  MLP n_in -> 64 -> 64 -> 2 with SiLU, FP32 master weights
- * used as BF16 with FP32 accumulation (CUDA cores), inputs log max(|y_k|,
- * 1e-30) for each component plus the parameter (normalised by statistics
- * of the training set), outputs log h0 and log sigma.  Training minimises
- * squared error on log h0 plus a pinball loss (quantile 0.9) on log sigma,
+ * Learned initial step / spectral-radius / cost proposal.  Not in the
+ * paper: the paper starts every RKC system with a power-method estimate
+ * (Appendix) and an Euler trial step (Section 2.2) and takes the systems in
+ * index order; this network proposes the first two from the initial state
+ * and predicts each system's cost, which orders the batch (ode_opts.cost).
+ * MLP n_in -> 64 -> 64 -> 3 with SiLU, FP32 master weights used as BF16
+ * with FP32 accumulation (CUDA cores), inputs log max(|y_k|, 1e-30) for
+ * each component plus the parameter (normalised by statistics of the
+ * training set), outputs log h0, log sigma and log cost (right-hand-side
+ * evaluations of the whole integration).  Training minimises squared error
+ * on log h0 and log cost plus a pinball loss (quantile 0.9) on log sigma,
  * so sigma leans to over-estimates, with Adam.  Device arrays throughout,
- * rows contiguous (X [n][n_in], Y [n][2]); returns ODE_OK or ODE_ERR_*.
+ * rows contiguous (X [n][n_in], Y [n][3]); returns ODE_OK or ODE_ERR_*.
  * The parameter vector layout: W1 [64][n_in], b1 [64], W2 [64][64],
- * b2 [64], W3 [2][64], b3 [2]; the normalisation block: x_mean, x_scale,
- * x_min, x_max [ODE_MLP_MAX_IN each], y_mean, y_scale [2 each]. */
+ * b2 [64], W3 [3][64], b3 [3]; the normalisation block: x_mean, x_scale,
+ * x_min, x_max [ODE_MLP_MAX_IN each], y_mean, y_scale [3 each]. */
 #define ODE_MLP_HIDDEN 64
 #define ODE_MLP_MAX_IN 33
-#define ODE_MLP_NORM_FLOATS 136
+#define ODE_MLP_OUT 3
+#define ODE_MLP_NORM_FLOATS 138
 
 typedef struct {
     int32_t epochs;   /* passes over the data */
@@ -321,15 +338,27 @@ int ode_mlp_train(int32_t mlp_handle, const float* X, const float* Y, int64_t n,
  * *loss_out (host) = the mean loss; synchronous */
 int ode_mlp_gradient(int32_t mlp_handle, const float* X, const float* Y, int64_t n, float* grad_out,
                      float* loss_out, void* stream);
-/* outputs (log h0, log sigma) for raw feature rows: out [n][2] */
+/* outputs (log h0, log sigma, log cost) for raw feature rows: out [n][3] */
 int ode_mlp_apply(int32_t mlp_handle, const float* X, int64_t n, float* out, void* stream);
 /* proposals for an SoA batch (y0 [neq][nsys], params [1][nsys], FP64): h0 and sigma0 [nsys], NaN where
- * an input lies outside the training range widened by `margin` of its width, or an output is not finite */
+ * an input lies outside the training range widened by `margin` of its width, or an output is not finite;
+ * cost [nsys] (may be NULL): the predicted right-hand-side evaluations, NaN only where not finite */
 int ode_mlp_propose(int32_t mlp_handle, int64_t nsys, int32_t neq, const double* y0, const double* params,
-                    float margin, float* h0, float* sigma0, void* stream);
+                    float margin, float* h0, float* sigma0, float* cost, void* stream);
 /* host copies of the FP32 parameters [num_params] and the normalisation block (either may be NULL) */
 int ode_mlp_get_params(int32_t mlp_handle, float* params, float* norm);
 int ode_mlp_set_params(int32_t mlp_handle, const float* params, const float* norm);
+
+/* The longest-first order that opts->cost gives a batch, on its own:
+ * index [n] (device int32) receives the permutation of 0..n-1 whose cost
+ * classes do not increase.  With lo and hi the smallest and largest bit
+ * pattern (as uint32) of the positive costs, a positive cost c is in class
+ * 1 + (bits(c) - lo) * 65535 / (hi - lo + 1) (integer division; positive
+ * floats order like their bit patterns, which grow about like log2 c), and
+ * NaN and values <= 0 are in class 0.  Systems of one class appear in an
+ * unspecified order.  cost: device [n].  Asynchronous on `stream`;
+ * n <= 2^31 - 1.  No counterpart in the paper. */
+int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream);
 
 /* Forget every cached ODE_MAP_AUTO timing (uniform calls and ragged plans),
  * so that the next such call or plan times its candidates again (after a

@@ -1,18 +1,24 @@
 """FP64 reference of the learned proposal network (test infrastructure only).
 
 Plain numpy restatement of the network and losses the CUDA kernels train:
-inputs normalised by (x - mean) / scale, layers n_in -> 64 -> 64 -> 2 with
-SiLU, outputs de-normalised by y * scale + mean; loss = mean over rows of
-(p0 - t0)^2 + pinball_0.9(t1 - p1) on normalised targets.  The parameter
-vector layout: W1 [64][n_in], b1 [64], W2 [64][64], b2 [64], W3 [2][64],
-b3 [2]; the normalisation block x_mean, x_scale, x_min, x_max [33 each],
-y_mean, y_scale [2 each].
+inputs normalised by (x - mean) / scale, layers n_in -> 64 -> 64 -> 3 with
+SiLU, outputs (log h0, log sigma, log cost) de-normalised by
+y * scale + mean; loss = mean over rows of
+(p0 - t0)^2 + pinball_0.9(t1 - p1) + (p2 - t2)^2 on normalised targets.
+The parameter vector layout: W1 [64][n_in], b1 [64], W2 [64][64], b2 [64],
+W3 [3][64], b3 [3]; the normalisation block x_mean, x_scale, x_min, x_max
+[33 each], y_mean, y_scale [3 each].
 """
 from __future__ import annotations
 
 import numpy as np
 
-H, MAX_IN, OUT, TAU = 64, 33, 2, 0.9
+H, MAX_IN, OUT, TAU = 64, 33, 3, 0.9
+NORM_SIZE = 4 * MAX_IN + 2 * OUT
+
+
+def num_params(n_in):
+    return H * n_in + H + H * H + H + OUT * H + OUT
 
 
 def unpack(params, n_in):
@@ -45,7 +51,7 @@ def silu_grad(z):
 
 
 def forward(params, norm, X):
-    """De-normalised outputs (log h0, log sigma) for raw feature rows X."""
+    """De-normalised outputs (log h0, log sigma, log cost) for raw feature rows X."""
     n_in = X.shape[1]
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in)
     xm, xs, ym, ys = unpack_norm(norm, n_in)
@@ -70,8 +76,9 @@ def loss_and_grad(params, norm, X, Y):
     n = x.shape[0]
     r0 = p[:, 0] - t[:, 0]
     r1 = t[:, 1] - p[:, 1]
-    loss = np.mean(r0 ** 2 + np.where(r1 > 0, TAU * r1, (TAU - 1.0) * r1))
-    g = np.stack([2.0 * r0, np.where(r1 > 0, -TAU, 1.0 - TAU)], axis=1) / n
+    r2 = p[:, 2] - t[:, 2]
+    loss = np.mean(r0 ** 2 + np.where(r1 > 0, TAU * r1, (TAU - 1.0) * r1) + r2 ** 2)
+    g = np.stack([2.0 * r0, np.where(r1 > 0, -TAU, 1.0 - TAU), 2.0 * r2], axis=1) / n
     gW3 = g.T @ a2
     gb3 = g.sum(axis=0)
     d2 = (g @ W3) * silu_grad(z2)

@@ -21,7 +21,7 @@ ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_UNSUPPORTED, ODE_ERR_NOMEM = 
 ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 3
 ODE_ST_SPECRAD_NOCONV = 256
 ODE_ST_PROPOSED = 512
-MLP_HIDDEN, MLP_MAX_IN, MLP_NORM_FLOATS = 64, 33, 136
+MLP_HIDDEN, MLP_MAX_IN, MLP_OUT, MLP_NORM_FLOATS = 64, 33, 3, 138
 ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION = 1, 2, 3, 4
 ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN = 0, 1, 2
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
@@ -33,7 +33,7 @@ EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_inte
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
             "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
-            "ode_ragged_plan_destroy", "ode_tuning_reset"]
+            "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -53,7 +53,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
                 ("codegen", C.c_int32), ("reserved", C.c_int32 * 9),
-                ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p)]
+                ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p), ("cost", C.c_void_p)]
 
 
 class RaggedBatch(C.Structure):
@@ -120,9 +120,10 @@ def load(build_if_missing: bool = True):
     L.ode_mlp_train.argtypes = [C.c_int32, P, P, C.c_int64, C.POINTER(TrainOpts), P, P]
     L.ode_mlp_gradient.argtypes = [C.c_int32, P, P, C.c_int64, P, C.POINTER(C.c_float), P]
     L.ode_mlp_apply.argtypes = [C.c_int32, P, C.c_int64, P, P]
-    L.ode_mlp_propose.argtypes = [C.c_int32, C.c_int64, C.c_int32, P, P, C.c_float, P, P, P]
+    L.ode_mlp_propose.argtypes = [C.c_int32, C.c_int64, C.c_int32, P, P, C.c_float, P, P, P, P]
     L.ode_mlp_get_params.argtypes = [C.c_int32, P, P]
     L.ode_mlp_set_params.argtypes = [C.c_int32, P, P]
+    L.ode_cost_order.argtypes = [P, C.c_int64, P, P]
     _lib = L
     return L
 
@@ -196,9 +197,11 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
               stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO, h0=None, sigma0=None,
-              log_xy=None):
+              log_xy=None, cost=None):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
-    tensor for device io, numpy array for host io); returns y_out."""
+    tensor for device io, numpy array for host io); returns y_out.  log_xy
+    rows are [neq + 4]; cost (float32 [nsys], device) orders the batch
+    longest-first."""
     host = isinstance(y0, np.ndarray)
     nsys = int(y0.shape[1])
     if y_out is None:
@@ -208,7 +211,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.io = ODE_IO_HOST if host else ODE_IO_DEVICE
     o.sync = 1 if sync else 0
     o.codegen = codegen
-    o.h0, o.sigma0, o.log_xy = _ptr(h0), _ptr(sigma0), _ptr(log_xy)
+    o.h0, o.sigma0, o.log_xy, o.cost = _ptr(h0), _ptr(sigma0), _ptr(log_xy), _ptr(cost)
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
@@ -268,8 +271,9 @@ def _stream(stream):
 
 
 class MLP:
-    """The learned h0 / sigma proposal (ode_mlp_*): inputs are torch CUDA
-    tensors, float32, rows contiguous."""
+    """The learned h0 / sigma / cost proposal (ode_mlp_*): inputs are torch
+    CUDA tensors, float32, rows contiguous; targets Y are [n, 3] (log h0,
+    log sigma, log cost)."""
 
     def __init__(self, n_in: int, seed: int = 0):
         h = C.c_int32(0)
@@ -302,18 +306,20 @@ class MLP:
 
     def apply(self, X, stream=None):
         import torch
-        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        out = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
         _check(load().ode_mlp_apply(self.handle, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)))
         return out
 
-    def propose(self, y0, params, margin: float = 0.05, stream=None):
+    def propose(self, y0, params, margin: float = 0.05, stream=None, with_cost: bool = False):
+        """(h0, sigma0) or, with_cost, (h0, sigma0, cost) as float32 [nsys]."""
         import torch
         nsys = int(y0.shape[1])
         h0 = torch.empty(nsys, dtype=torch.float32, device=y0.device)
         s0 = torch.empty(nsys, dtype=torch.float32, device=y0.device)
+        c = torch.empty(nsys, dtype=torch.float32, device=y0.device) if with_cost else None
         _check(load().ode_mlp_propose(self.handle, nsys, int(y0.shape[0]), _ptr(y0), _ptr(params), margin,
-                                      _ptr(h0), _ptr(s0), _stream(stream)))
-        return h0, s0
+                                      _ptr(h0), _ptr(s0), _ptr(c), _stream(stream)))
+        return (h0, s0, c) if with_cost else (h0, s0)
 
     def get_params(self):
         p = np.zeros(self.n_params, dtype=np.float32)
@@ -367,6 +373,14 @@ class RaggedPlan:
         if self.handle:
             _check(load().ode_ragged_plan_destroy(self.handle))
             self.handle = 0
+
+
+def cost_order(cost, stream=None):
+    """Longest-first order (int32 torch tensor) of a float32 CUDA cost vector."""
+    import torch
+    idx = torch.empty(int(cost.shape[0]), dtype=torch.int32, device=cost.device)
+    _check(load().ode_cost_order(_ptr(cost), int(cost.shape[0]), _ptr(idx), _stream(stream)))
+    return idx
 
 
 def tuning_reset() -> None:

@@ -2,6 +2,7 @@
 // validation, workspace, host-buffer staging and kernel dispatch.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,7 @@
 #include "batchode.h"
 #include "jit.h"
 #include "launch.cuh"
+#include "order.h"
 
 using namespace bode;
 
@@ -50,6 +52,14 @@ struct Workspace {
     int next_cursor = 0;
     double* tune_y = nullptr;  // output of mapping-tuning runs, grow-only
     size_t tune_bytes = 0;
+    // cost-ordering buffers per stream (grow-only): calls on one stream run
+    // in order, calls on different streams get their own buffers
+    struct OrderBuf {
+        int32_t* bins = nullptr;
+        int32_t* index = nullptr;
+        int64_t cap = 0;
+    };
+    std::map<cudaStream_t, OrderBuf> order;
     double* tab64 = nullptr;
     float4* tab32 = nullptr;
     void* stage = nullptr;
@@ -289,6 +299,10 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     if (!(rtol > 0.0) || !std::isfinite(rtol)) return fail(ODE_ERR_ARG, "rtol must be finite and > 0");
     if (!(atol >= 0.0) || !std::isfinite(atol)) return fail(ODE_ERR_ARG, "atol must be finite and >= 0");
     if (!std::isfinite(t0) || !std::isfinite(tend) || tend < t0) return fail(ODE_ERR_ARG, "need finite t0 <= tend");
+    if ((opts.h0 == nullptr) != (opts.sigma0 == nullptr)) return fail(ODE_ERR_ARG, "h0 and sigma0 go together");
+    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy || opts.cost))
+        return fail(ODE_ERR_ARG, "proposals, logs and cost ordering need device io");
+    if (opts.cost && nsys > INT32_MAX) return fail(ODE_ERR_ARG, "cost ordering takes at most 2^31 - 1 systems");
     if (nsys == 0) return ODE_OK;
     if (!y0 || !params || !y_out) return fail(ODE_ERR_ARG, "y0, params and y_out must be non-NULL");
 
@@ -358,8 +372,6 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     a.h0 = opts.h0;
     a.sigma0 = opts.sigma0;
     a.log_xy = opts.log_xy;
-    if ((opts.h0 == nullptr) != (opts.sigma0 == nullptr)) return fail(ODE_ERR_ARG, "h0 and sigma0 go together");
-    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy)) return fail(ODE_ERR_ARG, "proposals and logs need device io");
     a.rkc_tab64 = ws->tab64;
     a.rkc_tab32 = ws->tab32;
     a.rkc_tab_max = kRkcTabMax;
@@ -377,6 +389,24 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     if (opts.mapping == ODE_MAP_AUTO) {
         rc = tune_mapping(ws, handle, rhs, meth, opts.precision, use_jit, opts.block_size, a, &cfg);
         if (rc) return rc;
+    }
+    if (opts.cost) {
+        Workspace::OrderBuf& ob = ws->order[stream];
+        if (ob.cap < nsys) {
+            cudaFree(ob.index);
+            ob.index = nullptr;
+            ob.cap = 0;
+            e = cudaMalloc(&ob.index, sizeof(int32_t) * (size_t)nsys);
+            if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "order buffer of %lld systems", (long long)nsys);
+            ob.cap = nsys;
+        }
+        if (!ob.bins) {
+            e = cudaMalloc(&ob.bins, sizeof(int32_t) * kOrderScratchWords);
+            if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "order bins");
+        }
+        e = order_by_cost(opts.cost, nsys, ob.bins, ob.index, ws->sm_count, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cost ordering");
+        a.index = ob.index;
     }
     rc = dispatch(rhs, meth, opts.precision, use_jit, a, cfg);
     if (rc) return rc;
@@ -471,6 +501,25 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
                   double rtol, double atol, const ode_opts* opts, double* y_out, const ode_stats* stats,
                   void* stream) {
     return integrate(kRkc, rhs, nsys, y0, params, t0, tend, rtol, atol, opts, y_out, stats, stream);
+}
+
+int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream_ptr) {
+    g_err.clear();
+    if (n < 0 || n > INT32_MAX) return fail(ODE_ERR_ARG, "n must be in [0, 2^31 - 1]");
+    if (n == 0) return ODE_OK;
+    if (!cost || !index) return fail(ODE_ERR_ARG, "cost and index must be non-NULL");
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace* ws = nullptr;
+    int rc = get_workspace(&ws);
+    if (rc) return rc;
+    Workspace::OrderBuf& ob = ws->order[stream];
+    if (!ob.bins) {
+        cudaError_t e = cudaMalloc(&ob.bins, sizeof(int32_t) * kOrderScratchWords);
+        if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "order bins");
+    }
+    cudaError_t e = order_by_cost(cost, n, ob.bins, index, ws->sm_count, stream);
+    return e == cudaSuccess ? ODE_OK : cuda_fail(e, "cost ordering");
 }
 
 int ode_tuning_reset(void) {

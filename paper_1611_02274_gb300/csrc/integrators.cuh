@@ -546,9 +546,10 @@ struct RkcF64 {
     }
 
     // training record of the first accepted step: features of the initial
-    // state, the parameter, log h and log sigma
+    // state, the parameter, log h and log sigma (row of n + 4 floats; the
+    // last, log n_rhs, is written when the system finishes)
     __device__ void write_log(const BatchArgs& a, const TM& tm) const {
-        float* rec = a.log_xy + idx * (int64_t)(n + 3);
+        float* rec = a.log_xy + idx * (int64_t)(n + 4);
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
@@ -568,6 +569,7 @@ struct RkcF64 {
             if (c >= 0) a.y_out[a.yidx_out(i, c)] = yn[s];
         }
         if (tm.lane == 0) {
+            if (a.log_xy != nullptr && n_acc > 0) a.log_xy[idx * (int64_t)(n + 4) + n + 3] = (float)log((double)(n_rhs + n_sr));
             if (a.n_accept) a.n_accept[i] = n_acc;
             if (a.n_reject) a.n_reject[i] = n_rej;
             if (a.n_rhs) a.n_rhs[i] = n_rhs + n_sr;

@@ -1,13 +1,16 @@
 // mlp.cu -- training and inference kernels of the learned proposal.
 //
 // The network maps the features of a system's initial state (log |y_k| per
-// component and the raw parameter, normalised) to (log h0, log sigma): the
-// first accepted step size and the power-method spectral-radius bound the
-// FP64 solver found for it.  Weights are kept as FP32 masters and used in
+// component and the raw parameter, normalised) to (log h0, log sigma,
+// log cost): the first accepted step size and the power-method
+// spectral-radius bound the FP64 solver found for it, and the number of
+// right-hand-side evaluations the whole integration took (the key that
+// orders a batch longest-first).  Weights are kept as FP32 masters and used in
 // BF16 (round-to-nearest-even) for every forward pass; all sums are FP32.
 //
-// Losses: squared error on log h0; pinball (quantile tau = 0.9) on log sigma,
-// so the network leans to over-estimating sigma -- the stable side for RKC.
+// Losses: squared error on log h0 and log cost; pinball (quantile tau = 0.9)
+// on log sigma, so the network leans to over-estimating sigma -- the stable
+// side for RKC.
 //
 // Kernels:
 //   k_mlp_grad    one block = 64 threads = one thread per hidden neuron,
@@ -86,7 +89,7 @@ __device__ void load_weights(const __nv_bfloat16* w16, float* sw, int np) {
 }
 
 __device__ __forceinline__ float loss_grad(int o, float p, float t, float* loss) {
-    if (o == 0) {
+    if (o != 1) {  // squared error: log h0, log cost
         const float r = p - t;
         *loss += r * r;
         return 2.0f * r;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(kH) k_mlp_grad(const __nv_bfloat16* __restrict
     float* sa1 = sx + kMlpMaxIn;    // layer-1 activations
     float* sa2 = sa1 + kH;          // layer-2 activations
     float* sd2 = sa2 + kH;          // layer-2 deltas
-    float* sg3 = sd2 + kH;          // output gradients (2)
+    float* sg3 = sd2 + kH;          // output gradients (kMlpOut)
     load_weights(w16, sw, np);
     const int j = threadIdx.x;
     const float* W1 = sw + mlp_w1(n_in);
@@ -118,12 +121,14 @@ __global__ void __launch_bounds__(kH) k_mlp_grad(const __nv_bfloat16* __restrict
     const float* B2 = sw + mlp_b2(n_in);
     const float* W3 = sw + mlp_w3(n_in);
     const float* B3 = sw + mlp_b3(n_in);
-    float gW1[kMlpMaxIn], gW2[kH], gB1 = 0.f, gB2 = 0.f, gW3a = 0.f, gW3b = 0.f;
+    float gW1[kMlpMaxIn], gW2[kH], gB1 = 0.f, gB2 = 0.f, gW3[kMlpOut], gB3[kMlpOut];
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) gW3[o] = gB3[o] = 0.f;
 #pragma unroll
     for (int k = 0; k < kMlpMaxIn; ++k) gW1[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < kH; ++k) gW2[k] = 0.f;
-    float gB3a = 0.f, gB3b = 0.f, lsum = 0.f;
+    float lsum = 0.f;
     const int64_t s0 = (int64_t)blockIdx.x * per_block;
     const int64_t s1 = min(n, s0 + per_block);
     for (int64_t q = s0; q < s1; ++q) {
@@ -146,14 +151,15 @@ __global__ void __launch_bounds__(kH) k_mlp_grad(const __nv_bfloat16* __restrict
             sg3[j] = loss_grad(j, z3, t, &lsum);
         }
         __syncthreads();
-        const float g0 = sg3[0], g1 = sg3[1];
-        gW3a += g0 * sa2[j];
-        gW3b += g1 * sa2[j];
-        if (j == 0) {
-            gB3a += g0;
-            gB3b += g1;
+        float back3 = 0.f;
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) {
+            const float g = sg3[o];
+            gW3[o] += g * sa2[j];
+            gB3[o] += g;  // summed by thread 0 only
+            back3 += W3[o * kH + j] * g;
         }
-        const float d2 = (W3[j] * g0 + W3[kH + j] * g1) * silu_grad(z2);
+        const float d2 = back3 * silu_grad(z2);
         sd2[j] = d2;
         gB2 += d2;
 #pragma unroll 8
@@ -173,12 +179,11 @@ __global__ void __launch_bounds__(kH) k_mlp_grad(const __nv_bfloat16* __restrict
 #pragma unroll 8
     for (int k = 0; k < kH; ++k) atomicAdd(grad + mlp_w2(n_in) + j * kH + k, gW2[k]);
     atomicAdd(grad + mlp_b2(n_in) + j, gB2);
-    atomicAdd(grad + mlp_w3(n_in) + j, gW3a);
-    atomicAdd(grad + mlp_w3(n_in) + kH + j, gW3b);
-    if (j == 0) {
-        atomicAdd(grad + mlp_b3(n_in), gB3a);
-        atomicAdd(grad + mlp_b3(n_in) + 1, gB3b);
-    }
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) atomicAdd(grad + mlp_w3(n_in) + o * kH + j, gW3[o]);
+    if (j == 0)
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) atomicAdd(grad + mlp_b3(n_in) + o, gB3[o]);
     if (j < kMlpOut) atomicAdd(loss, lsum);
 }
 
@@ -203,7 +208,7 @@ __global__ void k_to_bf16(const float* master, __nv_bfloat16* w16, int np) {
 }
 
 // Forward pass of one normalised input row; returns the de-normalised
-// outputs (log h0, log sigma).
+// outputs (log h0, log sigma, log cost).
 __device__ void mlp_forward(const float* sw, int n_in, const float* x, const MlpNorm& norm, float* out) {
     const float* W1 = sw + mlp_w1(n_in);
     const float* B1 = sw + mlp_b1(n_in);
@@ -218,17 +223,19 @@ __device__ void mlp_forward(const float* sw, int n_in, const float* x, const Mlp
         for (int k = 0; k < n_in; ++k) z += W1[jj * n_in + k] * x[k];
         a1[jj] = silu(z);
     }
-    float o0 = B3[0], o1 = B3[1];
+    float o[kMlpOut];
+#pragma unroll
+    for (int q = 0; q < kMlpOut; ++q) o[q] = B3[q];
     for (int jj = 0; jj < kH; ++jj) {
         float z = B2[jj];
 #pragma unroll
         for (int k = 0; k < kH; ++k) z += W2[jj * kH + k] * a1[k];
         const float a2 = silu(z);
-        o0 += W3[jj] * a2;
-        o1 += W3[kH + jj] * a2;
+#pragma unroll
+        for (int q = 0; q < kMlpOut; ++q) o[q] += W3[q * kH + jj] * a2;
     }
-    out[0] = o0 * norm.y_scale[0] + norm.y_mean[0];
-    out[1] = o1 * norm.y_scale[1] + norm.y_mean[1];
+#pragma unroll
+    for (int q = 0; q < kMlpOut; ++q) out[q] = o[q] * norm.y_scale[q] + norm.y_mean[q];
 }
 
 // Outputs for feature rows X [n][n_in] (raw features, normalised here).
@@ -245,9 +252,11 @@ __global__ void k_mlp_apply(const __nv_bfloat16* w16, const MlpNorm norm, int n_
 
 // Proposals for an SoA batch: features log max(|y_k|, 1e-30) and the raw
 // parameter; NaN outputs (no proposal) outside the training input box
-// (widened by `margin` of its width) or when not finite.
+// (widened by `margin` of its width) or when not finite.  The predicted
+// cost (optional) is written wherever it is finite.
 __global__ void k_mlp_propose(const __nv_bfloat16* w16, const MlpNorm norm, int n_in, int64_t nsys, int neq,
-                              const double* y0, const double* params, float margin, float* h0, float* sigma0) {
+                              const double* y0, const double* params, float margin, float* h0, float* sigma0,
+                              float* cost) {
     extern __shared__ float sw[];
     load_weights(w16, sw, mlp_nparams(n_in));
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,6 +276,10 @@ __global__ void k_mlp_propose(const __nv_bfloat16* w16, const MlpNorm norm, int 
     const bool ok = inside && isfinite(h) && isfinite(s) && h > 0.f && s > 0.f;
     h0[i] = ok ? h : __int_as_float(0x7fffffff);
     sigma0[i] = ok ? s : __int_as_float(0x7fffffff);
+    if (cost) {
+        const float c = expf(out[2]);
+        cost[i] = isfinite(c) ? c : __int_as_float(0x7fffffff);
+    }
 }
 
 // Per-block partial sums / extrema of the feature and target columns.
@@ -514,7 +527,7 @@ int ode_mlp_apply(int32_t handle, const float* X, int64_t n, float* out, void* s
 }
 
 int ode_mlp_propose(int32_t handle, int64_t nsys, int32_t neq, const double* y0, const double* params, float margin,
-                    float* h0, float* sigma0, void* stream) {
+                    float* h0, float* sigma0, float* cost, void* stream) {
     clear_last_error();
     std::lock_guard<std::mutex> lk(g_mu);
     Mlp* net;
@@ -524,7 +537,7 @@ int ode_mlp_propose(int32_t handle, int64_t nsys, int32_t neq, const double* y0,
     if (!y0 || !params || !h0 || !sigma0 || nsys < 0) return fail(ODE_ERR_ARG, "need device y0, params, h0, sigma0");
     if (nsys == 0) return ODE_OK;
     k_mlp_propose<<<(unsigned)((nsys + 127) / 128), 128, apply_smem(net->n_in), (cudaStream_t)stream>>>(
-        net->w16, net->norm, net->n_in, nsys, neq, y0, params, margin, h0, sigma0);
+        net->w16, net->norm, net->n_in, nsys, neq, y0, params, margin, h0, sigma0, cost);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ODE_OK : cuda_fail(e, "mlp proposal");
 }

@@ -1,5 +1,6 @@
-// mlp.cuh -- the learned step / spectral-radius proposal: a 3-layer MLP
-// (n_in -> 64 -> 64 -> 2, SiLU) with BF16 weights and FP32 accumulation.
+// mlp.cuh -- the learned proposal: a 3-layer MLP (n_in -> 64 -> 64 -> 3,
+// SiLU) with BF16 weights and FP32 accumulation, predicting a system's first
+// step size, spectral-radius bound and integration cost.
 #pragma once
 #include <cstdint>
 
@@ -7,10 +8,10 @@ namespace bode {
 
 constexpr int kMlpHidden = 64;
 constexpr int kMlpMaxIn = 33;  // up to 32 state components + 1 parameter
-constexpr int kMlpOut = 2;     // log h0, log sigma
+constexpr int kMlpOut = 3;     // log h0, log sigma, log cost (right-hand-side evaluations)
 
 // Parameter layout (one flat array): W1 [64][n_in], b1 [64], W2 [64][64],
-// b2 [64], W3 [2][64], b3 [2].
+// b2 [64], W3 [3][64], b3 [3].
 __host__ __device__ constexpr int mlp_w1(int) { return 0; }
 __host__ __device__ constexpr int mlp_b1(int n_in) { return kMlpHidden * n_in; }
 __host__ __device__ constexpr int mlp_w2(int n_in) { return mlp_b1(n_in) + kMlpHidden; }

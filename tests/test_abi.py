@@ -74,7 +74,17 @@ def test_integrate_argument_errors_before_any_launch():
     rc = B.load().rkck_integrate(h, 4, C.c_void_p(y.ctypes.data), C.c_void_p(p.ctypes.data), 0.0, 1.0,
                                  1e-6, 1e-9, C.byref(o), C.c_void_p(y.ctypes.data), None, None)
     assert rc == B.ODE_ERR_ARG
+    # cost ordering, proposals and logs need device arrays
+    cost = np.ones(4, dtype=np.float32)
+    with pytest.raises(B.BatchOdeError) as e:
+        B.integrate("rkck", h, y, p, 0.0, 1.0, 1e-6, 1e-9, cost=cost)
+    assert e.value.code == B.ODE_ERR_ARG
     B.release(h)
+    # the stand-alone order: bad sizes and NULL arrays are refused before any launch
+    L = B.load()
+    assert L.ode_cost_order(None, -1, None, None) == B.ODE_ERR_ARG
+    assert L.ode_cost_order(None, 5, None, None) == B.ODE_ERR_ARG
+    assert L.ode_cost_order(None, 0, None, None) == B.ODE_OK
 
 
 def test_generated_network_kernels_compile():

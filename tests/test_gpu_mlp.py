@@ -1,5 +1,6 @@
 """The learned proposal's kernels against the FP64 reference network, and
-what the trained proposal changes in RKC integration.
+what the trained proposal (first step, spectral radius, cost) changes in RKC
+integration.
 
 Forward outputs and loss gradients are compared with oracle/mlp.py evaluated
 at the BF16-rounded weights the kernels use (FP32 accumulation on the GPU).
@@ -24,16 +25,16 @@ def make_net(n_in=14, seed=3):
     import torch
     rng = np.random.default_rng(seed)
     net = B.MLP(n_in, seed=seed)
-    norm = np.zeros(136, dtype=np.float32)
+    norm = np.zeros(M.NORM_SIZE, dtype=np.float32)
     norm[:n_in] = rng.normal(size=n_in)
     norm[33:33 + n_in] = rng.uniform(0.5, 2.0, size=n_in)
     norm[66:66 + n_in] = -1e30
     norm[99:99 + n_in] = 1e30
-    norm[132:134] = rng.normal(size=2)
-    norm[134:136] = rng.uniform(0.5, 2.0, size=2)
+    norm[132:135] = rng.normal(size=3)
+    norm[135:138] = rng.uniform(0.5, 2.0, size=3)
     net.set_params(norm=norm)
     X = rng.normal(size=(700, n_in)).astype(np.float32)
-    Y = rng.normal(size=(700, 2)).astype(np.float32)
+    Y = rng.normal(size=(700, 3)).astype(np.float32)
     return net, norm, X, Y, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
 
 
@@ -55,7 +56,7 @@ def test_gradient_matches_oracle():
     assert loss == pytest.approx(loss_ref, rel=1e-4)
     assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
     # every block of the parameter vector, not just the norm
-    for lo, hi in [(0, 64 * 14), (64 * 14, 64 * 15), (64 * 15, 64 * 15 + 4096), (params.size - 130, params.size)]:
+    for lo, hi in [(0, 64 * 14), (64 * 14, 64 * 15), (64 * 15, 64 * 15 + 4096), (params.size - 195, params.size)]:
         assert np.linalg.norm(g[lo:hi] - g_ref[lo:hi]) <= 1e-3 * np.linalg.norm(g_ref[lo:hi]) + 1e-9
     net.release()
 
@@ -64,7 +65,8 @@ def test_training_reduces_loss():
     import torch
     rng = np.random.default_rng(7)
     X = rng.normal(size=(20000, 6)).astype(np.float32)
-    Y = np.stack([np.sin(X[:, 0]) + 0.5 * X[:, 1], X[:, 2] * X[:, 3]], axis=1).astype(np.float32)
+    Y = np.stack([np.sin(X[:, 0]) + 0.5 * X[:, 1], X[:, 2] * X[:, 3], np.cos(X[:, 4]) - X[:, 5]],
+                 axis=1).astype(np.float32)
     Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     net = B.MLP(6, seed=1)
     net.fit_normalization(Xt, Yt)
@@ -78,14 +80,15 @@ def test_training_reduces_loss():
     net.release()
 
 
-def log_pairs(w):
-    """(features -> log h, log sigma) of the first accepted step, by the plain FP64 solver."""
+def log_pairs(w, counters=None):
+    """(features -> log h, log sigma of the first accepted step, log n_rhs), by the plain FP64 solver."""
     import torch
     h = B.register_workload(w)
     y0 = torch.from_numpy(w.y0).cuda()
     p = torch.from_numpy(w.params).cuda()
-    log = torch.full((w.nsys, w.neq + 3), float("nan"), dtype=torch.float32, device="cuda")
-    B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, precision=B.ODE_PREC_FP64, log_xy=log, sync=True)
+    log = torch.full((w.nsys, w.neq + 4), float("nan"), dtype=torch.float32, device="cuda")
+    B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, precision=B.ODE_PREC_FP64, log_xy=log,
+                counters=counters, sync=True)
     B.release(h)
     ok = torch.isfinite(log).all(dim=1)
     return log[ok, :w.neq + 1].contiguous(), log[ok, w.neq + 1:].contiguous()
@@ -93,11 +96,17 @@ def log_pairs(w):
 
 def test_training_log_records_the_first_step():
     w = W.massaction(300, seed=41)
-    X, Y = log_pairs(w)
-    assert X.shape[0] == 300
-    X = X.cpu().numpy()
+    cnt = B.counters_like(w.nsys, "cuda")
+    X, Y = log_pairs(w, cnt)
+    assert X.shape[0] == 300 and Y.shape[1] == 3
+    X, Y = X.cpu().numpy(), Y.cpu().numpy()
     np.testing.assert_allclose(X[:, :13], np.log(np.maximum(np.abs(w.y0.T), 1e-30)), rtol=1e-6)
     np.testing.assert_allclose(X[:, 13], w.params[0], rtol=1e-6)
+    # the last column is the log of the system's whole right-hand-side count
+    np.testing.assert_allclose(Y[:, 2], np.log(cnt.n_rhs.cpu().numpy()), rtol=1e-6)
+    # and the oracle takes the same number of evaluations (plain FP64 parity)
+    ref = O.integrate_workload(w)
+    np.testing.assert_array_equal(cnt.n_rhs.cpu().numpy(), ref.n_rhs)
 
 
 def test_proposal_pipeline_gain(record_property):
@@ -113,9 +122,10 @@ def test_proposal_pipeline_gain(record_property):
     h = B.register_workload(w)
     y0 = torch.from_numpy(w.y0).cuda()
     p = torch.from_numpy(w.params).cuda()
-    h0, s0 = net.propose(y0, p)
+    h0, s0, cost = net.propose(y0, p, with_cost=True)
     runs = {}
-    for name, kw in (("plain", {}), ("proposal", dict(h0=h0, sigma0=s0))):
+    for name, kw in (("plain", {}), ("proposal", dict(h0=h0, sigma0=s0)),
+                     ("proposal_ordered", dict(h0=h0, sigma0=s0, cost=cost))):
         cnt = B.counters_like(w.nsys, "cuda")
         y = B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, counters=cnt,
                         precision=B.ODE_PREC_MIXED_LEAN, sync=True, **kw)
@@ -125,7 +135,18 @@ def test_proposal_pipeline_gain(record_property):
     net.release()
     ref = O.integrate_workload(w)
     pr, pl = runs["proposal"], runs["plain"]
+    # taking the systems longest-first changes nothing but the time
+    for k in pr:
+        np.testing.assert_array_equal(runs["proposal_ordered"][k], pr[k], err_msg=k)
+    # the predicted cost tracks the actual one
+    c_pred = np.log(cost.cpu().numpy())
+    c_true = np.log(pr["n_rhs"].astype(np.float64))
+    corr = float(np.corrcoef(c_pred, c_true)[0, 1])
+    record_property("cost_corr", corr)
+    print("log-cost correlation", corr)
+    assert corr > 0.8
     used = np.mean((pr["status"] & B.ODE_ST_PROPOSED) != 0)
+    runs.pop("proposal_ordered")
     rej = {k: float(np.sum(r["n_reject"]) / np.sum(r["n_accept"] + r["n_reject"])) for k, r in runs.items()}
     rhs = {k: float(np.mean(r["n_rhs"])) for k, r in runs.items()}
     sr = {k: float(np.mean(r["n_specrad_iter"])) for k, r in runs.items()}

@@ -6,18 +6,26 @@ import pytest
 from oracle import mlp as M
 
 
+YM, YS = 132, 135  # offsets of y_mean[3] and y_scale[3] in the normalisation block
+
+
 def random_case(n_in=5, n=7, seed=0):
     rng = np.random.default_rng(seed)
-    npar = 64 * n_in + 64 + 64 * 64 + 64 + 2 * 64 + 2
+    npar = 64 * n_in + 64 + 64 * 64 + 64 + 3 * 64 + 3
     params = rng.normal(scale=0.3, size=npar)
-    norm = np.zeros(136)
+    norm = np.zeros(138)
     norm[:n_in] = rng.normal(size=n_in)
     norm[33:33 + n_in] = rng.uniform(0.5, 2.0, size=n_in)
-    norm[132:134] = rng.normal(size=2)
-    norm[134:136] = rng.uniform(0.5, 2.0, size=2)
+    norm[YM:YM + 3] = rng.normal(size=3)
+    norm[YS:YS + 3] = rng.uniform(0.5, 2.0, size=3)
     X = rng.normal(size=(n, n_in))
-    Y = rng.normal(size=(n, 2))
+    Y = rng.normal(size=(n, 3))
     return params, norm, X, Y
+
+
+def test_layout_sizes():
+    assert M.num_params(5) == 64 * 5 + 64 + 64 * 64 + 64 + 3 * 64 + 3
+    assert M.NORM_SIZE == 138
 
 
 def test_gradient_matches_finite_differences():
@@ -36,24 +44,38 @@ def test_gradient_matches_finite_differences():
 
 def test_biases_only_network_outputs_biases():
     n_in = 3
-    params = np.zeros(64 * n_in + 64 + 4096 + 64 + 128 + 2)
-    params[-2:] = [0.7, -1.3]
-    norm = np.zeros(136)
+    params = np.zeros(64 * n_in + 64 + 4096 + 64 + 192 + 3)
+    params[-3:] = [0.7, -1.3, 0.25]
+    norm = np.zeros(138)
     norm[33:36] = 1.0
-    norm[132:134] = [1.0, 2.0]
-    norm[134:136] = [2.0, 3.0]
+    norm[YM:YM + 3] = [1.0, 2.0, -1.0]
+    norm[YS:YS + 3] = [2.0, 3.0, 4.0]
     out = M.forward(params, norm, np.ones((4, n_in)))
-    np.testing.assert_allclose(out, [[0.7 * 2 + 1, -1.3 * 3 + 2]] * 4)
+    np.testing.assert_allclose(out, [[0.7 * 2 + 1, -1.3 * 3 + 2, 0.25 * 4 - 1]] * 4)
+
+
+def test_zero_residual_rows_have_zero_loss_and_gradient():
+    # targets equal to the outputs: every loss term is at its minimum, zero
+    params, norm, X, _ = random_case(n=4)
+    Y = M.forward(params, norm, X)
+    loss, g = M.loss_and_grad(params, norm, X, Y)
+    assert loss == pytest.approx(0.0, abs=1e-12)
+    # the pinball term has a kink at zero residual (subgradient 1 - tau);
+    # the squared terms contribute nothing
+    Y2 = Y.copy()
+    Y2[:, 2] += norm[YS + 2] * 0.5          # log-cost residual of -0.5 normalised
+    loss2, _ = M.loss_and_grad(params, norm, X, Y2)
+    assert loss2 == pytest.approx(0.25)
 
 
 def test_pinball_loss_prefers_overestimates():
     # an over-estimate of log sigma by d costs (1 - tau) d, an under-estimate tau d
     params, norm, X, Y = random_case(n=1)
     p = M.forward(params, norm, X)
-    ys = norm[134:136]
-    base = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1]]]))[0]
-    up = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] - ys[1]]]))[0]
-    down = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] + ys[1]]]))[0]
+    ys = norm[YS:YS + 3]
+    base = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1], p[0, 2]]]))[0]
+    up = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] - ys[1], p[0, 2]]]))[0]
+    down = M.loss_and_grad(params, norm, X, np.array([[p[0, 0], p[0, 1] + ys[1], p[0, 2]]]))[0]
     assert base == pytest.approx(0.0, abs=1e-12)
     assert up == pytest.approx(1 - M.TAU) and down == pytest.approx(M.TAU)
 
