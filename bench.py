@@ -40,6 +40,11 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per system of the chosen kernel, from one ncu
+# capture of k_static<RkcMixed<JitMass, false>> on 262,144 systems of this
+# workload (29.868 MB read + 0.376 MB written); traffic grows with the
+# number of systems (each state is read once and written once)
+NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.868032e6 + 0.37632e6) / 262144
 
 
 def dist_env():
@@ -150,9 +155,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    MAPPING = {"auto": B.ODE_MAP_AUTO, "thread": B.ODE_MAP_THREAD, "queue": B.ODE_MAP_QUEUE}[args.mapping]
+
     def step(prec, counters=None):
         B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
-                    precision=prec, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
+                    precision=prec, mapping=MAPPING, block_size=args.block, stream=stream.cuda_stream)
 
     CHOSEN = B.ODE_PREC_MIXED_LEAN
     for prec in (CHOSEN, B.ODE_PREC_MIXED, B.ODE_PREC_FP64):
@@ -200,16 +207,26 @@ def run_ours(args):
     y_mixed = yout.cpu().numpy()
     flops_mixed = rkc_flops(w, c_mixed["n_accept"], c_mixed["n_reject"], c_mixed["n_rhs"], c_mixed["n_specrad_iter"])
 
-    # the mixed form with the split as specified (FP64 time, step, norm accumulation)
-    ms_mixed64, _ = timed(B.ODE_PREC_MIXED, args.plain_steps, 1)
+    # the kernel the chosen form ran (ODE_MAP_AUTO's choice unless --mapping fixes it)
+    amap, ablock, _ = B.mapping_info(h, "rkc", CHOSEN, block_size=args.block)
+    if MAPPING != B.ODE_MAP_AUTO:
+        amap, ablock = MAPPING, (args.block or 128)
+    kname = ("k_static" if amap == B.ODE_MAP_THREAD else "k_queue") + \
+        f"<RkcMixed<JitMass, false>> (generated network code, lean split; block {ablock})"
 
-    # plain FP64 form on the same inputs
-    ms_plain, _ = timed(B.ODE_PREC_FP64, args.plain_steps, 1)
-    step(B.ODE_PREC_FP64, cnt)
-    torch.cuda.synchronize()
-    c_plain = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
-    y_plain = yout.cpu().numpy()
-    flops_plain = rkc_flops(w, c_plain["n_accept"], c_plain["n_reject"], c_plain["n_rhs"], c_plain["n_specrad_iter"])
+    ms_mixed64 = ms_plain = None
+    c_plain = y_plain = None
+    if args.plain_steps > 0:
+        # the mixed form with the split as specified (FP64 time, step, norm accumulation)
+        ms_mixed64, _ = timed(B.ODE_PREC_MIXED, args.plain_steps, 1)
+
+        # plain FP64 form on the same inputs
+        ms_plain, _ = timed(B.ODE_PREC_FP64, args.plain_steps, 1)
+        step(B.ODE_PREC_FP64, cnt)
+        torch.cuda.synchronize()
+        c_plain = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+        y_plain = yout.cpu().numpy()
+        flops_plain = rkc_flops(w, c_plain["n_accept"], c_plain["n_reject"], c_plain["n_rhs"], c_plain["n_specrad_iter"])
 
     # end to end through the C ABI with pinned host buffers
     hy0 = torch.from_numpy(w.y0).pin_memory()
@@ -220,7 +237,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
-                    precision=CHOSEN, mapping=B.ODE_MAP_AUTO)
+                    precision=CHOSEN, mapping=MAPPING, block_size=args.block)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
@@ -233,7 +250,7 @@ def run_ours(args):
     total_sys = w.nsys * world
     value = total_sys / (ms_chosen * 1e-3)
     achieved = flops_mixed / (ms_chosen * 1e-3) / 1e12
-    achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12
+    achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12 if ms_plain else None
 
     out = {}
     if rank == 0:
@@ -246,20 +263,26 @@ def run_ours(args):
             "data": "synthetic (seeded mass-action network and states; no dataset)",
             "config": {"workload": "massaction-13sp-27rx RKC, 1,048,576 systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
                        "nsys_per_gpu": w.nsys, "method": "rkc",
-                       "form": "chosen: FP32 RHS/stages/step size + Kahan state, FP64 time t, compensated-FP32 "
-                               "error norm, generated network code, persistent queue",
+                       "form": "chosen: FP32 RHS, stages, step size, spectral radius and error norms, Kahan "
+                               "state, remaining interval as an FP32 pair, FP64 coefficient tables, generated "
+                               "network code, mapping chosen by ODE_MAP_AUTO",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
             "rhs_evals_per_s": float(np.sum(c_mixed["n_rhs"])) * world / (ms_chosen * 1e-3),
-            "plain_fp64": {"value": total_sys / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                           "rhs_evals_per_s": float(np.sum(c_plain["n_rhs"])) * world / (ms_plain * 1e-3),
-                           "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
-                           "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
-            "speedup_chosen_vs_plain": ms_plain / ms_chosen,
-            "mixed_spec_split": {"value": total_sys / (ms_mixed64 * 1e-3), "ms_per_step": ms_mixed64,
-                                 "form": "FP32 stages + Kahan state; FP64 time, step size, error-norm accumulation"},
+            "plain_fp64": None if not ms_plain else {
+                "value": total_sys / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                "rhs_evals_per_s": float(np.sum(c_plain["n_rhs"])) * world / (ms_plain * 1e-3),
+                "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
+                "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
+            "speedup_chosen_vs_plain": ms_plain / ms_chosen if ms_plain else None,
+            "mixed_spec_split": None if not ms_mixed64 else {
+                "value": total_sys / (ms_mixed64 * 1e-3), "ms_per_step": ms_mixed64,
+                "form": "FP32 stages + Kahan state; FP64 time, step size, error-norm accumulation"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_queue<RkcMixed<JitMass, false>> (generated network code, lean split)",
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": NCU_TRAFFIC_BYTES_PER_SYSTEM * w.nsys if amap == B.ODE_MAP_THREAD else None,
+                         "traffic_source": "ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by "
+                                           "the system count (null when another kernel ran)",
+                         "kernel": kname,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                          "peak_measured_fma": peak32 / 1e3, "frac_of_measured": achieved / (peak32 / 1e3),
                          "flops_per_launch": flops_mixed},
@@ -270,7 +293,7 @@ def run_ours(args):
             "clocks": clocks,
             "status_ok_frac": float(np.mean((c_mixed["status"] & 0xFF) == 0)),
         }
-        if not args.no_cpu:
+        if not args.no_cpu and c_plain is not None:
             out["cpu_baseline"], acc = cpu_baseline(w, args, y_mixed, y_plain, c_plain)
             out["accuracy_vs_oracle"] = acc
     if args.proposal_nsys > 0:
@@ -413,7 +436,7 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
         ms = e0.elapsed_time(e1) / args.mixed_steps
         res[name] = {"systems_per_s": b.nsys * world / (ms * 1e-3), "ms_per_step": ms,
                      "buckets": [{k: d[k] for k in ("family", "method", "size_class", "systems", "lanes",
-                                                     "points_per_lane", "block")} for d in plan.info()]}
+                                                     "points_per_lane", "block", "mapping")} for d in plan.info()]}
         plan.destroy()
     B.release(hb)
     B.release(hc)
@@ -504,7 +527,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nsys", type=int, default=NSYS)
-    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=3, help="0 skips the plain FP64 and specified-split legs")
+    ap.add_argument("--mapping", choices=["auto", "thread", "queue"], default="auto",
+                    help="mapping of the main leg (fix it under a profiler, whose overhead distorts the "
+                         "timing runs of auto)")
+    ap.add_argument("--block", type=int, default=0, help="block size of the main leg (0: tuned / default)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu", action="store_true")

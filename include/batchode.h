@@ -349,6 +349,14 @@ int ode_mlp_propose(int32_t mlp_handle, int64_t nsys, int32_t neq, const double*
 int ode_mlp_get_params(int32_t mlp_handle, float* params, float* norm);
 int ode_mlp_set_params(int32_t mlp_handle, const float* params, const float* norm);
 
+/* The mapping and block size an ODE_MAP_AUTO call with these options
+ * (method 0 = RKCK, 1 = RKC; precision, codegen and block_size as in
+ * ode_opts) uses on the current device.  Returns ODE_OK when they come from
+ * a timing already made, ODE_ERR_UNSUPPORTED (outputs still set) when the
+ * untuned default would be used, ODE_ERR_HANDLE / ODE_ERR_ARG otherwise. */
+int ode_mapping_info(int32_t rhs_handle, int32_t method, int32_t precision, int32_t codegen, int32_t block_size,
+                     int32_t* mapping, int32_t* block);
+
 /* The longest-first order that opts->cost gives a batch, on its own:
  * index [n] (device int32) receives the permutation of 0..n-1 whose cost
  * classes do not increase.  With lo and hi the smallest and largest bit

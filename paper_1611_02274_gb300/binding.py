@@ -33,7 +33,7 @@ EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_inte
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
             "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
-            "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order"]
+            "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order", "ode_mapping_info"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
     L.ode_mlp_get_params.argtypes = [C.c_int32, P, P]
     L.ode_mlp_set_params.argtypes = [C.c_int32, P, P]
     L.ode_cost_order.argtypes = [P, C.c_int64, P, P]
+    L.ode_mapping_info.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P]
     _lib = L
     return L
 
@@ -381,6 +382,16 @@ def cost_order(cost, stream=None):
     idx = torch.empty(int(cost.shape[0]), dtype=torch.int32, device=cost.device)
     _check(load().ode_cost_order(_ptr(cost), int(cost.shape[0]), _ptr(idx), _stream(stream)))
     return idx
+
+
+def mapping_info(handle: int, method: str, precision: int, codegen: int = ODE_CODEGEN_AUTO, block_size: int = 0):
+    """(mapping, block, tuned) that ODE_MAP_AUTO uses for these options."""
+    m, b = C.c_int32(0), C.c_int32(0)
+    rc = load().ode_mapping_info(handle, 0 if method == "rkck" else 1, precision, codegen, block_size,
+                                 C.byref(m), C.byref(b))
+    if rc not in (ODE_OK, ODE_ERR_UNSUPPORTED):
+        _check(rc)
+    return int(m.value), int(b.value), rc == ODE_OK
 
 
 def tuning_reset() -> None:

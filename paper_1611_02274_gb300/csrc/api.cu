@@ -503,6 +503,32 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
     return integrate(kRkc, rhs, nsys, y0, params, t0, tend, rtol, atol, opts, y_out, stats, stream);
 }
 
+int ode_mapping_info(int32_t rhs_handle, int32_t method, int32_t precision, int32_t codegen, int32_t block_size,
+                     int32_t* mapping, int32_t* block) {
+    g_err.clear();
+    if (!mapping || !block) return fail(ODE_ERR_ARG, "mapping and block must be non-NULL");
+    if (method != 0 && method != 1) return fail(ODE_ERR_ARG, "method must be 0 (RKCK) or 1 (RKC)");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_reg.find(rhs_handle);
+    if (it == g_reg.end()) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    const bool use_jit = it->second.kind == ODE_RHS_MASSACTION &&
+                         (codegen == ODE_CODEGEN_ON || (codegen == ODE_CODEGEN_AUTO && jit_available()));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int meth = method == 0 ? kMethodRkck : kMethodRkc;
+    auto t = g_map_tuned.find(std::make_tuple(rhs_handle, meth, precision, (int)use_jit, dev, block_size));
+    LaunchCfg cfg;
+    if (t != g_map_tuned.end()) {
+        cfg.mapping = t->second.first;
+        cfg.block = t->second.second;
+    } else {
+        default_mapping(&cfg, block_size);
+    }
+    *mapping = cfg.mapping;
+    *block = cfg.block;
+    return t != g_map_tuned.end() ? ODE_OK : ODE_ERR_UNSUPPORTED;
+}
+
 int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream_ptr) {
     g_err.clear();
     if (n < 0 || n > INT32_MAX) return fail(ODE_ERR_ARG, "n must be in [0, 2^31 - 1]");
