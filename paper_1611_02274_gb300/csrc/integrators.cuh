@@ -59,6 +59,7 @@ __device__ __forceinline__ void df_sub(float& hi, float& lo, float b) {
 
 template <class Model>
 struct RkckF64 {
+    static constexpr bool kStepSync = false;  // fixed six stages: lanes stay aligned
     static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
@@ -240,6 +241,7 @@ struct RkckF64 {
 
 template <class Model>
 struct RkcF64 {
+    static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
     static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
@@ -282,6 +284,8 @@ struct RkcF64 {
         phase = PH_F0;  // F_n = f(t0, y0)
     }
     __device__ bool done() const { return phase == PH_DONE; }
+    __device__ bool in_stages() const { return phase == PH_STAGE; }
+    __device__ bool at_step_end() const { return phase == PH_FINAL; }
 
     __device__ double sumsq(const TM& tm, const double* x) const {
         double sq[P];
@@ -602,6 +606,7 @@ struct SumF2 {
 // FP32 and a step that reaches the end of the interval lands on tend exactly.
 template <class Model, bool SPEC = true>
 struct RkckMixed {
+    static constexpr bool kStepSync = false;  // fixed six stages: lanes stay aligned
     static constexpr int SMEM_FLOATS = 0;
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
@@ -790,6 +795,7 @@ struct RkckMixed {
 // and norms in FP32.
 template <class Model, bool SPEC = true>
 struct RkcMixed {
+    static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
     using TM = Team<W>;
@@ -870,6 +876,8 @@ struct RkcMixed {
         phase = PH_F0;
     }
     __device__ bool done() const { return phase == PH_DONE; }
+    __device__ bool in_stages() const { return phase == PH_STAGE; }
+    __device__ bool at_step_end() const { return phase == PH_FINAL; }
 
     template <class X>
     __device__ float sumsq(const TM& tm, X x_of) const {

@@ -26,28 +26,66 @@ __device__ __forceinline__ void bind_method_smem(Method& m) {
     if constexpr (Method::SMEM_FLOATS > 0) m.bind_smem(bode_dyn_smem + threadIdx.x, (int)blockDim.x);
 }
 
+// Step-end hold (methods with a variable stage count, Method::kStepSync):
+// a system whose stages are done and whose next evaluation closes the step
+// (F_{n+1}, then the error test and the next step's set-up) waits while
+// any system of the warp is still in its stages.  The step-closing work
+// then runs once for all lanes that reached it, instead of once per lane
+// in different iterations; the price is idle evaluation slots of the lanes
+// with fewer stages.  Every iteration in which a lane is in its stages
+// advances that lane, so the hold always ends.  The arithmetic of each
+// system is unchanged.
+template <class Method>
+__device__ __forceinline__ bool step_hold(const Method& m, bool live) {
+    if constexpr (Method::kStepSync && Method::W < 32) {
+        const bool staging = __any_sync(0xffffffffu, live && m.in_stages());
+        return live && staging && m.at_step_end();
+    } else {
+        return false;
+    }
+}
+
 // One system per team, one launch over the batch (the paper's intDriver
 // mapping when the team is one thread), grid rounded up.  Each iteration
 // evaluates the right-hand side once, at the point the system's phase needs.
+// Lanes past the end of the batch stay in the loop (inactive) so that the
+// warp votes see every lane.
 template <class Method, class Ctx>
 __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-    if (k >= a.nsys) return;  // team-uniform
-    const int64_t i = a.sys_of(k);
+    const bool in_range = k < a.nsys;  // team-uniform
     Method m;
     bind_method_smem(m);
-    m.init(a, ctx, tm, i);
-    R x[P], f[P];
-    while (!m.done()) {
-        R tx;
-        m.point(x, tx);
-        m.sys.rhs(tm, tx, x, f);
-        m.consume(a, tm, x, f);
+    int64_t i = 0;
+    if (in_range) {
+        i = a.sys_of(k);
+        m.init(a, ctx, tm, i);
     }
-    m.store(a, tm, i);
+    R x[P], f[P];
+    if constexpr (Method::kStepSync && W < 32) {
+        for (;;) {
+            const bool live = in_range && !m.done();
+            if (!__any_sync(0xffffffffu, live)) break;
+            const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
+            if (live && !hold) {
+                R tx;
+                m.point(x, tx);
+                m.sys.rhs(tm, tx, x, f);
+                m.consume(a, tm, x, f);
+            }
+        }
+    } else if (in_range) {  // one team per warp, or a fixed stage count: nothing to hold for
+        while (!m.done()) {
+            R tx;
+            m.point(x, tx);
+            m.sys.rhs(tm, tx, x, f);
+            m.consume(a, tm, x, f);
+        }
+    }
+    if (in_range) m.store(a, tm, i);
 }
 
 // Persistent kernel: each team pulls a system index from the queue cursor;
@@ -83,7 +121,8 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_queue(con
     next();
     R x[P], f[P];
     while (__any_sync(0xffffffffu, live)) {
-        if (live) {
+        const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
+        if (live && !hold) {
             R tx;
             m.point(x, tx);
             m.sys.rhs(tm, tx, x, f);
