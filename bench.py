@@ -41,10 +41,10 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per system of the chosen kernel, from one ncu
-# capture of k_static<RkcMixed<JitMass, false>> on 262,144 systems of this
-# workload (29.868 MB read + 0.376 MB written); traffic grows with the
-# number of systems (each state is read once and written once)
-NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.868032e6 + 0.37632e6) / 262144
+# capture of k_static<RkcMixed<JitMass, false>> (step-end hold) on 262,144
+# systems of this workload (29.584 MB read + 0.342 MB written); traffic
+# grows with the number of systems (each state is read once, written once)
+NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.584128e6 + 0.34176e6) / 262144
 
 
 def dist_env():
