@@ -45,6 +45,21 @@
  *   R10 Powers in the step-size rules and the Arrhenius rate use the series
  *       logarithm / exponential below, a fixed sequence of correctly
  *       rounded operations, so their values are reproducible bit for bit.
+ *   R21 Warm restart (the outer global-step loop of Section 3, where the
+ *       paper notes that carrying step information from one global step to
+ *       the next could help but restarts every call): an optional carry
+ *       state per system, CARRY_WORDS(neq) doubles -- valid flag, time
+ *       reached, h (the controller's next step), sigma, h_old, err_old,
+ *       accepted-step count, count at the last spectral-radius estimate,
+ *       rejected flag, eigenvector v (RKC; RKCK uses the flag, time and h).
+ *       A call given a valid carry resumes the step-size controller and the
+ *       25-step spectral-radius schedule where the previous call left
+ *       them, instead of the power method and the trial step; F(t0, y0) is
+ *       evaluated again.  The carry is written when the system ends, valid
+ *       unless the state is unusable (H_UNDERFLOW, NONFINITE).  A run
+ *       stopped by the attempt cap and continued this way repeats the
+ *       uninterrupted run step for step, wherever the per-call quantities
+ *       hmax = |tend - t0| and hmin do not bind.
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,6 +89,9 @@
 #define KIND_MASSACTION 4
 #define KIND_LINEAR 100    /* f = A y, A row-major in the params (tests only) */
 #define KIND_TIME 101      /* f_i = t (tests of the stage times only) */
+
+#define CARRY_FIXED 9
+#define CARRY_WORDS(neq) (CARRY_FIXED + (neq))
 
 #define OR_MAX_REAC 64
 #define OR_MAX_PARAMS 300
@@ -353,7 +371,8 @@ typedef struct {
 /* Adaptive RKCK for one system (rkckDriver of Section 3.1 with R1, R2, R8).
  * y holds y(t0) on entry and the final state on exit. */
 static void rkck_system(const or_sys* s, double t, double tend, double rtol, double atol,
-                        int max_attempts, double* y, or_counts* cnt) {
+                        int max_attempts, double* y, or_counts* cnt, const double* carry_in,
+                        double* carry_out) {
     int n = s->neq;
     double* mem = (double*)malloc(sizeof(double) * (size_t)n * 11);
     double* F = mem;
@@ -364,6 +383,7 @@ static void rkck_system(const or_sys* s, double t, double tend, double rtol, dou
     const double hmin = 1.0e-20;
     const double delta = (atol > 0.0) ? atol / rtol : TINY;
     double h = 0.5 * fabs(tend - t);
+    if (carry_in && carry_in[0] == 1.0 && carry_in[2] > 0.0) h = carry_in[2];  /* R21 */
     memset(cnt, 0, sizeof(*cnt));
     while (t < tend) {
         if (cnt->n_accept + cnt->n_reject >= max_attempts) {
@@ -405,6 +425,12 @@ static void rkck_system(const or_sys* s, double t, double tend, double rtol, dou
                 break;
             }
         }
+    }
+    if (carry_out) {
+        for (int w = 0; w < CARRY_WORDS(n); ++w) carry_out[w] = 0.0;
+        carry_out[0] = (cnt->status == ST_OK || cnt->status == ST_MAX_ATTEMPTS) ? 1.0 : 0.0;
+        carry_out[1] = t;
+        carry_out[2] = h;
     }
     free(mem);
 }
@@ -550,7 +576,8 @@ static double rkc_specrad(const or_sys* s, double t, const double* y, const doub
 /* Adaptive RKC for one system (rkcDriver of Section 3.2 with R1, R4-R9).
  * y holds y(t0) on entry and the final state on exit. */
 static void rkc_system(const or_sys* s, double t, double tend, double rtol, double atol,
-                       int max_attempts, double* y, or_counts* cnt) {
+                       int max_attempts, double* y, or_counts* cnt, const double* carry_in,
+                       double* carry_out) {
     int n = s->neq;
     double* mem = (double*)malloc(sizeof(double) * (size_t)n * 10);
     double* yn = mem;
@@ -575,6 +602,17 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
 
     int num_step = 0;
     int have_sigma = 0, rejected = 0, sr_step = -1;
+    if (carry_in && carry_in[0] == 1.0) {  /* R21: resume the controller */
+        h = carry_in[2];
+        sigma = carry_in[3];
+        h_old = carry_in[4];
+        err_old = carry_in[5];
+        num_step = (int)carry_in[6];
+        sr_step = (int)carry_in[7];
+        rejected = (int)carry_in[8];
+        for (int i = 0; i < n; ++i) v[i] = carry_in[CARRY_FIXED + i];
+        have_sigma = 1;
+    }
     while (t < tend) {
         if (cnt->n_accept + cnt->n_reject >= max_attempts) {
             cnt->status |= ST_MAX_ATTEMPTS;
@@ -669,6 +707,19 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
     }
     cnt->n_rhs += cnt->n_specrad_iter;
     for (int i = 0; i < n; ++i) y[i] = yn[i];
+    if (carry_out) {
+        const int st = cnt->status & 0xFF;
+        carry_out[0] = (st == ST_OK || st == ST_MAX_ATTEMPTS) && have_sigma ? 1.0 : 0.0;
+        carry_out[1] = t;
+        carry_out[2] = h;
+        carry_out[3] = sigma;
+        carry_out[4] = h_old;
+        carry_out[5] = err_old;
+        carry_out[6] = (double)num_step;
+        carry_out[7] = (double)sr_step;
+        carry_out[8] = (double)rejected;
+        for (int i = 0; i < n; ++i) carry_out[CARRY_FIXED + i] = v[i];
+    }
     free(mem);
 }
 
@@ -690,10 +741,12 @@ static void gather(const double* src, int64_t nsys, int64_t i, int n, double* ds
 
 /* Batched integration of a uniform batch (SoA [neq][nsys] in and out).
  * method 0 = RKCK, 1 = RKC.  Counters are per system and may be NULL. */
+/* carry_in / carry_out (R21, may be NULL): SoA [CARRY_WORDS(neq)][nsys]. */
 int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* y0,
                      const double* params, double t0, double tend, double rtol, double atol,
                      int max_attempts, double* y_out, int32_t* n_accept, int32_t* n_reject,
-                     int32_t* n_rhs, int32_t* n_specrad_iter, int32_t* status, int nthreads) {
+                     int32_t* n_rhs, int32_t* n_specrad_iter, int32_t* status, int nthreads,
+                     const double* carry_in, double* carry_out) {
     if (m->neq <= 0 || m->n_params > OR_MAX_PARAMS) return -1;
     int nt = resolve_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
@@ -704,12 +757,24 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
         sys_init(&s, m, m->neq, p, m->n_params);
         double* y = (double*)malloc(sizeof(double) * (size_t)m->neq);
         gather(y0, nsys, i, m->neq, y);
+        const int K = CARRY_WORDS(m->neq);
+        double* cin = NULL;
+        double* cout = NULL;
+        if (carry_in) {
+            cin = (double*)malloc(sizeof(double) * (size_t)K);
+            gather(carry_in, nsys, i, K, cin);
+        }
+        if (carry_out) cout = (double*)malloc(sizeof(double) * (size_t)K);
         or_counts cnt;
         if (method == 0)
-            rkck_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt);
+            rkck_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout);
         else
-            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt);
+            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout);
         for (int j = 0; j < m->neq; ++j) y_out[i + nsys * (int64_t)j] = y[j];
+        if (cout)
+            for (int w = 0; w < K; ++w) carry_out[i + nsys * (int64_t)w] = cout[w];
+        free(cin);
+        free(cout);
         if (n_accept) n_accept[i] = cnt.n_accept;
         if (n_reject) n_reject[i] = cnt.n_reject;
         if (n_rhs) n_rhs[i] = cnt.n_rhs;
@@ -739,9 +804,9 @@ int oracle_integrate_ragged(const or_model* models, const int32_t* model_idx, in
         for (int j = 0; j < neq[i]; ++j) y[j] = y0[offset[i] + j];
         or_counts cnt;
         if (method[i] == 0)
-            rkck_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt);
+            rkck_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL);
         else
-            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt);
+            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL);
         if (n_accept) n_accept[i] = cnt.n_accept;
         if (n_reject) n_reject[i] = cnt.n_reject;
         if (n_rhs) n_rhs[i] = cnt.n_rhs;

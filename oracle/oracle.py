@@ -16,6 +16,11 @@ MAX_REAC = 64
 KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION = 1, 2, 3, 4
 KIND_LINEAR, KIND_TIME = 100, 101
 ST_OK, ST_H_UNDERFLOW, ST_MAX_ATTEMPTS, ST_NONFINITE, ST_SPECRAD_NOCONV = 0, 1, 2, 3, 256
+CARRY_FIXED = 9   # warm-restart state: valid, t, h, sigma, h_old, err_old, num_step, sr_step, rejected; then v
+
+
+def carry_words(neq: int) -> int:
+    return CARRY_FIXED + neq
 
 
 class Model(C.Structure):
@@ -41,7 +46,7 @@ def lib():
         L = C.CDLL(path)
         P = C.c_void_p
         L.oracle_integrate.argtypes = [P, C.c_int, C.c_int64, P, P, C.c_double, C.c_double,
-                                       C.c_double, C.c_double, C.c_int, P, P, P, P, P, P, C.c_int]
+                                       C.c_double, C.c_double, C.c_int, P, P, P, P, P, P, C.c_int, P, P]
         L.oracle_integrate_ragged.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int,
                                               P, P, P, P, P, P, C.c_int]
         L.oracle_rhs.argtypes = [P, P, C.c_double, P, P]
@@ -108,22 +113,31 @@ class Result:
     n_rhs: np.ndarray
     n_specrad_iter: np.ndarray
     status: np.ndarray
+    carry: np.ndarray | None = None
 
 
 def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
-              max_attempts: int = 1_000_000, nthreads: int = 0) -> Result:
-    """Integrate a uniform SoA batch y0[neq, nsys]; method 0 = RKCK, 1 = RKC."""
+              max_attempts: int = 1_000_000, nthreads: int = 0, carry_in=None,
+              carry_out: bool = False) -> Result:
+    """Integrate a uniform SoA batch y0[neq, nsys]; method 0 = RKCK, 1 = RKC.
+    carry_in (SoA [carry_words(neq), nsys]) resumes a previous call's
+    controller state; carry_out returns this call's in ``Result.carry``."""
     y0 = _f64(y0)
     params = _f64(params)
     nsys = y0.shape[1]
     assert y0.shape[0] == m.neq and params.shape == (m.n_params, nsys)
     y = np.empty_like(y0)
     c = [np.zeros(nsys, dtype=np.int32) for _ in range(5)]
+    cin = None if carry_in is None else _f64(carry_in)
+    if cin is not None:
+        assert cin.shape == (carry_words(m.neq), nsys)
+    cout = np.zeros((carry_words(m.neq), nsys)) if carry_out else None
     rc = lib().oracle_integrate(C.byref(m), method, nsys, _p(y0), _p(params), t0, tend, rtol,
-                                atol, max_attempts, _p(y), *[_p(a) for a in c], nthreads)
+                                atol, max_attempts, _p(y), *[_p(a) for a in c], nthreads,
+                                _p(cin) if cin is not None else None, _p(cout) if cout is not None else None)
     if rc != 0:
         raise ValueError(f"oracle_integrate failed ({rc})")
-    return Result(y, *c)
+    return Result(y, *c, carry=cout)
 
 
 def integrate_workload(w, nthreads: int = 0, max_attempts: int = 1_000_000) -> Result:
