@@ -304,6 +304,10 @@ def run_ours(args):
         mixed = mixed_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
             out["mixed_batch"] = mixed
+    if args.split_steps > 0:
+        split = split_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["global_steps"] = split
     if rank == 0:
         print(json.dumps(out), flush=True)
     B.release(h)
@@ -402,6 +406,98 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
                                 "FP32 accumulate"}
     res["speedup_with_proposal"] = res["without"]["ms_per_step"] / res["with_proposal"]["ms_per_step"]
     res["speedup_with_proposal_ordered"] = res["without"]["ms_per_step"] / res["with_proposal_ordered"]["ms_per_step"]
+    return res
+
+
+def split_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The paper's outer loop (Section 3): the mass-action batch integrated
+    over [0, 1e-4] as G global steps, one rkc_integrate call each, states
+    resident on the device.  cold = every call restarts (the paper's
+    driver); warm_continue / warm_restart = the controller state carried
+    across calls (ode_opts.carry, carry modes CONTINUE / RESTART); *_ordered
+    = also taking each call's systems longest-first by the previous call's
+    n_rhs counters.  One repetition of all G calls is one timed step."""
+    import torch.distributed as dist
+    import oracle as O
+    w = W.massaction(nsys=args.nsys, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    y = torch.empty_like(y0)
+    carry = B.carry_like(w.neq, w.nsys, dev)
+    cnt = B.counters_like(w.nsys, dev)
+    CH = B.ODE_PREC_MIXED_LEAN
+    B.prepare(h, "rkc", CH)
+    edges = np.linspace(w.t0, w.tend, args.split_steps + 1)
+
+    def chain(mode, total=None):
+        for g, (t_a, t_b) in enumerate(zip(edges[:-1], edges[1:])):
+            kw = {}
+            if mode.startswith("warm"):
+                kw["carry"] = carry
+                kw["carry_mode"] = B.ODE_CARRY_RESTART if "restart" in mode else B.ODE_CARRY_CONTINUE
+            if mode.endswith("ordered") and g > 0:
+                kw["cost"] = cnt.n_rhs
+            B.integrate("rkc", h, y, p, float(t_a), float(t_b), w.rtol, w.atol, y_out=y, counters=cnt,
+                        precision=CH, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream, **kw)
+            if total is not None:
+                torch.cuda.synchronize()
+                total += cnt.n_rhs.cpu().numpy()
+
+    res = {}
+    MODES = ("cold", "cold_ordered", "warm_continue", "warm_restart", "warm_restart_ordered")
+    for mode in MODES:
+        ms = []
+        for rep in range(1 + args.split_reps):   # the first repetition warms up (and tunes the mapping)
+            y.copy_(y0)
+            carry.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            chain(mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                ms.append(e0.elapsed_time(e1))
+        t = float(np.mean(ms))
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        # counts and the final state of one more chain
+        y.copy_(y0)
+        carry.zero_()
+        total = np.zeros(w.nsys, np.int64)
+        chain(mode, total)
+        res[mode] = {"systems_per_s": w.nsys * world / (t * 1e-3), "ms_per_chain": t,
+                     "mean_rhs": float(total.mean()), "y_sample": y[:, :2048].cpu().numpy()}
+    B.release(h)
+    # accuracy: the oracle's own chain (same mode of restart) and its single call, on 2048 systems
+    ws = W.subset(w, np.arange(2048))
+    m = O.model_for(ws)
+    ref_single = O.integrate_workload(ws)
+    ref_chain = {}
+    for kind in ("cold", "continue", "restart"):
+        ys, c = ws.y0.copy(), None
+        for t_a, t_b in zip(edges[:-1], edges[1:]):
+            r = O.integrate(m, 1, ys, ws.params, float(t_a), float(t_b), ws.rtol, ws.atol,
+                            carry_in=c if kind != "cold" else None, carry_out=True,
+                            carry_mode=O.CARRY_RESTART if kind == "restart" else O.CARRY_CONTINUE)
+            ys, c = r.y, r.carry
+        ref_chain[kind] = ys
+    for mode, r in res.items():
+        ys = r.pop("y_sample")
+        rc = ref_chain["cold" if mode.startswith("cold") else ("restart" if "restart" in mode else "continue")]
+        e_chain = (np.abs(ys - rc) / (np.abs(rc) + w.atol)).max(axis=0)
+        e_single = (np.abs(ys - ref_single.y) / (np.abs(ref_single.y) + w.atol)).max(axis=0)
+        r["err_vs_oracle_chain_p999"] = float(np.quantile(e_chain, 0.999))
+        r["err_vs_single_call_p999"] = float(np.quantile(e_single, 0.999))
+    res["speedup_vs_cold"] = {m: res["cold"]["ms_per_chain"] / res[m]["ms_per_chain"] for m in MODES}
+    res["config"] = {"nsys_per_gpu": w.nsys, "global_steps": args.split_steps, "interval": [w.t0, w.tend],
+                     "timed": f"{args.split_reps} repetitions of the whole chain after one warm-up repetition",
+                     "precision": "mixed lean", "state": "device resident (the paper copies each global step)"}
     return res
 
 
@@ -541,6 +637,8 @@ def main():
     ap.add_argument("--proposal-epochs", type=int, default=24)
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)
+    ap.add_argument("--split-steps", type=int, default=10, help="global steps of the outer-loop leg (0 skips it)")
+    ap.add_argument("--split-reps", type=int, default=2)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # at least three untimed warm-up steps
     if args.impl == "reference":

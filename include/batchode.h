@@ -135,7 +135,9 @@ typedef struct {
     int32_t io;            /* ODE_IO_DEVICE or ODE_IO_HOST */
     int32_t sync;          /* nonzero: synchronise the stream before returning */
     int32_t codegen;       /* ODE_CODEGEN_* (default AUTO) */
-    int32_t reserved[9];   /* must be zero */
+    int32_t cost_kind;     /* element type of `cost`: 0 = float32, 1 = int32 (e.g. a previous n_rhs) */
+    int32_t carry_mode;    /* ODE_CARRY_CONTINUE (default) or ODE_CARRY_RESTART, see `carry` */
+    int32_t reserved[7];   /* must be zero */
     /* RKC, mixed precisions: optional per-system proposals [nsys] (device
      * arrays, NaN = none) of the initial step and the spectral-radius bound,
      * e.g. from ode_mlp_propose.  A system with a finite positive pair skips
@@ -150,8 +152,9 @@ typedef struct {
      * system finishes, log of its right-hand-side evaluations (n_rhs). */
     float* log_xy;
     /* Optional per-system cost estimates [nsys] (device, io DEVICE only;
-     * larger = more work, e.g. the previous call's n_rhs or the cost that
-     * ode_mlp_propose predicts; NaN or <= 0 counts as cheapest).  When
+     * float32 or, with cost_kind = 1, int32; larger = more work, e.g. the
+     * previous call's n_rhs counters or the cost that ode_mlp_propose
+     * predicts; NaN or <= 0 counts as cheapest).  When
      * given, the systems are taken longest-first: the library sorts them
      * into 65536 classes spread about log-uniformly over the batch's range
      * of costs, with its own kernels, and the integration kernel reads them
@@ -160,7 +163,38 @@ typedef struct {
      * systems of similar cost, and the long ones start first).  Not in the
      * paper, whose mapping takes the systems in index order. */
     const float* cost;
+    /* Optional warm-restart state, read and written (device, io DEVICE only;
+     * SoA: word w of system i at carry[i + nsys * w], ODE_CARRY_WORDS(neq)
+     * words per system).  The paper's outer loop (Section 3) calls the
+     * integrator once per global step and every call restarts cold; it
+     * notes that carrying step information across calls could help.  Words:
+     * 0 valid flag (1.0 = usable), 1 time reached, 2 the controller's next
+     * step size h, 3 sigma, 4 h_old, 5 err_old, 6 accepted-step count, 7 the
+     * count at the last spectral-radius estimate, 8 rejected flag (RKC; RKCK
+     * uses words 0-2 and writes zeros elsewhere), then the power-method
+     * eigenvector v (neq words, RKC).  A system whose carry is valid resumes
+     * the step-size controller and the 25-step spectral-radius schedule
+     * instead of running the power method and the trial step; F(t0, y0) is
+     * evaluated again.  On return every system's carry is written (valid
+     * unless it ended in H_UNDERFLOW or NONFINITE); zero the array for a
+     * cold start.  carry_mode ODE_CARRY_CONTINUE resumes everything: a run
+     * stopped by the attempt cap and continued from the time it reached
+     * repeats the uninterrupted run step for step.  ODE_CARRY_RESTART keeps
+     * the controller (h, h_old, err_old) and the eigenvector but estimates
+     * sigma again at the start of the call (from the carried eigenvector,
+     * so in few iterations) and counts the 25-step schedule from there --
+     * the choice for operator splitting, where the state changes between
+     * calls, and faster in a batch: the lanes of a warp then re-estimate
+     * together instead of at scattered steps.  The error test judges every
+     * step either way. */
+    double* carry;
 } ode_opts;
+
+#define ODE_CARRY_CONTINUE 0
+#define ODE_CARRY_RESTART 1
+
+#define ODE_CARRY_FIXED 9
+#define ODE_CARRY_WORDS(neq) ((neq) + ODE_CARRY_FIXED)
 
 /* Per-system outputs, each an array of nsys int32 (device pointers unless
  * io == ODE_IO_HOST) or NULL when not wanted.  n_rhs counts RHS evaluations
@@ -230,7 +264,8 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
  * and the stats arrays are HOST pointers (pinned memory gives asynchronous
  * copies; y_out may alias y0); opts->io and opts->codegen are ignored (the
  * built-in kernels are used, never run-time generated ones, since loading
- * generated code allocates), and so are opts->h0, sigma0, log_xy and cost.  A batch whose staged arrays need more than the
+ * generated code allocates), and so are opts->h0, sigma0, log_xy, cost and
+ * carry.  A batch whose staged arrays need more than the
  * scratch offers -- nsys * 8 * (neq + n_params) bytes plus 4 * nsys per
  * requested counter array, each rounded up to 256 bytes, against 16 MiB
  * minus the cursor and table -- is rejected with ODE_ERR_ARG before any GPU
@@ -263,8 +298,8 @@ int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const dou
  * precision / size class; an in-place plan's sample writes to a temporary
  * copy of the state), ODE_MAP_THREAD is the paper's
  * one-thread-per-system mapping with 64-thread blocks, ODE_MAP_QUEUE the
- * default warp-per-system shape; opts->h0, sigma0, log_xy and cost are
- * ignored (a plan orders each bucket by system size).  Families: Brusselator and oscillator
+ * default warp-per-system shape; opts->h0, sigma0, log_xy, cost and carry
+ * are ignored (a plan orders each bucket by system size).  Families: Brusselator and oscillator
  * chains (register each family once with its largest neq).  Layout: system
  * i's components are contiguous from offset[i]. */
 typedef struct {
@@ -367,6 +402,8 @@ int ode_mapping_info(int32_t rhs_handle, int32_t method, int32_t precision, int3
  * unspecified order.  cost: device [n].  Asynchronous on `stream`;
  * n <= 2^31 - 1.  No counterpart in the paper. */
 int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream);
+/* The same for int32 costs (e.g. n_rhs counters), each taken as a float. */
+int ode_cost_order_i32(const int32_t* cost, int64_t n, int32_t* index, void* stream);
 
 /* Forget every cached ODE_MAP_AUTO timing (uniform calls and ragged plans),
  * so that the next such call or plan times its candidates again (after a

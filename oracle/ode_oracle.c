@@ -59,7 +59,12 @@
  *       unless the state is unusable (H_UNDERFLOW, NONFINITE).  A run
  *       stopped by the attempt cap and continued this way repeats the
  *       uninterrupted run step for step, wherever the per-call quantities
- *       hmax = |tend - t0| and hmin do not bind.
+ *       hmax = |tend - t0| and hmin do not bind.  Carry mode RESTART keeps
+ *       the controller (h, h_old, err_old) and the eigenvector but restarts
+ *       the spectral-radius schedule: sigma is estimated at the first loop
+ *       top (from the carried eigenvector) and the 25-step count starts
+ *       again, i.e. the carry is read with num_step = 0, sr_step = -1 and
+ *       no rejection pending.
  */
 #include <math.h>
 #include <stdint.h>
@@ -91,6 +96,8 @@
 #define KIND_TIME 101      /* f_i = t (tests of the stage times only) */
 
 #define CARRY_FIXED 9
+#define CARRY_CONTINUE 0
+#define CARRY_RESTART 1
 #define CARRY_WORDS(neq) (CARRY_FIXED + (neq))
 
 #define OR_MAX_REAC 64
@@ -577,7 +584,7 @@ static double rkc_specrad(const or_sys* s, double t, const double* y, const doub
  * y holds y(t0) on entry and the final state on exit. */
 static void rkc_system(const or_sys* s, double t, double tend, double rtol, double atol,
                        int max_attempts, double* y, or_counts* cnt, const double* carry_in,
-                       double* carry_out) {
+                       double* carry_out, int carry_mode) {
     int n = s->neq;
     double* mem = (double*)malloc(sizeof(double) * (size_t)n * 10);
     double* yn = mem;
@@ -612,6 +619,11 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
         rejected = (int)carry_in[8];
         for (int i = 0; i < n; ++i) v[i] = carry_in[CARRY_FIXED + i];
         have_sigma = 1;
+        if (carry_mode == CARRY_RESTART) {
+            num_step = 0;
+            sr_step = -1;
+            rejected = 0;
+        }
     }
     while (t < tend) {
         if (cnt->n_accept + cnt->n_reject >= max_attempts) {
@@ -746,7 +758,7 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
                      const double* params, double t0, double tend, double rtol, double atol,
                      int max_attempts, double* y_out, int32_t* n_accept, int32_t* n_reject,
                      int32_t* n_rhs, int32_t* n_specrad_iter, int32_t* status, int nthreads,
-                     const double* carry_in, double* carry_out) {
+                     const double* carry_in, double* carry_out, int carry_mode) {
     if (m->neq <= 0 || m->n_params > OR_MAX_PARAMS) return -1;
     int nt = resolve_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
@@ -769,7 +781,7 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
         if (method == 0)
             rkck_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout);
         else
-            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout);
+            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout, carry_mode);
         for (int j = 0; j < m->neq; ++j) y_out[i + nsys * (int64_t)j] = y[j];
         if (cout)
             for (int w = 0; w < K; ++w) carry_out[i + nsys * (int64_t)w] = cout[w];
@@ -806,7 +818,7 @@ int oracle_integrate_ragged(const or_model* models, const int32_t* model_idx, in
         if (method[i] == 0)
             rkck_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL);
         else
-            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL);
+            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL, 0);
         if (n_accept) n_accept[i] = cnt.n_accept;
         if (n_reject) n_reject[i] = cnt.n_reject;
         if (n_rhs) n_rhs[i] = cnt.n_rhs;

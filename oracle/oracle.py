@@ -17,6 +17,7 @@ KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION = 1, 2, 3, 4
 KIND_LINEAR, KIND_TIME = 100, 101
 ST_OK, ST_H_UNDERFLOW, ST_MAX_ATTEMPTS, ST_NONFINITE, ST_SPECRAD_NOCONV = 0, 1, 2, 3, 256
 CARRY_FIXED = 9   # warm-restart state: valid, t, h, sigma, h_old, err_old, num_step, sr_step, rejected; then v
+CARRY_CONTINUE, CARRY_RESTART = 0, 1
 
 
 def carry_words(neq: int) -> int:
@@ -46,7 +47,8 @@ def lib():
         L = C.CDLL(path)
         P = C.c_void_p
         L.oracle_integrate.argtypes = [P, C.c_int, C.c_int64, P, P, C.c_double, C.c_double,
-                                       C.c_double, C.c_double, C.c_int, P, P, P, P, P, P, C.c_int, P, P]
+                                       C.c_double, C.c_double, C.c_int, P, P, P, P, P, P, C.c_int, P, P,
+                                       C.c_int]
         L.oracle_integrate_ragged.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int,
                                               P, P, P, P, P, P, C.c_int]
         L.oracle_rhs.argtypes = [P, P, C.c_double, P, P]
@@ -118,10 +120,11 @@ class Result:
 
 def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
               max_attempts: int = 1_000_000, nthreads: int = 0, carry_in=None,
-              carry_out: bool = False) -> Result:
+              carry_out: bool = False, carry_mode: int = CARRY_CONTINUE) -> Result:
     """Integrate a uniform SoA batch y0[neq, nsys]; method 0 = RKCK, 1 = RKC.
     carry_in (SoA [carry_words(neq), nsys]) resumes a previous call's
-    controller state; carry_out returns this call's in ``Result.carry``."""
+    controller state (carry_mode CARRY_CONTINUE or CARRY_RESTART); carry_out
+    returns this call's in ``Result.carry``."""
     y0 = _f64(y0)
     params = _f64(params)
     nsys = y0.shape[1]
@@ -134,7 +137,8 @@ def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: f
     cout = np.zeros((carry_words(m.neq), nsys)) if carry_out else None
     rc = lib().oracle_integrate(C.byref(m), method, nsys, _p(y0), _p(params), t0, tend, rtol,
                                 atol, max_attempts, _p(y), *[_p(a) for a in c], nthreads,
-                                _p(cin) if cin is not None else None, _p(cout) if cout is not None else None)
+                                _p(cin) if cin is not None else None, _p(cout) if cout is not None else None,
+                                carry_mode)
     if rc != 0:
         raise ValueError(f"oracle_integrate failed ({rc})")
     return Result(y, *c, carry=cout)

@@ -33,7 +33,8 @@ EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_inte
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
             "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
-            "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order", "ode_mapping_info"]
+            "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order", "ode_cost_order_i32",
+            "ode_mapping_info"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -52,8 +53,10 @@ class RhsDesc(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
-                ("codegen", C.c_int32), ("reserved", C.c_int32 * 9),
-                ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p), ("cost", C.c_void_p)]
+                ("codegen", C.c_int32), ("cost_kind", C.c_int32), ("carry_mode", C.c_int32),
+                ("reserved", C.c_int32 * 7),
+                ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p), ("cost", C.c_void_p),
+                ("carry", C.c_void_p)]
 
 
 class RaggedBatch(C.Structure):
@@ -124,6 +127,7 @@ def load(build_if_missing: bool = True):
     L.ode_mlp_get_params.argtypes = [C.c_int32, P, P]
     L.ode_mlp_set_params.argtypes = [C.c_int32, P, P]
     L.ode_cost_order.argtypes = [P, C.c_int64, P, P]
+    L.ode_cost_order_i32.argtypes = [P, C.c_int64, P, P]
     L.ode_mapping_info.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P]
     _lib = L
     return L
@@ -198,11 +202,12 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
               stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO, h0=None, sigma0=None,
-              log_xy=None, cost=None):
+              log_xy=None, cost=None, carry=None, carry_mode: int = 0):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
     tensor for device io, numpy array for host io); returns y_out.  log_xy
     rows are [neq + 4]; cost (float32 [nsys], device) orders the batch
-    longest-first."""
+    longest-first; carry (float64 [carry_words(neq), nsys], device) is the
+    warm-restart state, read and written."""
     host = isinstance(y0, np.ndarray)
     nsys = int(y0.shape[1])
     if y_out is None:
@@ -212,7 +217,9 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.io = ODE_IO_HOST if host else ODE_IO_DEVICE
     o.sync = 1 if sync else 0
     o.codegen = codegen
-    o.h0, o.sigma0, o.log_xy, o.cost = _ptr(h0), _ptr(sigma0), _ptr(log_xy), _ptr(cost)
+    o.h0, o.sigma0, o.log_xy, o.cost, o.carry = _ptr(h0), _ptr(sigma0), _ptr(log_xy), _ptr(cost), _ptr(carry)
+    o.cost_kind = 1 if cost is not None and str(getattr(cost, "dtype", "")).endswith("int32") else 0
+    o.carry_mode = carry_mode
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
@@ -376,11 +383,27 @@ class RaggedPlan:
             self.handle = 0
 
 
+CARRY_FIXED = 9
+ODE_CARRY_CONTINUE, ODE_CARRY_RESTART = 0, 1
+
+
+def carry_words(neq: int) -> int:
+    """Words of warm-restart state per system (ode_opts.carry)."""
+    return neq + CARRY_FIXED
+
+
+def carry_like(neq: int, nsys: int, device="cuda"):
+    """A zeroed (cold) warm-restart state for a batch."""
+    import torch
+    return torch.zeros((carry_words(neq), nsys), dtype=torch.float64, device=device)
+
+
 def cost_order(cost, stream=None):
-    """Longest-first order (int32 torch tensor) of a float32 CUDA cost vector."""
+    """Longest-first order (int32 torch tensor) of a float32 or int32 CUDA cost vector."""
     import torch
     idx = torch.empty(int(cost.shape[0]), dtype=torch.int32, device=cost.device)
-    _check(load().ode_cost_order(_ptr(cost), int(cost.shape[0]), _ptr(idx), _stream(stream)))
+    fn = load().ode_cost_order_i32 if cost.dtype == torch.int32 else load().ode_cost_order
+    _check(fn(_ptr(cost), int(cost.shape[0]), _ptr(idx), _stream(stream)))
     return idx
 
 

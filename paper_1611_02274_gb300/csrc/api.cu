@@ -230,6 +230,7 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
     t.y_out = ws->tune_y;
     t.n_accept = t.n_reject = t.n_rhs = t.n_specrad = t.status = nullptr;
     t.log_xy = nullptr;
+    t.carry = nullptr;  // the timing runs neither read nor overwrite the caller's warm-restart state
     t.cursor = ws->cursors + kCursorRing;
     std::vector<std::pair<int, int>> cand;
     for (int b : {64, 128, 256})
@@ -285,8 +286,11 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     ode_opts opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    for (int k = 0; k < 9; ++k)
+    for (int k = 0; k < 7; ++k)
         if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
+    if (opts.carry_mode != ODE_CARRY_CONTINUE && opts.carry_mode != ODE_CARRY_RESTART)
+        return fail(ODE_ERR_ARG, "unknown carry_mode %d", opts.carry_mode);
+    if (opts.cost_kind != 0 && opts.cost_kind != 1) return fail(ODE_ERR_ARG, "cost_kind must be 0 or 1");
     if (opts.codegen < ODE_CODEGEN_AUTO || opts.codegen > ODE_CODEGEN_ON) return fail(ODE_ERR_ARG, "unknown codegen mode %d", opts.codegen);
     if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_LEAN)
         return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
@@ -300,8 +304,8 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     if (!(atol >= 0.0) || !std::isfinite(atol)) return fail(ODE_ERR_ARG, "atol must be finite and >= 0");
     if (!std::isfinite(t0) || !std::isfinite(tend) || tend < t0) return fail(ODE_ERR_ARG, "need finite t0 <= tend");
     if ((opts.h0 == nullptr) != (opts.sigma0 == nullptr)) return fail(ODE_ERR_ARG, "h0 and sigma0 go together");
-    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy || opts.cost))
-        return fail(ODE_ERR_ARG, "proposals, logs and cost ordering need device io");
+    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy || opts.cost || opts.carry))
+        return fail(ODE_ERR_ARG, "proposals, logs, cost ordering and warm-restart state need device io");
     if (opts.cost && nsys > INT32_MAX) return fail(ODE_ERR_ARG, "cost ordering takes at most 2^31 - 1 systems");
     if (nsys == 0) return ODE_OK;
     if (!y0 || !params || !y_out) return fail(ODE_ERR_ARG, "y0, params and y_out must be non-NULL");
@@ -372,6 +376,8 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     a.h0 = opts.h0;
     a.sigma0 = opts.sigma0;
     a.log_xy = opts.log_xy;
+    a.carry = opts.carry;
+    a.carry_mode = opts.carry_mode;
     a.rkc_tab64 = ws->tab64;
     a.rkc_tab32 = ws->tab32;
     a.rkc_tab_max = kRkcTabMax;
@@ -404,7 +410,7 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
             e = cudaMalloc(&ob.bins, sizeof(int32_t) * kOrderScratchWords);
             if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "order bins");
         }
-        e = order_by_cost(opts.cost, nsys, ob.bins, ob.index, ws->sm_count, stream);
+        e = order_by_cost(opts.cost, opts.cost_kind, nsys, ob.bins, ob.index, ws->sm_count, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cost ordering");
         a.index = ob.index;
     }
@@ -529,7 +535,22 @@ int ode_mapping_info(int32_t rhs_handle, int32_t method, int32_t precision, int3
     return t != g_map_tuned.end() ? ODE_OK : ODE_ERR_UNSUPPORTED;
 }
 
+namespace {
+int cost_order_any(const void* cost, int kind, int64_t n, int32_t* index, void* stream_ptr);
+}
+
 int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream_ptr) {
+    return cost_order_any(cost, 0, n, index, stream_ptr);
+}
+
+int ode_cost_order_i32(const int32_t* cost, int64_t n, int32_t* index, void* stream_ptr) {
+    return cost_order_any(cost, 1, n, index, stream_ptr);
+}
+
+}  // extern "C"
+
+namespace {
+int cost_order_any(const void* cost, int kind, int64_t n, int32_t* index, void* stream_ptr) {
     g_err.clear();
     if (n < 0 || n > INT32_MAX) return fail(ODE_ERR_ARG, "n must be in [0, 2^31 - 1]");
     if (n == 0) return ODE_OK;
@@ -544,9 +565,12 @@ int ode_cost_order(const float* cost, int64_t n, int32_t* index, void* stream_pt
         cudaError_t e = cudaMalloc(&ob.bins, sizeof(int32_t) * kOrderScratchWords);
         if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "order bins");
     }
-    cudaError_t e = order_by_cost(cost, n, ob.bins, index, ws->sm_count, stream);
+    cudaError_t e = order_by_cost(cost, kind, n, ob.bins, index, ws->sm_count, stream);
     return e == cudaSuccess ? ODE_OK : cuda_fail(e, "cost ordering");
 }
+}  // namespace
+
+extern "C" {
 
 int ode_tuning_reset(void) {
     g_err.clear();

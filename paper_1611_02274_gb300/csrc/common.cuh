@@ -61,6 +61,14 @@ struct Pick<false, T, F> {
 // or multi-lane systems keep it in registers).
 __host__ __device__ constexpr int rkc_mixed_smem_floats(int lanes, int per_lane) { return (lanes == 1 && per_lane <= 32) ? per_lane : 0; }
 
+// Warm-restart carry words (see batchode.h): valid flag, time reached, h,
+// sigma, h_old, err_old, accepted-step count, count at the last
+// spectral-radius estimate, rejected flag; then the eigenvector.
+enum : int {
+    kCarryValid = 0, kCarryT, kCarryH, kCarrySigma, kCarryHold, kCarryErrOld, kCarryNumStep, kCarrySrStep,
+    kCarryRejected, kCarryFixed
+};
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 
@@ -109,8 +117,13 @@ struct BatchArgs {
     // systems of a batch (mapping autotuning) keeps the batch's input stride
     // and writes a k-system output.
     int64_t ld_in, ld_out;
+    // warm-restart state, in and out (uniform batches; NULL = none): word w
+    // of system i at carry[i + nsys w], layout as in batchode.h
+    double* carry;
+    int32_t carry_mode;  // ODE_CARRY_CONTINUE / ODE_CARRY_RESTART
 
     __host__ __device__ int64_t sys_of(int64_t k) const { return index ? (int64_t)index[k] : k; }
+    __host__ __device__ int64_t cidx(int64_t i, int w) const { return i + nsys * (int64_t)w; }
     __host__ __device__ int64_t yidx(int64_t i, int c) const {
         return offset ? offset[i] + c : i + (ld_in ? ld_in : nsys) * (int64_t)c;
     }

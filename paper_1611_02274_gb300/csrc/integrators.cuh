@@ -55,6 +55,28 @@ __device__ __forceinline__ void df_sub(float& hi, float& lo, float b) {
     lo = l - (hi - s);
 }
 
+// Warm-restart carry (the outer global-step loop of Section 3; layout in
+// batchode.h).  carry_warm: a valid carry for system i.  carry_store: the
+// scalars from team lane 0, v from every lane (slots past the system's
+// size hold no component and are skipped); RKCK stores only its step size.
+__device__ __forceinline__ bool carry_warm(const BatchArgs& a, int64_t i) {
+    return a.carry != nullptr && a.carry[a.cidx(i, kCarryValid)] == 1.0;
+}
+__device__ __forceinline__ void carry_scalars(const BatchArgs& a, int64_t i, bool valid, double t, double h,
+                                              double sigma, double h_old, double err_old, int num_step,
+                                              int sr_step, bool rejected) {
+    double* c = a.carry;
+    c[a.cidx(i, kCarryValid)] = valid ? 1.0 : 0.0;
+    c[a.cidx(i, kCarryT)] = t;
+    c[a.cidx(i, kCarryH)] = h;
+    c[a.cidx(i, kCarrySigma)] = sigma;
+    c[a.cidx(i, kCarryHold)] = h_old;
+    c[a.cidx(i, kCarryErrOld)] = err_old;
+    c[a.cidx(i, kCarryNumStep)] = (double)num_step;
+    c[a.cidx(i, kCarrySrStep)] = (double)sr_step;
+    c[a.cidx(i, kCarryRejected)] = rejected ? 1.0 : 0.0;
+}
+
 // ================================================================ RKCK F64
 
 template <class Model>
@@ -81,6 +103,7 @@ struct RkckF64 {
         rtol = a.rtol_of(i);
         hmax = fabs(tend - t);
         h = 0.5 * fabs(tend - t);
+        if (carry_warm(a, i) && a.carry[a.cidx(i, kCarryH)] > 0.0) h = a.carry[a.cidx(i, kCarryH)];
         delta = (a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny;
         n_acc = n_rej = status = 0;
         max_att = a.max_attempts;
@@ -226,7 +249,10 @@ struct RkckF64 {
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
             if (c >= 0) a.y_out[a.yidx_out(i, c)] = y[s];
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = 0.0;
         }
+        if (a.carry != nullptr && tm.lane == 0)
+            carry_scalars(a, i, status == ODE_ST_OK || status == ODE_ST_MAX_ATTEMPTS, t, h, 0.0, 0.0, 0.0, 0, 0, false);
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;
             if (a.n_reject) a.n_reject[i] = n_rej;
@@ -254,7 +280,7 @@ struct RkcF64 {
     CoefSource cs;
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
     int32_t phase, m, j, sr_iter;
-    bool have_sigma, rejected;
+    bool have_sigma, rejected, warm;
     int64_t idx;  // system index (training log)
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
@@ -281,6 +307,27 @@ struct RkcF64 {
         num_step = 0;
         sr_step = -1;
         have_sigma = rejected = false;
+        warm = carry_warm(a, i);
+        if (warm) {  // resume the controller and the spectral-radius schedule
+            h = a.carry[a.cidx(i, kCarryH)];
+            sigma = a.carry[a.cidx(i, kCarrySigma)];
+            h_old = a.carry[a.cidx(i, kCarryHold)];
+            err_old = a.carry[a.cidx(i, kCarryErrOld)];
+            num_step = (int)a.carry[a.cidx(i, kCarryNumStep)];
+            sr_step = (int)a.carry[a.cidx(i, kCarrySrStep)];
+            rejected = (int)a.carry[a.cidx(i, kCarryRejected)] != 0;
+            have_sigma = true;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                const int c = sys.comp(tm, s);
+                v[s] = c >= 0 ? a.carry[a.cidx(i, kCarryFixed + c)] : 0.0;
+            }
+            if (a.carry_mode == ODE_CARRY_RESTART) {  // the spectral-radius schedule starts again
+                num_step = 0;
+                sr_step = -1;
+                rejected = false;
+            }
+        }
         phase = PH_F0;  // F_n = f(t0, y0)
     }
     __device__ bool done() const { return phase == PH_DONE; }
@@ -329,7 +376,7 @@ struct RkcF64 {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 Fn[s] = f[s];
-                v[s] = f[s];  // first eigenvector guess
+                if (!warm) v[s] = f[s];  // first eigenvector guess
             }
             loop_top(a, tm);
             break;
@@ -571,6 +618,12 @@ struct RkcF64 {
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
             if (c >= 0) a.y_out[a.yidx_out(i, c)] = yn[s];
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = v[s];
+        }
+        if (a.carry != nullptr && tm.lane == 0) {
+            const int st = status & 0xFF;
+            carry_scalars(a, i, (st == ODE_ST_OK || st == ODE_ST_MAX_ATTEMPTS) && have_sigma, t, h, sigma, h_old,
+                          err_old, num_step, sr_step, rejected);
         }
         if (tm.lane == 0) {
             if (a.log_xy != nullptr && n_acc > 0) a.log_xy[idx * (int64_t)(n + 4) + n + 3] = (float)log((double)(n_rhs + n_sr));
@@ -633,6 +686,7 @@ struct RkckMixed {
         tend = a.tend_of(i);
         hmax = (HT)fabs(tend - t);
         h = (HT)(0.5 * fabs(tend - t));
+        if (carry_warm(a, i) && a.carry[a.cidx(i, kCarryH)] > 0.0) h = (HT)a.carry[a.cidx(i, kCarryH)];
         remf = (float)(tend - t);
         reml = (float)((tend - t) - (double)remf);
         tendf = (float)tend;
@@ -776,6 +830,12 @@ struct RkckMixed {
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
             if (c >= 0) a.y_out[a.yidx_out(i, c)] = (double)yh[s] + (double)yl[s];
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = 0.0;
+        }
+        if (a.carry != nullptr && tm.lane == 0) {
+            const double t_end = SPEC ? (double)t : tend - ((double)remf + (double)reml);
+            carry_scalars(a, i, status == ODE_ST_OK || status == ODE_ST_MAX_ATTEMPTS, t_end, (double)h, 0.0, 0.0,
+                          0.0, 0, 0, false);
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;
@@ -828,7 +888,7 @@ struct RkcMixed {
     CoefSource cs;
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
     int32_t phase, m, j, sr_iter;
-    bool have_sigma, rejected;
+    bool have_sigma, rejected, warm;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
         sys.load(ctx, tm, a.params[i], a.neq_of(i));
@@ -860,7 +920,27 @@ struct RkcMixed {
         num_step = 0;
         sr_step = -1;
         have_sigma = rejected = false;
-        if (a.h0 != nullptr) {
+        warm = carry_warm(a, i);
+        if (warm) {  // resume the controller and the spectral-radius schedule
+            h = (HT)a.carry[a.cidx(i, kCarryH)];
+            sigma = (HT)a.carry[a.cidx(i, kCarrySigma)];
+            h_old = (HT)a.carry[a.cidx(i, kCarryHold)];
+            c3_old = fpow((float)a.carry[a.cidx(i, kCarryErrOld)], 1.0f / 3.0f);
+            num_step = (int)a.carry[a.cidx(i, kCarryNumStep)];
+            sr_step = (int)a.carry[a.cidx(i, kCarrySrStep)];
+            rejected = (int)a.carry[a.cidx(i, kCarryRejected)] != 0;
+            have_sigma = true;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                const int c = sys.comp(tm, s);
+                V(s) = c >= 0 ? (float)a.carry[a.cidx(i, kCarryFixed + c)] : 0.0f;
+            }
+            if (a.carry_mode == ODE_CARRY_RESTART) {  // the spectral-radius schedule starts again
+                num_step = 0;
+                sr_step = -1;
+                rejected = false;
+            }
+        } else if (a.h0 != nullptr) {
             // a proposed start replaces the initial power method and Euler
             // trial; the first rejection returns the system to the power method
             const float hp = a.h0[i], sp = a.sigma0[i];
@@ -918,7 +998,7 @@ struct RkcMixed {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 Fn[s] = f[s];
-                V(s) = f[s];
+                if (!warm) V(s) = f[s];  // first eigenvector guess
             }
             loop_top(a, tm);
             break;
@@ -1235,6 +1315,14 @@ struct RkcMixed {
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
             if (c >= 0) a.y_out[a.yidx_out(i, c)] = (double)yh[s] + (double)yl[s];
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = (double)V(s);
+        }
+        if (a.carry != nullptr && tm.lane == 0) {
+            const int st = status & 0xFF;
+            const double t_end = SPEC ? (double)t : tend - ((double)remf + (double)reml);
+            carry_scalars(a, i, (st == ODE_ST_OK || st == ODE_ST_MAX_ATTEMPTS) && have_sigma, t_end, (double)h,
+                          (double)sigma, (double)h_old, (double)c3_old * (double)c3_old * (double)c3_old, num_step,
+                          sr_step, rejected);
         }
         if (tm.lane == 0) {
             if (a.n_accept) a.n_accept[i] = n_acc;

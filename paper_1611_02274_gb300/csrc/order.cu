@@ -33,6 +33,11 @@ constexpr int kScanThreads = 1024;
 constexpr int kBinsPerThread = kOrderBins / kScanThreads;
 static_assert(kOrderBins % kScanThreads == 0, "bins split evenly over the scan block");
 
+// a cost as float: float32 estimates, or int32 counts (e.g. n_rhs)
+__device__ __forceinline__ float cost_at(const void* cost, int kind, int64_t i) {
+    return kind == 1 ? (float)static_cast<const int32_t*>(cost)[i] : static_cast<const float*>(cost)[i];
+}
+
 // range[0] = lo, range[1] = hi (bit patterns of the positive costs)
 __device__ __forceinline__ int cost_class(float c, const uint32_t* range) {
     if (!(c > 0.0f)) return 0;  // NaN, zero and negative estimates: cheapest
@@ -41,10 +46,10 @@ __device__ __forceinline__ int cost_class(float c, const uint32_t* range) {
     return 1 + (int)(step / ((uint64_t)(hi - lo) + 1u));
 }
 
-__global__ void k_order_range(const float* __restrict__ cost, int64_t n, uint32_t* __restrict__ range) {
+__global__ void k_order_range(const void* __restrict__ cost, int kind, int64_t n, uint32_t* __restrict__ range) {
     uint32_t lo = 0xffffffffu, hi = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float c = cost[i];
+        const float c = cost_at(cost, kind, i);
         if (c > 0.0f) {
             lo = min(lo, __float_as_uint(c));
             hi = max(hi, __float_as_uint(c));
@@ -60,13 +65,13 @@ __global__ void k_order_range(const float* __restrict__ cost, int64_t n, uint32_
     }
 }
 
-__global__ void k_order_hist(const float* __restrict__ cost, int64_t n, const uint32_t* __restrict__ range,
+__global__ void k_order_hist(const void* __restrict__ cost, int kind, int64_t n, const uint32_t* __restrict__ range,
                              int32_t* __restrict__ hist) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < n;
     const unsigned active = __ballot_sync(0xffffffffu, live);
     if (!live) return;
-    const int cls = cost_class(cost[i], range);
+    const int cls = cost_class(cost_at(cost, kind, i), range);
     const unsigned peers = __match_any_sync(active, cls);
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[cls], __popc(peers));
 }
@@ -105,11 +110,12 @@ __global__ void __launch_bounds__(kScanThreads) k_order_scan(const int32_t* __re
     }
 }
 
-__global__ void k_order_scatter(const float* __restrict__ cost, int64_t n, const uint32_t* __restrict__ range,
-                                 int32_t* __restrict__ offset, int32_t* __restrict__ index) {
+__global__ void k_order_scatter(const void* __restrict__ cost, int kind, int64_t n,
+                                 const uint32_t* __restrict__ range, int32_t* __restrict__ offset,
+                                 int32_t* __restrict__ index) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < n;
-    const int cls = live ? cost_class(cost[i], range) : -1;
+    const int cls = live ? cost_class(cost_at(cost, kind, i), range) : -1;
     const unsigned active = __ballot_sync(0xffffffffu, live);
     if (!live) return;
     const unsigned peers = __match_any_sync(active, cls);
@@ -123,7 +129,7 @@ __global__ void k_order_scatter(const float* __restrict__ cost, int64_t n, const
 
 }  // namespace
 
-cudaError_t order_by_cost(const float* cost, int64_t n, int32_t* bins, int32_t* index, int sm_count,
+cudaError_t order_by_cost(const void* cost, int kind, int64_t n, int32_t* bins, int32_t* index, int sm_count,
                           cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int32_t* hist = bins;
@@ -135,10 +141,10 @@ cudaError_t order_by_cost(const float* cost, int64_t n, int32_t* bins, int32_t* 
     if (e != cudaSuccess) return e;
     const int64_t blocks = (n + 255) / 256;
     const unsigned grid = (unsigned)(blocks < 4 * (int64_t)sm_count ? blocks : 4 * (int64_t)sm_count);
-    k_order_range<<<grid, 256, 0, s>>>(cost, n, range);
-    k_order_hist<<<(unsigned)blocks, 256, 0, s>>>(cost, n, range, hist);
+    k_order_range<<<grid, 256, 0, s>>>(cost, kind, n, range);
+    k_order_hist<<<(unsigned)blocks, 256, 0, s>>>(cost, kind, n, range, hist);
     k_order_scan<<<1, kScanThreads, 0, s>>>(hist, offset);
-    k_order_scatter<<<(unsigned)blocks, 256, 0, s>>>(cost, n, range, offset, index);
+    k_order_scatter<<<(unsigned)blocks, 256, 0, s>>>(cost, kind, n, range, offset, index);
     return cudaGetLastError();
 }
 

@@ -14,8 +14,8 @@ constexpr int kOrderScratchWords = 2 * kOrderBins + 2;
 
 // Writes index[0..n) = the systems 0..n-1, most expensive class first,
 // on stream s.  bins: device scratch of kOrderScratchWords int32; index:
-// n int32.  cost: device [n].
-cudaError_t order_by_cost(const float* cost, int64_t n, int32_t* bins, int32_t* index, int sm_count,
+// n int32.  cost: device [n], float32 (kind 0) or int32 (kind 1).
+cudaError_t order_by_cost(const void* cost, int kind, int64_t n, int32_t* bins, int32_t* index, int sm_count,
                           cudaStream_t s);
 
 }  // namespace bode

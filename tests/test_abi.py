@@ -79,6 +79,10 @@ def test_integrate_argument_errors_before_any_launch():
     with pytest.raises(B.BatchOdeError) as e:
         B.integrate("rkck", h, y, p, 0.0, 1.0, 1e-6, 1e-9, cost=cost)
     assert e.value.code == B.ODE_ERR_ARG
+    carry = np.zeros((B.carry_words(2), 4))
+    with pytest.raises(B.BatchOdeError) as e:
+        B.integrate("rkc", h, y, p, 0.0, 1.0, 1e-6, 1e-9, carry=carry)
+    assert e.value.code == B.ODE_ERR_ARG
     B.release(h)
     # the stand-alone order: bad sizes and NULL arrays are refused before any launch
     L = B.load()

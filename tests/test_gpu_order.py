@@ -63,6 +63,16 @@ def test_order_all_nonpositive():
     check_order(np.array([0.0, -2.0, np.nan] * 50))
 
 
+def test_int32_costs_order_like_their_float_values():
+    import torch
+    rng = np.random.default_rng(11)
+    c = rng.integers(-5, 5000, size=70001).astype(np.int32)
+    idx = B.cost_order(torch.from_numpy(c).cuda()).cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(np.sort(idx), np.arange(c.size))
+    cls = host_class(c.astype(np.float32))
+    assert np.all(np.diff(cls[idx]) <= 0)
+
+
 def test_order_many_equal_costs():
     # heavy contention on a few classes (the scatter's aggregated atomics)
     rng = np.random.default_rng(5)

@@ -6,7 +6,8 @@ the time it reached with the carried state repeats the uninterrupted run
 step for step, so the final states agree bit for bit and the accepted /
 rejected counts add up.  (The per-call quantities hmax = |tend - t0| and
 hmin do not bind on these stiff workloads.)  A cold carry (flag 0) is no
-carry at all.
+carry at all.  Carry mode RESTART is the continuation with the
+spectral-radius schedule started again.
 """
 import numpy as np
 import pytest
@@ -114,3 +115,23 @@ def test_warm_chain_saves_the_start_up():
         e = np.abs(y - ref.y) / (np.abs(ref.y) + w.atol)
         assert e.max() < 5e-3, (warm, e.max())
     assert runs[True][1].sum() < runs[False][1].sum()
+
+
+def test_restart_mode_is_continue_with_the_schedule_reset():
+    w = W.massaction(24, seed=17)
+    m = O.model_for(w)
+    t1 = 0.4 * w.tend
+    a = O.integrate(m, RKC, w.y0, w.params, w.t0, t1, w.rtol, w.atol, carry_out=True)
+    c = a.carry.copy()
+    r = O.integrate(m, RKC, a.y, w.params, t1, w.tend, w.rtol, w.atol, carry_in=c, carry_out=True,
+                    carry_mode=O.CARRY_RESTART)
+    c2 = c.copy()
+    c2[6], c2[7], c2[8] = 0.0, -1.0, 0.0
+    k = O.integrate(m, RKC, a.y, w.params, t1, w.tend, w.rtol, w.atol, carry_in=c2, carry_out=True,
+                    carry_mode=O.CARRY_CONTINUE)
+    np.testing.assert_array_equal(r.y, k.y)
+    np.testing.assert_array_equal(r.n_rhs, k.n_rhs)
+    np.testing.assert_array_equal(r.carry, k.carry)
+    # the schedule restarted: sigma is estimated at the call start, from the carried eigenvector
+    assert np.all(r.n_specrad_iter > 0)
+    np.testing.assert_array_equal(r.carry[6], r.n_accept)
