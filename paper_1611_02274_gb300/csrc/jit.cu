@@ -103,13 +103,15 @@ Nvrtc& nvrtc() {
 }
 
 // Resident blocks of 128 threads per SM the generated kernels are compiled
-// for (a register budget of 65536 / (128 n) per thread).  3 measured best for
-// the 13-species network (168 registers; 1 and 2 leave 231, 4 spills);
-// BATCHODE_JIT_MINBLOCKS overrides it (1 = no budget).
-int jit_min_blocks() {
+// for (a register budget of 65536 / (128 n) per thread).  Measured on the
+// 13-species network: the mixed forms run best at 3 (168 registers; 2 and
+// 4 are slower), the plain FP64 form at 2 (its FP64 state spills at 168
+// registers).  BATCHODE_JIT_MINBLOCKS overrides both (1 = no budget).
+int jit_min_blocks(int prec) {
+    const int def = prec == ODE_PREC_FP64 ? 2 : 3;
     const char* v = getenv("BATCHODE_JIT_MINBLOCKS");
-    const int n = v ? atoi(v) : 3;
-    return n >= 1 && n <= 16 ? n : 3;
+    const int n = v ? atoi(v) : def;
+    return n >= 1 && n <= 16 ? n : def;
 }
 
 std::string lit(double x) {
@@ -242,7 +244,7 @@ int compile_image(const RhsEntry& r, int method, int prec, JitImage* img, std::s
                                      prec == ODE_PREC_FP64 ? "--fmad=false" : "--fmad=true"};
     // occupancy tuning: blocks of at most 128 threads with a register budget
     // for BATCHODE_JIT_MINBLOCKS resident blocks per SM
-    const int minb = jit_min_blocks();
+    const int minb = jit_min_blocks(prec);
     if (minb > 1) {
         opts.push_back("-DBODE_MAX_THREADS=128");
         opts.push_back("-DBODE_MIN_BLOCKS=" + std::to_string(minb));
@@ -354,7 +356,7 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
 std::string cache_key(const RhsEntry& r, int method, int prec, int dev) {
     char key[96];
     snprintf(key, sizeof(key), "%d/%d/%d/%016llx/%d", dev, method, prec, (unsigned long long)fnv1a(model_source(r)),
-             jit_min_blocks());
+             jit_min_blocks(prec));
     return key;
 }
 
@@ -402,7 +404,7 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
     NoCtx ctx;
     BatchArgs args = a;
     void* params[] = {&args, &ctx};
-    const int block = jit_min_blocks() > 1 && c.block > 128 ? 128 : c.block;
+    const int block = jit_min_blocks(prec) > 1 && c.block > 128 ? 128 : c.block;
     // the generated model is one thread per system with PER = species count
     const int smem_floats = method == kMethodRkc && prec != ODE_PREC_FP64 ? rkc_mixed_smem_floats(1, r.net.n_species) : 0;
     const size_t smem = sizeof(float) * smem_floats * (size_t)block;
