@@ -65,6 +65,15 @@
  *       top (from the carried eigenvector) and the 25-step count starts
  *       again, i.e. the carry is read with num_step = 0, sr_step = -1 and
  *       no rejection pending.
+ *   R23 Gershgorin bound (the Appendix names the circle theorem as an
+ *       upper-bound alternative to the power method): every eigenvalue of
+ *       the Jacobian J lies in a disc centred at J_ii of radius
+ *       sum_{j != i} |J_ij|, so sigma <= G = max_i sum_j |J_ij|.  J is the
+ *       analytic Jacobian of each right-hand side below; each row sum runs
+ *       over the columns in increasing order.  Spectral-radius modes:
+ *       POWER (the Appendix method), GERSHGORIN (sigma = G at every point
+ *       the power method would run, no right-hand-side evaluations),
+ *       POWER_CAPPED (the power method's 1.2 sigma, capped at G).
  */
 #include <math.h>
 #include <stdint.h>
@@ -98,6 +107,9 @@
 #define CARRY_FIXED 9
 #define CARRY_CONTINUE 0
 #define CARRY_RESTART 1
+#define SPECRAD_POWER 0
+#define SPECRAD_GERSHGORIN 1
+#define SPECRAD_POWER_CAPPED 2
 #define CARRY_WORDS(neq) (CARRY_FIXED + (neq))
 
 #define OR_MAX_REAC 64
@@ -198,6 +210,122 @@ static void rhs_linear(const or_sys* s, const double* y, double* f) {
         for (int j = 0; j < n; ++j) acc = acc + s->p[i * n + j] * y[j];
         f[i] = acc;
     }
+}
+
+/* ------------------------------------------------------------ Jacobians
+ * Analytic df/dy, row-major n x n (R23).  Each entry is written as the
+ * derivative of the expression above it, term by term. */
+
+static void jac_vdp(const or_sys* s, const double* y, double* J) {
+    double mu = s->p[0];
+    J[0] = 0.0;
+    J[1] = 1.0;
+    J[2] = mu * (-2.0 * y[0]) * y[1] - 1.0;
+    J[3] = mu * (1.0 - y[0] * y[0]);
+}
+
+static void jac_vdp_chain(const or_sys* s, const double* y, double* J) {
+    int n = s->neq / 2, N = s->neq;
+    double mu = s->p[0];
+    double c = s->m->coupling;
+    const double* x = y;
+    const double* v = y + n;
+    for (int k = 0; k < N * N; ++k) J[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double nb = (double)((i > 0) + (i < n - 1));
+        J[i * N + (n + i)] = 1.0;                                   /* dx_i'/dv_i */
+        double* row = J + (n + i) * N;
+        row[i] = mu * (-2.0 * x[i]) * v[i] - 1.0 - c * nb;          /* dv_i'/dx_i */
+        if (i > 0) row[i - 1] = c;
+        if (i < n - 1) row[i + 1] = c;
+        row[n + i] = mu * (1.0 - x[i] * x[i]);                      /* dv_i'/dv_i */
+    }
+}
+
+static void jac_bruss(const or_sys* s, const double* y, double* J) {
+    int n = s->neq / 2, N = s->neq;
+    const or_model* m = s->m;
+    double a = s->p[0];
+    double dx = 1.0 / (double)(n + 1);
+    double D = a / (dx * dx);
+    const double* u = y;
+    const double* v = y + n;
+    for (int k = 0; k < N * N; ++k) J[k] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double* ru = J + k * N;
+        double* rv = J + (n + k) * N;
+        ru[k] = 2.0 * u[k] * v[k] - (m->bruss_B + 1.0) - 2.0 * D;  /* du'/du */
+        ru[n + k] = u[k] * u[k];                                    /* du'/dv */
+        rv[k] = m->bruss_B - 2.0 * u[k] * v[k];                     /* dv'/du */
+        rv[n + k] = -(u[k] * u[k]) - 2.0 * D;                       /* dv'/dv */
+        if (k > 0) {
+            ru[k - 1] = D;
+            rv[n + k - 1] = D;
+        }
+        if (k < n - 1) {
+            ru[k + 1] = D;
+            rv[n + k + 1] = D;
+        }
+    }
+}
+
+/* dr_j/dC_l summed over the reactant occurrences of species l; the rows of
+ * the reaction's reactants lose it and its products' rows gain it, reaction
+ * by reaction, reactants before products. */
+static void jac_massaction(const or_sys* s, const double* y, double* J) {
+    const or_model* m = s->m;
+    int N = s->neq;
+    for (int k = 0; k < N * N; ++k) J[k] = 0.0;
+    for (int j = 0; j < m->n_reactions; ++j) {
+        int nr = m->n_reac[j];
+        double d[2];
+        for (int q = 0; q < nr; ++q) {  /* d[q]: derivative by the q-th reactant occurrence */
+            double t = s->k[j];
+            for (int o = 0; o < nr; ++o)
+                if (o != q) t = t * y[m->reac[j][o]];
+            d[q] = t;
+        }
+        for (int l = 0; l < N; ++l) {
+            double dl = 0.0;
+            int any = 0;
+            for (int q = 0; q < nr; ++q)
+                if (m->reac[j][q] == l) {
+                    dl = dl + d[q];
+                    any = 1;
+                }
+            if (!any) continue;
+            for (int q = 0; q < nr; ++q) J[m->reac[j][q] * N + l] -= dl;
+            for (int q = 0; q < m->n_prod[j]; ++q) J[m->prod[j][q] * N + l] += dl;
+        }
+    }
+}
+
+static void jacobian(const or_sys* s, const double* y, double* J) {
+    int N = s->neq;
+    switch (s->m->kind) {
+    case KIND_VDP: jac_vdp(s, y, J); break;
+    case KIND_VDP_CHAIN: jac_vdp_chain(s, y, J); break;
+    case KIND_BRUSS1D: jac_bruss(s, y, J); break;
+    case KIND_MASSACTION: jac_massaction(s, y, J); break;
+    case KIND_LINEAR:
+        for (int k = 0; k < N * N; ++k) J[k] = s->p[k];
+        break;
+    default:
+        for (int k = 0; k < N * N; ++k) J[k] = (s->m->kind == KIND_TIME) ? 0.0 : NAN;
+    }
+}
+
+/* G = max_i sum_j |J_ij| (R23). */
+static double gershgorin(const or_sys* s, const double* y, double* J) {
+    int N = s->neq;
+    jacobian(s, y, J);
+    double g = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc = acc + fabs(J[i * N + j]);
+        g = fmax(g, acc);
+    }
+    return g;
 }
 
 static void dydt(const or_sys* s, double t, const double* y, double* f) {
@@ -584,9 +712,10 @@ static double rkc_specrad(const or_sys* s, double t, const double* y, const doub
  * y holds y(t0) on entry and the final state on exit. */
 static void rkc_system(const or_sys* s, double t, double tend, double rtol, double atol,
                        int max_attempts, double* y, or_counts* cnt, const double* carry_in,
-                       double* carry_out, int carry_mode) {
+                       double* carry_out, int carry_mode, int specrad_mode) {
     int n = s->neq;
-    double* mem = (double*)malloc(sizeof(double) * (size_t)n * 10);
+    double* mem = (double*)malloc(sizeof(double) * ((size_t)n * 10 + (size_t)n * n));
+    double* jac = mem + (size_t)n * 10;
     double* yn = mem;
     double* Fn = yn + n;
     double* Fnp1 = Fn + n;
@@ -633,7 +762,12 @@ static void rkc_system(const or_sys* s, double t, double tend, double rtol, doub
         if (1.1 * h >= fabs(tend - t)) h = fabs(tend - t);
 
         if (!have_sigma || rejected || (num_step % 25 == 0 && sr_step != num_step)) {
-            sigma = rkc_specrad(s, t, yn, Fn, hmax, v, tmp2, &cnt->n_specrad_iter, &cnt->status);
+            if (specrad_mode == SPECRAD_GERSHGORIN) {
+                sigma = gershgorin(s, yn, jac);
+            } else {
+                sigma = rkc_specrad(s, t, yn, Fn, hmax, v, tmp2, &cnt->n_specrad_iter, &cnt->status);
+                if (specrad_mode == SPECRAD_POWER_CAPPED) sigma = fmin(sigma, gershgorin(s, yn, jac));
+            }
             have_sigma = 1;
             sr_step = num_step;
         }
@@ -758,7 +892,7 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
                      const double* params, double t0, double tend, double rtol, double atol,
                      int max_attempts, double* y_out, int32_t* n_accept, int32_t* n_reject,
                      int32_t* n_rhs, int32_t* n_specrad_iter, int32_t* status, int nthreads,
-                     const double* carry_in, double* carry_out, int carry_mode) {
+                     const double* carry_in, double* carry_out, int carry_mode, int specrad_mode) {
     if (m->neq <= 0 || m->n_params > OR_MAX_PARAMS) return -1;
     int nt = resolve_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
@@ -781,7 +915,7 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
         if (method == 0)
             rkck_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout);
         else
-            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout, carry_mode);
+            rkc_system(&s, t0, tend, rtol, atol, max_attempts, y, &cnt, cin, cout, carry_mode, specrad_mode);
         for (int j = 0; j < m->neq; ++j) y_out[i + nsys * (int64_t)j] = y[j];
         if (cout)
             for (int w = 0; w < K; ++w) carry_out[i + nsys * (int64_t)w] = cout[w];
@@ -818,7 +952,7 @@ int oracle_integrate_ragged(const or_model* models, const int32_t* model_idx, in
         if (method[i] == 0)
             rkck_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL);
         else
-            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL, 0);
+            rkc_system(&s, t0[i], tend[i], rtol[i], atol[i], max_attempts, y, &cnt, NULL, NULL, 0, SPECRAD_POWER);
         if (n_accept) n_accept[i] = cnt.n_accept;
         if (n_reject) n_reject[i] = cnt.n_reject;
         if (n_rhs) n_rhs[i] = cnt.n_rhs;
@@ -892,6 +1026,21 @@ void oracle_fixed_steps(const or_model* m, const double* p, int method, int stag
     }
     for (int i = 0; i < n; ++i) yout[i] = y[i];
     free(mem);
+}
+
+void oracle_jacobian(const or_model* m, const double* p, const double* y, double* J) {
+    or_sys s;
+    sys_init(&s, m, m->neq, p, m->n_params);
+    jacobian(&s, y, J);
+}
+
+double oracle_gershgorin(const or_model* m, const double* p, const double* y) {
+    or_sys s;
+    sys_init(&s, m, m->neq, p, m->n_params);
+    double* J = (double*)malloc(sizeof(double) * (size_t)m->neq * m->neq);
+    double g = gershgorin(&s, y, J);
+    free(J);
+    return g;
 }
 
 double oracle_specrad(const or_model* m, const double* p, double t, const double* y, double hmax,

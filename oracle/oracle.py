@@ -18,6 +18,7 @@ KIND_LINEAR, KIND_TIME = 100, 101
 ST_OK, ST_H_UNDERFLOW, ST_MAX_ATTEMPTS, ST_NONFINITE, ST_SPECRAD_NOCONV = 0, 1, 2, 3, 256
 CARRY_FIXED = 9   # warm-restart state: valid, t, h, sigma, h_old, err_old, num_step, sr_step, rejected; then v
 CARRY_CONTINUE, CARRY_RESTART = 0, 1
+SPECRAD_POWER, SPECRAD_GERSHGORIN, SPECRAD_POWER_CAPPED = 0, 1, 2
 
 
 def carry_words(neq: int) -> int:
@@ -48,7 +49,10 @@ def lib():
         P = C.c_void_p
         L.oracle_integrate.argtypes = [P, C.c_int, C.c_int64, P, P, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_int, P, P, P, P, P, P, C.c_int, P, P,
-                                       C.c_int]
+                                       C.c_int, C.c_int]
+        L.oracle_jacobian.argtypes = [P, P, P, P]
+        L.oracle_gershgorin.argtypes = [P, P, P]
+        L.oracle_gershgorin.restype = C.c_double
         L.oracle_integrate_ragged.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int,
                                               P, P, P, P, P, P, C.c_int]
         L.oracle_rhs.argtypes = [P, P, C.c_double, P, P]
@@ -120,11 +124,13 @@ class Result:
 
 def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
               max_attempts: int = 1_000_000, nthreads: int = 0, carry_in=None,
-              carry_out: bool = False, carry_mode: int = CARRY_CONTINUE) -> Result:
+              carry_out: bool = False, carry_mode: int = CARRY_CONTINUE,
+              specrad: int = SPECRAD_POWER) -> Result:
     """Integrate a uniform SoA batch y0[neq, nsys]; method 0 = RKCK, 1 = RKC.
     carry_in (SoA [carry_words(neq), nsys]) resumes a previous call's
     controller state (carry_mode CARRY_CONTINUE or CARRY_RESTART); carry_out
-    returns this call's in ``Result.carry``."""
+    returns this call's in ``Result.carry``.  specrad: SPECRAD_POWER (the
+    Appendix power method), SPECRAD_GERSHGORIN or SPECRAD_POWER_CAPPED."""
     y0 = _f64(y0)
     params = _f64(params)
     nsys = y0.shape[1]
@@ -138,7 +144,7 @@ def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: f
     rc = lib().oracle_integrate(C.byref(m), method, nsys, _p(y0), _p(params), t0, tend, rtol,
                                 atol, max_attempts, _p(y), *[_p(a) for a in c], nthreads,
                                 _p(cin) if cin is not None else None, _p(cout) if cout is not None else None,
-                                carry_mode)
+                                carry_mode, specrad)
     if rc != 0:
         raise ValueError(f"oracle_integrate failed ({rc})")
     return Result(y, *c, carry=cout)
@@ -164,6 +170,20 @@ def integrate_mixed(b, nthreads: int = 0, max_attempts: int = 1_000_000) -> Resu
     lib().oracle_integrate_ragged(models, _p(midx), nsys, *[_p(a) for a in arrs], max_attempts,
                                   _p(y), *[_p(a) for a in c], nthreads)
     return Result(y, *c)
+
+
+def jacobian(m: Model, p, y) -> np.ndarray:
+    """The oracle's analytic Jacobian df/dy at y, [neq, neq]."""
+    p, y = _f64(p), _f64(y)
+    J = np.empty((m.neq, m.neq))
+    lib().oracle_jacobian(C.byref(m), _p(p), _p(y), _p(J))
+    return J
+
+
+def gershgorin(m: Model, p, y) -> float:
+    """The Gershgorin bound max_i sum_j |J_ij| at y."""
+    p, y = _f64(p), _f64(y)
+    return float(lib().oracle_gershgorin(C.byref(m), _p(p), _p(y)))
 
 
 def rhs(m: Model, p, y, t: float = 0.0) -> np.ndarray:
