@@ -441,6 +441,14 @@ static void sys_init(or_sys* s, const or_model* m, int neq, const double* p, int
     }
 }
 
+/* A model the fixed-size parameter store can hold (a linear test model
+ * needs neq^2 parameters). */
+static int model_fits(const or_model* m) {
+    if (m->neq <= 0 || m->n_params > OR_MAX_PARAMS) return 0;
+    if (m->kind == KIND_LINEAR && m->neq * m->neq > m->n_params) return 0;
+    return 1;
+}
+
 static int all_finite(const double* y, int n) {
     for (int i = 0; i < n; ++i)
         if (!isfinite(y[i])) return 0;
@@ -893,7 +901,7 @@ int oracle_integrate(const or_model* m, int method, int64_t nsys, const double* 
                      int max_attempts, double* y_out, int32_t* n_accept, int32_t* n_reject,
                      int32_t* n_rhs, int32_t* n_specrad_iter, int32_t* status, int nthreads,
                      const double* carry_in, double* carry_out, int carry_mode, int specrad_mode) {
-    if (m->neq <= 0 || m->n_params > OR_MAX_PARAMS) return -1;
+    if (!model_fits(m)) return -1;
     int nt = resolve_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int64_t i = 0; i < nsys; ++i) {
@@ -965,6 +973,10 @@ int oracle_integrate_ragged(const or_model* models, const int32_t* model_idx, in
 /* Single-system entry points used by the oracle's own tests. */
 
 void oracle_rhs(const or_model* m, const double* p, double t, const double* y, double* f) {
+    if (!model_fits(m)) {
+        for (int k = 0; k < m->neq; ++k) f[k] = NAN;
+        return;
+    }
     or_sys s;
     sys_init(&s, m, m->neq, p, m->n_params);
     dydt(&s, t, y, f);
@@ -1029,12 +1041,17 @@ void oracle_fixed_steps(const or_model* m, const double* p, int method, int stag
 }
 
 void oracle_jacobian(const or_model* m, const double* p, const double* y, double* J) {
+    if (!model_fits(m)) {
+        for (int k = 0; k < m->neq * m->neq; ++k) J[k] = NAN;
+        return;
+    }
     or_sys s;
     sys_init(&s, m, m->neq, p, m->n_params);
     jacobian(&s, y, J);
 }
 
 double oracle_gershgorin(const or_model* m, const double* p, const double* y) {
+    if (!model_fits(m)) return NAN;
     or_sys s;
     sys_init(&s, m, m->neq, p, m->n_params);
     double* J = (double*)malloc(sizeof(double) * (size_t)m->neq * m->neq);

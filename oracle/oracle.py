@@ -85,6 +85,7 @@ def _f64(a) -> np.ndarray:
 
 def model(kind: int, neq: int, n_params: int = 1, network=None, bruss=(1.0, 3.0, 1.0, 3.0),
           coupling: float = 0.1) -> Model:
+    assert n_params <= 300, "the oracle stores at most 300 parameters per system"
     m = Model()
     m.kind, m.neq, m.n_params = kind, neq, n_params
     m.bruss_A, m.bruss_B, m.bruss_ubc, m.bruss_vbc = bruss

@@ -69,11 +69,14 @@ def test_bound_is_exact_for_a_diagonal_matrix():
 def test_bound_of_the_laplacian():
     # tridiagonal (1, -2, 1) D: interior rows sum to 4 D, the spectral
     # radius 4 D sin^2(n pi / (2 (n + 1))) approaches it from below
-    n, D = 20, 3.0
+    n, D = 16, 3.0   # n^2 parameters: the oracle stores at most 300
     L = (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)) * D
     m = O.model(O.KIND_LINEAR, n, n * n)
     G = O.gershgorin(m, L.ravel(), np.ones(n))
     assert G == 4 * D
+    # a model too large for the parameter store is refused, not read past
+    big = O.model(O.KIND_LINEAR, 18, 300)
+    assert np.isnan(O.gershgorin(big, np.zeros(300), np.ones(18)))
     rho = 4 * D * np.sin(n * np.pi / (2 * (n + 1))) ** 2
     assert rho < G < 1.01 * rho
 
