@@ -304,6 +304,10 @@ def run_ours(args):
         mixed = mixed_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
             out["mixed_batch"] = mixed
+    if args.specrad_steps > 0:
+        sr = specrad_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["specrad_modes"] = sr
     if args.split_steps > 0:
         split = split_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
@@ -406,6 +410,56 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
                                 "FP32 accumulate"}
     res["speedup_with_proposal"] = res["without"]["ms_per_step"] / res["with_proposal"]["ms_per_step"]
     res["speedup_with_proposal_ordered"] = res["without"]["ms_per_step"] / res["with_proposal_ordered"]["ms_per_step"]
+    return res
+
+
+def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The chosen form on the mass-action batch with each spectral-radius
+    estimate: the Appendix's power method (the paper's), the Gershgorin
+    bound instead of it, and the power method capped by the bound."""
+    import torch.distributed as dist
+    w = W.massaction(nsys=args.nsys, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    y = torch.empty_like(y0)
+    cnt = B.counters_like(w.nsys, dev)
+    CH = B.ODE_PREC_MIXED_LEAN
+    B.prepare(h, "rkc", CH)
+    res = {}
+    ref = None
+    for name, mode in (("power", B.ODE_SPECRAD_POWER), ("gershgorin", B.ODE_SPECRAD_GERSHGORIN),
+                       ("power_capped", B.ODE_SPECRAD_POWER_CAPPED)):
+        def step(counters=None):
+            B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters, precision=CH,
+                        mapping=B.ODE_MAP_AUTO, specrad=mode, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.specrad_steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.specrad_steps
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        step(cnt)
+        torch.cuda.synchronize()
+        yy = y.cpu().numpy()
+        if ref is None:
+            ref = yy
+        e = (np.abs(yy - ref) / (np.abs(ref) + w.atol)).max(axis=0)
+        res[name] = {"systems_per_s": w.nsys * world / (ms * 1e-3), "ms_per_step": ms,
+                     "mean_rhs": float(cnt.n_rhs.float().mean().item()),
+                     "mean_power_iterations": float(cnt.n_specrad_iter.float().mean().item()),
+                     "p999_diff_vs_power": float(np.quantile(e, 0.999))}
+    B.release(h)
     return res
 
 
@@ -637,6 +691,7 @@ def main():
     ap.add_argument("--proposal-epochs", type=int, default=24)
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)
+    ap.add_argument("--specrad-steps", type=int, default=2, help="timed steps per spectral-radius mode (0 skips)")
     ap.add_argument("--split-steps", type=int, default=10, help="global steps of the outer-loop leg (0 skips it)")
     ap.add_argument("--split-reps", type=int, default=2)
     args = ap.parse_args()

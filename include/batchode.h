@@ -137,7 +137,8 @@ typedef struct {
     int32_t codegen;       /* ODE_CODEGEN_* (default AUTO) */
     int32_t cost_kind;     /* element type of `cost`: 0 = float32, 1 = int32 (e.g. a previous n_rhs) */
     int32_t carry_mode;    /* ODE_CARRY_CONTINUE (default) or ODE_CARRY_RESTART, see `carry` */
-    int32_t reserved[7];   /* must be zero */
+    int32_t specrad;       /* RKC spectral radius: ODE_SPECRAD_POWER (default) / _GERSHGORIN / _POWER_CAPPED */
+    int32_t reserved[6];   /* must be zero */
     /* RKC, mixed precisions: optional per-system proposals [nsys] (device
      * arrays, NaN = none) of the initial step and the spectral-radius bound,
      * e.g. from ode_mlp_propose.  A system with a finite positive pair skips
@@ -192,6 +193,22 @@ typedef struct {
 
 #define ODE_CARRY_CONTINUE 0
 #define ODE_CARRY_RESTART 1
+
+/* RKC spectral-radius estimate (opts->specrad).  The Appendix gives the
+ * nonlinear power method and names the Gershgorin circle theorem as an
+ * upper-bound alternative: every eigenvalue of the Jacobian J lies in a
+ * disc centred at J_ii of radius sum_{j != i} |J_ij|, so the spectral radius
+ * is at most G = max_i sum_j |J_ij| (the analytic Jacobian of each built-in
+ * right-hand side; row sums over the columns in increasing order).
+ *   POWER         the Appendix method, 1.2 x its estimate (the paper's)
+ *   GERSHGORIN    sigma = G wherever the power method would run: no
+ *                 right-hand-side evaluations, an estimate never below the
+ *                 true radius, but often above it (more stages per step)
+ *   POWER_CAPPED  the power method's value capped at G (the bound as a
+ *                 safety check: the 20 % margin never exceeds a rigorous bound) */
+#define ODE_SPECRAD_POWER 0
+#define ODE_SPECRAD_GERSHGORIN 1
+#define ODE_SPECRAD_POWER_CAPPED 2
 
 #define ODE_CARRY_FIXED 9
 #define ODE_CARRY_WORDS(neq) ((neq) + ODE_CARRY_FIXED)

@@ -54,7 +54,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
                 ("codegen", C.c_int32), ("cost_kind", C.c_int32), ("carry_mode", C.c_int32),
-                ("reserved", C.c_int32 * 7),
+                ("specrad", C.c_int32), ("reserved", C.c_int32 * 6),
                 ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p), ("cost", C.c_void_p),
                 ("carry", C.c_void_p)]
 
@@ -202,7 +202,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
               stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO, h0=None, sigma0=None,
-              log_xy=None, cost=None, carry=None, carry_mode: int = 0):
+              log_xy=None, cost=None, carry=None, carry_mode: int = 0, specrad: int = 0):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
     tensor for device io, numpy array for host io); returns y_out.  log_xy
     rows are [neq + 4]; cost (float32 [nsys], device) orders the batch
@@ -220,6 +220,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.h0, o.sigma0, o.log_xy, o.cost, o.carry = _ptr(h0), _ptr(sigma0), _ptr(log_xy), _ptr(cost), _ptr(carry)
     o.cost_kind = 1 if cost is not None and str(getattr(cost, "dtype", "")).endswith("int32") else 0
     o.carry_mode = carry_mode
+    o.specrad = specrad
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
@@ -385,6 +386,7 @@ class RaggedPlan:
 
 CARRY_FIXED = 9
 ODE_CARRY_CONTINUE, ODE_CARRY_RESTART = 0, 1
+ODE_SPECRAD_POWER, ODE_SPECRAD_GERSHGORIN, ODE_SPECRAD_POWER_CAPPED = 0, 1, 2
 
 
 def carry_words(neq: int) -> int:

@@ -286,8 +286,10 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     ode_opts opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 6; ++k)
         if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
+    if (opts.specrad < ODE_SPECRAD_POWER || opts.specrad > ODE_SPECRAD_POWER_CAPPED)
+        return fail(ODE_ERR_ARG, "unknown specrad mode %d", opts.specrad);
     if (opts.carry_mode != ODE_CARRY_CONTINUE && opts.carry_mode != ODE_CARRY_RESTART)
         return fail(ODE_ERR_ARG, "unknown carry_mode %d", opts.carry_mode);
     if (opts.cost_kind != 0 && opts.cost_kind != 1) return fail(ODE_ERR_ARG, "cost_kind must be 0 or 1");
@@ -378,6 +380,7 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     a.log_xy = opts.log_xy;
     a.carry = opts.carry;
     a.carry_mode = opts.carry_mode;
+    a.specrad = opts.specrad;
     a.rkc_tab64 = ws->tab64;
     a.rkc_tab32 = ws->tab32;
     a.rkc_tab_max = kRkcTabMax;

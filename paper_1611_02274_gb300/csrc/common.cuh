@@ -121,6 +121,7 @@ struct BatchArgs {
     // of system i at carry[i + nsys w], layout as in batchode.h
     double* carry;
     int32_t carry_mode;  // ODE_CARRY_CONTINUE / ODE_CARRY_RESTART
+    int32_t specrad;     // ODE_SPECRAD_POWER / _GERSHGORIN / _POWER_CAPPED (RKC)
 
     __host__ __device__ int64_t sys_of(int64_t k) const { return index ? (int64_t)index[k] : k; }
     __host__ __device__ int64_t cidx(int64_t i, int w) const { return i + nsys * (int64_t)w; }

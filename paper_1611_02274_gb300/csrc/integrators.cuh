@@ -401,6 +401,13 @@ struct RkcF64 {
         }
         if (1.1 * h >= fabs(tend - t)) h = fabs(tend - t);
         if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
+            if (a.specrad == ODE_SPECRAD_GERSHGORIN) {  // the bound replaces the power method
+                sigma = sys.gershgorin(tm, yn);
+                have_sigma = true;
+                sr_step = num_step;
+                after_sr(a);
+                return;
+            }
             sr_begin(tm);
             return;
         }
@@ -445,7 +452,7 @@ struct RkcF64 {
         if (sr_iter >= 2 && fabs(sig - sig_prev) <= fmax(sig, 1.0 / hmax) * 0.01) {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yn[s];
-            sr_end(a);
+            sr_end(a, tm);
             return;
         }
         if (d != 0.0) {
@@ -461,12 +468,13 @@ struct RkcF64 {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) v[s] = v[s] - yn[s];
             status |= ODE_ST_SPECRAD_NOCONV;
-            sr_end(a);
+            sr_end(a, tm);
         }
     }
 
-    __device__ void sr_end(const BatchArgs& a) {
+    __device__ void sr_end(const BatchArgs& a, const TM& tm) {
         sigma = 1.2 * sig;
+        if (a.specrad == ODE_SPECRAD_POWER_CAPPED) sigma = fmin(sigma, sys.gershgorin(tm, yn));
         have_sigma = true;
         sr_step = num_step;
         after_sr(a);
@@ -1033,6 +1041,13 @@ struct RkcMixed {
             if (1.1f * h >= remf) h = remf;
         }
         if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
+            if (a.specrad == ODE_SPECRAD_GERSHGORIN) {  // the bound replaces the power method
+                sigma = (HT)sys.gershgorin(tm, yh);
+                have_sigma = true;
+                sr_step = num_step;
+                after_sr(a);
+                return;
+            }
             sr_begin(tm);
             return;
         }
@@ -1080,7 +1095,7 @@ struct RkcMixed {
         if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) V(s) = V(s) - yh[s];
-            sr_end(a);
+            sr_end(a, tm);
             return;
         }
         if (d != 0.0f) {
@@ -1097,12 +1112,19 @@ struct RkcMixed {
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) V(s) = V(s) - yh[s];
             status |= ODE_ST_SPECRAD_NOCONV;
-            sr_end(a);
+            sr_end(a, tm);
         }
     }
 
-    __device__ void sr_end(const BatchArgs& a) {
+    __device__ void sr_end(const BatchArgs& a, const TM& tm) {
         sigma = (HT)1.2 * (HT)sig;
+        if (a.specrad == ODE_SPECRAD_POWER_CAPPED) {
+            const HT g = (HT)sys.gershgorin(tm, yh);
+            if constexpr (SPEC)
+                sigma = fmin(sigma, g);
+            else
+                sigma = fminf(sigma, g);
+        }
         have_sigma = true;
         sr_step = num_step;
         after_sr(a);

@@ -168,7 +168,53 @@ std::string model_source(const RhsEntry& r) {
         o << " }\n";
     }
     for (int s = 0; s < S; ++s) o << "      f[" << s << "] = a" << s << ";\n";
-    o << "    }\n"
+    o << "    }\n";
+    // Gershgorin bound, row by row: J_sl accumulates reaction by reaction
+    // -dr_j/dC_l per reactant occurrence of s, +dr_j/dC_l per product
+    // occurrence, dr_j/dC_l summed over the reactant occurrences of l; the
+    // row sum runs over the touched columns in increasing order
+    o << "    __device__ R gershgorin(const bode::Team<1>&, const R* y) const {\n"
+      << "      R g = R(0);\n";
+    for (int s = 0; s < S; ++s) {
+        std::vector<int> touched(S, 0);
+        std::ostringstream body;
+        for (int j = 0; j < NR; ++j) {
+            const int nr = net.n_reac[j];
+            int occ = 0, pocc = 0;
+            for (int q = 0; q < nr; ++q) occ += net.reac[j][q] == s;
+            for (int q = 0; q < net.n_prod[j]; ++q) pocc += net.prod[j][q] == s;
+            if (!occ && !pocc) continue;
+            body << "        {";
+            if (nr == 1)
+                body << " const R d0 = k[" << j << "];";
+            else
+                body << " const R d0 = k[" << j << "] * y[" << (int)net.reac[j][1] << "]; const R d1 = k[" << j
+                     << "] * y[" << (int)net.reac[j][0] << "];";
+            for (int l = 0; l < S; ++l) {
+                bool any = false;
+                for (int q = 0; q < nr; ++q) any = any || net.reac[j][q] == l;
+                if (!any) continue;
+                touched[l] = 1;
+                body << " { R dl = R(0);";
+                for (int q = 0; q < nr; ++q)
+                    if (net.reac[j][q] == l) body << " dl = dl + d" << q << ";";
+                for (int q = 0; q < occ; ++q) body << " J" << l << " = J" << l << " - dl;";
+                for (int q = 0; q < pocc; ++q) body << " J" << l << " = J" << l << " + dl;";
+                body << " }";
+            }
+            body << " }\n";
+        }
+        o << "      {\n";
+        for (int l = 0; l < S; ++l)
+            if (touched[l]) o << "        R J" << l << " = R(0);\n";
+        o << body.str() << "        R acc = R(0);";
+        for (int l = 0; l < S; ++l)
+            if (touched[l]) o << " acc = acc + bode::rabs(J" << l << ");";
+        o << "\n        g = bode::rmax(g, acc);\n"
+          << "      }\n";
+    }
+    o << "      return g;\n"
+      << "    }\n"
       << "  };\n"
       << "};\n";
     return o.str();

@@ -5,6 +5,9 @@
 // (R = double for the plain form, float for the mixed form) and provides
 //   comp(team, s)  component index held in slot s by this lane (-1 = unused)
 //   rhs(team, t, y, f)  f = f(t, y) on this lane's slots.
+//   gershgorin(team, y)  max_i sum_j |J_ij| of the analytic Jacobian J at y
+//                  (the Gershgorin bound on the spectral radius), each row
+//                  sum over its nonzero columns in increasing order
 // Grid families (Brusselator, oscillator chain) place grid point
 // g = q W + lane in slots 2q (u or x) and 2q + 1 (v), so stencil neighbours
 // are one lane away and come from shuffles.  Evaluation orders follow the
@@ -17,6 +20,21 @@
 #include "xmath.cuh"
 
 namespace bode {
+
+template <class R>
+__device__ __forceinline__ R rabs(R x) {
+    if constexpr (sizeof(R) == 8)
+        return fabs(x);
+    else
+        return fabsf(x);
+}
+template <class R>
+__device__ __forceinline__ R rmax(R a, R b) {
+    if constexpr (sizeof(R) == 8)
+        return fmax(a, b);
+    else
+        return fmaxf(a, b);
+}
 
 // van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1.  params [mu].
 struct VdpModel {
@@ -42,6 +60,12 @@ struct VdpModel {
         __device__ void rhs(const Team<W>&, R, const R* y, R* f) const {
             f[0] = y[1];
             f[1] = mu * (R(1) - y[0] * y[0]) * y[1] - y[0];
+        }
+        // rows: (0, 1) and (mu (-2 y1) y2 - 1, mu (1 - y1^2))
+        __device__ R gershgorin(const Team<W>&, const R* y) const {
+            const R j10 = mu * (R(-2) * y[0]) * y[1] - R(1);
+            const R j11 = mu * (R(1) - y[0] * y[0]);
+            return rmax(R(1), rabs(j10) + rabs(j11));
         }
     };
 };
@@ -110,6 +134,28 @@ struct ChainModel {
                 f[2 * q] = v;
                 f[2 * q + 1] = mu * (R(1) - x * x) * v - x + c * coup;
             }
+        }
+        // row x_i: one entry 1; row v_i: c (x_{i-1}), mu (-2 x) v - 1 - c nb
+        // (x_i), c (x_{i+1}), mu (1 - x^2) (v_i), neighbours that exist only
+        __device__ R gershgorin(const Team<W>& tm, const R* y) const {
+            R g = R(0);
+#pragma unroll(G <= 32 ? G : 2)
+            for (int q = 0; q < G; ++q) {
+                const int gp = q * W + tm.lane;
+                if (gp >= npts) continue;
+                const R x = y[2 * q], v = y[2 * q + 1];
+                const bool left = gp > 0, right = gp + 1 < npts;
+                const R nb = R((int)left + (int)right);
+                const R jxx = mu * (R(-2) * x) * v - R(1) - c * nb;
+                const R jvv = mu * (R(1) - x * x);
+                R acc = R(0);
+                if (left) acc = acc + rabs(c);
+                acc = acc + rabs(jxx);
+                if (right) acc = acc + rabs(c);
+                acc = acc + rabs(jvv);
+                g = rmax(g, rmax(R(1), acc));
+            }
+            return tm.max(g);
         }
     };
 };
@@ -191,6 +237,34 @@ struct BrussModel {
                 f[2 * q + 1] = B * u - uuv + D * (vl - R(2) * v + vr);
             }
         }
+        // row u_k: D (u_{k-1}), 2 u v - (B + 1) - 2 D (u_k), D (u_{k+1}), u^2 (v_k);
+        // row v_k: B - 2 u v (u_k), D (v_{k-1}), -u^2 - 2 D (v_k), D (v_{k+1});
+        // the Dirichlet ghosts are constants: no boundary neighbour entries
+        __device__ R gershgorin(const Team<W>& tm, const R* y) const {
+            R g = R(0);
+#pragma unroll(G <= 32 ? G : 2)
+            for (int q = 0; q < G; ++q) {
+                const int gp = q * W + tm.lane;
+                if (gp >= npts) continue;
+                const R u = y[2 * q], v = y[2 * q + 1];
+                const bool left = gp > 0, right = gp + 1 < npts;
+                const R juu = R(2) * u * v - B1 - R(2) * D;
+                const R juv = u * u;
+                const R jvu = B - R(2) * u * v;
+                const R jvv = -(u * u) - R(2) * D;
+                R ru = R(0), rv = R(0);
+                if (left) ru = ru + rabs(D);
+                ru = ru + rabs(juu);
+                if (right) ru = ru + rabs(D);
+                ru = ru + rabs(juv);
+                rv = rv + rabs(jvu);
+                if (left) rv = rv + rabs(D);
+                rv = rv + rabs(jvv);
+                if (right) rv = rv + rabs(D);
+                g = rmax(g, rmax(ru, rv));
+            }
+            return tm.max(g);
+        }
     };
 };
 
@@ -271,6 +345,44 @@ struct MassActionModel {
             }
 #pragma unroll
             for (int s = 0; s < NS; ++s) f[s] = acc[s];
+        }
+        // row by row: J_sl accumulates, reaction by reaction, -dr_j/dC_l for
+        // each reactant occurrence of s and +dr_j/dC_l for each product
+        // occurrence, dr_j/dC_l summed over the reactant occurrences of l
+        __device__ R gershgorin(const Team<W>&, const R* y) const {
+            const MassActionNet& nt = *net;
+            R g = R(0);
+            for (int s = 0; s < n; ++s) {
+                R J[NS];
+                for (int l = 0; l < NS; ++l) J[l] = R(0);
+                for (int j = 0; j < nt.n_reactions; ++j) {
+                    const int nr = nt.n_reac[j];
+                    int occ = 0;  // occurrences of s: reactant count, product count
+                    for (int q = 0; q < nr; ++q) occ += nt.reac[j][q] == s;
+                    int pocc = 0;
+                    for (int q = 0; q < nt.n_prod[j]; ++q) pocc += nt.prod[j][q] == s;
+                    if (occ == 0 && pocc == 0) continue;
+                    R d[2];
+                    d[0] = nr == 2 ? k[j] * y[nt.reac[j][1]] : k[j];
+                    d[1] = k[j] * y[nt.reac[j][0]];
+                    for (int l = 0; l < n; ++l) {
+                        R dl = R(0);
+                        bool any = false;
+                        for (int q = 0; q < nr; ++q)
+                            if (nt.reac[j][q] == l) {
+                                dl = dl + d[q];
+                                any = true;
+                            }
+                        if (!any) continue;
+                        for (int q = 0; q < occ; ++q) J[l] = J[l] - dl;
+                        for (int q = 0; q < pocc; ++q) J[l] = J[l] + dl;
+                    }
+                }
+                R acc = R(0);
+                for (int l = 0; l < n; ++l) acc = acc + rabs(J[l]);
+                g = rmax(g, acc);
+            }
+            return g;
         }
     };
 };
