@@ -101,6 +101,7 @@
 #define KIND_VDP_CHAIN 2
 #define KIND_BRUSS1D 3
 #define KIND_MASSACTION 4
+#define KIND_NBODY 5
 #define KIND_LINEAR 100    /* f = A y, A row-major in the params (tests only) */
 #define KIND_TIME 101      /* f_i = t (tests of the stage times only) */
 
@@ -113,6 +114,7 @@
 #define CARRY_WORDS(neq) (CARRY_FIXED + (neq))
 
 #define OR_MAX_REAC 64
+#define OR_MAX_BODIES 16
 #define OR_MAX_PARAMS 300
 
 typedef struct {
@@ -131,6 +133,7 @@ typedef struct {
     double kmin, kmax;
     double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
     double coupling;
+    double masses[OR_MAX_BODIES];
 } or_model;
 
 /* One system: the model, its dimension, its parameters and (mass-action)
@@ -200,6 +203,36 @@ static void rhs_massaction(const or_sys* s, const double* y, double* f) {
         for (int q = 0; q < m->n_reac[j]; ++q) r = r * y[m->reac[j][q]];
         for (int q = 0; q < m->n_reac[j]; ++q) f[m->reac[j][q]] -= r;
         for (int q = 0; q < m->n_prod[j]; ++q) f[m->prod[j][q]] += r;
+    }
+}
+
+/* Planar n-body gravity (the form of the Pleiades problem, Section 4.1),
+ * state [x_1..x_n, y_1..y_n, u_1..u_n, v_1..v_n], masses from the model,
+ * gravitational constant G the system's parameter:
+ * x_i' = u_i, y_i' = v_i, (u_i', v_i') = G sum_{j != i} m_j d_ij / r_ij^3,
+ * d_ij = (x_j - x_i, y_j - y_i), r_ij^3 = r2 sqrt(r2), j ascending. */
+static void rhs_nbody(const or_sys* s, const double* y, double* f) {
+    int n = s->neq / 4;
+    double G = s->p[0];
+    const double* x = y;
+    const double* yy = y + n;
+    for (int i = 0; i < n; ++i) {
+        f[i] = y[2 * n + i];
+        f[n + i] = y[3 * n + i];
+    }
+    for (int i = 0; i < n; ++i) {
+        double ax = 0.0, ay = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[j] - x[i];
+            double dy = yy[j] - yy[i];
+            double r2 = dx * dx + dy * dy;
+            double r3 = r2 * sqrt(r2);
+            ax = ax + s->m->masses[j] * dx / r3;
+            ay = ay + s->m->masses[j] * dy / r3;
+        }
+        f[2 * n + i] = G * ax;
+        f[3 * n + i] = G * ay;
     }
 }
 
@@ -300,6 +333,42 @@ static void jac_massaction(const or_sys* s, const double* y, double* J) {
     }
 }
 
+/* d(G m_j d / r^3)/dp_j = G m_j (I / r^3 - 3 d d^T / r^5); the body's own
+ * block is minus the sum of the others, subtracted j by j in order. */
+static void jac_nbody(const or_sys* s, const double* y, double* J) {
+    int n = s->neq / 4, N = s->neq;
+    double G = s->p[0];
+    const double* x = y;
+    const double* yy = y + n;
+    for (int k = 0; k < N * N; ++k) J[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        J[i * N + 2 * n + i] = 1.0;
+        J[(n + i) * N + 3 * n + i] = 1.0;
+        double* ru = J + (2 * n + i) * N;
+        double* rv = J + (3 * n + i) * N;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[j] - x[i];
+            double dy = yy[j] - yy[i];
+            double r2 = dx * dx + dy * dy;
+            double r3 = r2 * sqrt(r2);
+            double r5 = r3 * r2;
+            double gm = G * s->m->masses[j];
+            double axx = gm * (1.0 / r3 - 3.0 * dx * dx / r5);
+            double axy = gm * (-3.0 * dx * dy / r5);
+            double ayy = gm * (1.0 / r3 - 3.0 * dy * dy / r5);
+            ru[j] = axx;
+            ru[n + j] = axy;
+            rv[j] = axy;
+            rv[n + j] = ayy;
+            ru[i] -= axx;
+            ru[n + i] -= axy;
+            rv[i] -= axy;
+            rv[n + i] -= ayy;
+        }
+    }
+}
+
 static void jacobian(const or_sys* s, const double* y, double* J) {
     int N = s->neq;
     switch (s->m->kind) {
@@ -307,6 +376,7 @@ static void jacobian(const or_sys* s, const double* y, double* J) {
     case KIND_VDP_CHAIN: jac_vdp_chain(s, y, J); break;
     case KIND_BRUSS1D: jac_bruss(s, y, J); break;
     case KIND_MASSACTION: jac_massaction(s, y, J); break;
+    case KIND_NBODY: jac_nbody(s, y, J); break;
     case KIND_LINEAR:
         for (int k = 0; k < N * N; ++k) J[k] = s->p[k];
         break;
@@ -334,6 +404,7 @@ static void dydt(const or_sys* s, double t, const double* y, double* f) {
     case KIND_VDP_CHAIN: rhs_vdp_chain(s, y, f); break;
     case KIND_BRUSS1D: rhs_bruss(s, y, f); break;
     case KIND_MASSACTION: rhs_massaction(s, y, f); break;
+    case KIND_NBODY: rhs_nbody(s, y, f); break;
     case KIND_LINEAR: rhs_linear(s, y, f); break;
     case KIND_TIME:
         for (int i = 0; i < s->neq; ++i) f[i] = t;

@@ -13,7 +13,8 @@ import numpy as np
 from . import build as _build
 
 MAX_REAC = 64
-KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION = 1, 2, 3, 4
+KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION, KIND_NBODY = 1, 2, 3, 4, 5
+MAX_BODIES = 16
 KIND_LINEAR, KIND_TIME = 100, 101
 ST_OK, ST_H_UNDERFLOW, ST_MAX_ATTEMPTS, ST_NONFINITE, ST_SPECRAD_NOCONV = 0, 1, 2, 3, 256
 CARRY_FIXED = 9   # warm-restart state: valid, t, h, sigma, h_old, err_old, num_step, sr_step, rejected; then v
@@ -34,7 +35,7 @@ class Model(C.Structure):
         ("log10A", C.c_double * MAX_REAC), ("beta", C.c_double * MAX_REAC),
         ("Ea", C.c_double * MAX_REAC), ("kmin", C.c_double), ("kmax", C.c_double),
         ("bruss_A", C.c_double), ("bruss_B", C.c_double), ("bruss_ubc", C.c_double),
-        ("bruss_vbc", C.c_double), ("coupling", C.c_double),
+        ("bruss_vbc", C.c_double), ("coupling", C.c_double), ("masses", C.c_double * MAX_BODIES),
     ]
 
 
@@ -84,12 +85,16 @@ def _f64(a) -> np.ndarray:
 
 
 def model(kind: int, neq: int, n_params: int = 1, network=None, bruss=(1.0, 3.0, 1.0, 3.0),
-          coupling: float = 0.1) -> Model:
+          coupling: float = 0.1, masses=None) -> Model:
     assert n_params <= 300, "the oracle stores at most 300 parameters per system"
     m = Model()
     m.kind, m.neq, m.n_params = kind, neq, n_params
     m.bruss_A, m.bruss_B, m.bruss_ubc, m.bruss_vbc = bruss
     m.coupling = coupling
+    if masses is not None:
+        assert len(masses) <= MAX_BODIES and kind == KIND_NBODY and neq == 4 * len(masses)
+        for i, mi in enumerate(masses):
+            m.masses[i] = float(mi)
     if network is not None:
         R = network.n_reactions
         assert R <= MAX_REAC
@@ -109,7 +114,7 @@ def model(kind: int, neq: int, n_params: int = 1, network=None, bruss=(1.0, 3.0,
 
 def model_for(w) -> Model:
     """The oracle model of a ``workloads.Workload``."""
-    return model(w.kind, w.neq, w.params.shape[0], network=w.network)
+    return model(w.kind, w.neq, w.params.shape[0], network=w.network, masses=w.aux.get("masses"))
 
 
 @dataclass

@@ -40,6 +40,7 @@ RHS_VDP = 1
 RHS_VDP_CHAIN = 2
 RHS_BRUSS1D = 3
 RHS_MASSACTION = 4
+RHS_NBODY = 5
 
 METHOD_RKCK = 0
 METHOD_RKC = 1
@@ -109,6 +110,40 @@ def vdp(nsys: int = 4096, seed: int = 0) -> Workload:
     y0 = rng.uniform(-2.0, 2.0, size=(2, nsys))
     return Workload("vdp", RHS_VDP, METHOD_RKCK, nsys, 2, np.ascontiguousarray(y0),
                     mu[None, :].copy(), 0.0, 20.0, 1e-6, 1e-9)
+
+
+def pleiades_base(n: int = 7, base_seed: int = 0):
+    """A planar n-body configuration of the Pleiades problem's shape (masses
+    1..n, G = 1): bodies spread around a ring of radius 1.5-3.5 with roughly
+    bound tangential velocities, pairwise separations at least 0.8, zero
+    total momentum.  Returns (masses, state [x.., y.., u.., v..])."""
+    rng = _rng(base_seed)
+    m = np.arange(1, n + 1, dtype=np.float64)
+    while True:
+        ang = 2 * np.pi * np.arange(n) / n + rng.uniform(-0.3, 0.3, n)
+        rad = rng.uniform(1.5, 3.5, n)
+        x, y = rad * np.cos(ang), rad * np.sin(ang)
+        d = np.hypot(x[:, None] - x[None, :], y[:, None] - y[None, :]) + np.eye(n) * 1e9
+        if d.min() >= 0.8:
+            break
+    speed = 0.5 * np.sqrt(m.sum() / rad) * rng.uniform(0.8, 1.2, n)
+    u, v = -speed * np.sin(ang), speed * np.cos(ang)
+    u -= (m * u).sum() / m.sum()
+    v -= (m * v).sum() / m.sum()
+    return m, np.concatenate([x, y, u, v])
+
+
+def pleiades(nsys: int = 262144, seed: int = 0, n: int = 7, perturb: float = 1e-3,
+             tend: float = 1.0) -> Workload:
+    """Copies of one n-body configuration (pleiades_base) with perturbed
+    initial states (each component + perturb * N(0, 1), the paper's
+    perturbed-IC batch), integrated by RKCK with eps = 1e-10 over [0, tend]."""
+    m, base = pleiades_base(n)
+    rng = _rng(seed)
+    y0 = base[:, None] + perturb * rng.standard_normal((4 * n, nsys))
+    G = np.ones((1, nsys))
+    return Workload("pleiades", RHS_NBODY, METHOD_RKCK, nsys, 4 * n, np.ascontiguousarray(y0), G,
+                    0.0, tend, 1e-10, 1e-10, aux={"masses": m})
 
 
 def bruss(nsys: int = 65536, n: int = 32, seed: int = 0) -> Workload:
