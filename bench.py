@@ -304,6 +304,10 @@ def run_ours(args):
         mixed = mixed_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
             out["mixed_batch"] = mixed
+    if args.pleiades_nsys > 0:
+        pl = pleiades_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["pleiades_rkck"] = pl
     if args.specrad_steps > 0:
         sr = specrad_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
@@ -411,6 +415,71 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     res["speedup_with_proposal"] = res["without"]["ms_per_step"] / res["with_proposal"]["ms_per_step"]
     res["speedup_with_proposal_ordered"] = res["without"]["ms_per_step"] / res["with_proposal_ordered"]["ms_per_step"]
     return res
+
+
+def pleiades_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The paper's RKCK benchmark shape (Section 4.1): copies of a seven-body
+    planar gravity problem (28 equations) with perturbed initial states,
+    eps = 1e-10, t in [0, 1], plain FP64 (the tolerance is beyond FP32
+    stages), one 8-lane team per system; against the oracle on the host
+    cores."""
+    import torch.distributed as dist
+    import oracle as O
+    w = W.pleiades(nsys=args.pleiades_nsys, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    y = torch.empty_like(y0)
+    cnt = B.counters_like(w.nsys, dev)
+
+    def step(counters=None):
+        B.integrate("rkck", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters,
+                    precision=B.ODE_PREC_FP64, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.pleiades_steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.pleiades_steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    step(cnt)
+    torch.cuda.synchronize()
+    c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "status")}
+    yg = y.cpu().numpy()
+    B.release(h)
+    # RHS: per body 6 flops per other body (differences, r2) + sqrt + 2 mult/div pairs; count
+    # 20 flops per pair and direction as the algorithmic work, FP64
+    n = w.neq // 4
+    rhs_flops = 20 * n * (n - 1)
+    flops = float(np.sum(c["n_rhs"])) * rhs_flops + float(np.sum(c["n_accept"] + c["n_reject"])) * 60 * w.neq
+    sample = np.arange(min(w.nsys, 4096))
+    t0 = time.perf_counter()
+    ref = O.integrate_workload(W.subset(w, sample))
+    cpu_s = time.perf_counter() - t0
+    same = (c["n_accept"][sample] == ref.n_accept) & (c["n_reject"][sample] == ref.n_reject)
+    e = (np.abs(yg[:, sample] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+    return {"systems_per_s": w.nsys * world / (ms * 1e-3), "ms_per_step": ms,
+            "mean_attempts": float(np.mean(c["n_accept"] + c["n_reject"])),
+            "rhs_evals_per_s": float(np.sum(c["n_rhs"])) * world / (ms * 1e-3),
+            "achieved_tflops_fp64": flops / (ms * 1e-3) / 1e12,
+            "frac_fp64_peak": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "status_ok_frac": float(np.mean(c["status"] == 0)),
+            "parity_sample": {"systems": int(sample.size), "same_counts_frac": float(same.mean()),
+                              "max_rel_err_same_counts": float(e[same].max()) if same.any() else None},
+            "cpu_oracle_systems_per_s": sample.size / cpu_s, "cpu_cores": os.cpu_count(),
+            "config": {"nsys_per_gpu": w.nsys, "bodies": n, "neq": w.neq, "eps": w.rtol,
+                       "interval": [w.t0, w.tend], "perturbation": 1e-3,
+                       "flops_model": "20 per ordered pair per evaluation + 60 per unknown per attempt"}}
 
 
 def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
@@ -692,6 +761,8 @@ def main():
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)
     ap.add_argument("--specrad-steps", type=int, default=2, help="timed steps per spectral-radius mode (0 skips)")
+    ap.add_argument("--pleiades-nsys", type=int, default=262144, help="n-body RKCK leg batch (0 skips)")
+    ap.add_argument("--pleiades-steps", type=int, default=3)
     ap.add_argument("--split-steps", type=int, default=10, help="global steps of the outer-loop leg (0 skips it)")
     ap.add_argument("--split-reps", type=int, default=2)
     args = ap.parse_args()

@@ -70,6 +70,11 @@ extern "C" {
 #define ODE_RHS_MASSACTION 4 /* mass-action kinetics (Section 4.2 omega_i with constant T), Arrhenius
                                 k_j = clip(10^log10A_j T^beta_j exp(-Ea_j / T), kmin, kmax);
                                 params [T]; neq = n_species */
+#define ODE_RHS_NBODY 5      /* planar n-body gravity (the Pleiades problem's form, Section 4.1),
+                                [x_1..x_n, y_1..y_n, u_1..u_n, v_1..v_n]: x' = u, y' = v,
+                                (u_i', v_i') = G sum_{j != i} m_j d_ij / |d_ij|^3,
+                                d_ij = (x_j - x_i, y_j - y_i), j ascending; masses from the
+                                descriptor; params [G]; neq 4n, n <= 16 */
 
 /* precision of the integrator */
 #define ODE_PREC_FP64 0      /* plain form: every operation in FP64, as the paper's listings */
@@ -125,6 +130,8 @@ typedef struct {
     double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
     /* ODE_RHS_VDP_CHAIN only */
     double coupling;
+    /* ODE_RHS_NBODY only: neq / 4 body masses (host pointer, copied; > 0) */
+    const double* masses;
 } ode_rhs_desc;
 
 typedef struct {
@@ -230,7 +237,7 @@ typedef struct {
  * network arrays) is validated and copied; *rhs_handle receives a positive
  * handle.  Errors: ODE_ERR_ARG for an unknown kind, neq out of range
  * (VDP: 2; chain: even, 2..128; Brusselator: even, 2..256; mass-action: 1..32 species,
- * 1..64 reactions) or bad indices. */
+ * 1..64 reactions; n-body: multiple of 4, 4..64) or bad indices / masses. */
 int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle);
 
 /* Release a handle.  ODE_ERR_HANDLE if it is not registered. */

@@ -113,6 +113,17 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
         r->bruss_ubc = d->bruss_ubc;
         r->bruss_vbc = d->bruss_vbc;
         return ODE_OK;
+    case ODE_RHS_NBODY: {
+        if (d->neq < 4 || d->neq > 4 * kMaxBodies || d->neq % 4)
+            return fail(ODE_ERR_ARG, "n-body neq must be a multiple of 4 in [4, %d]", 4 * kMaxBodies);
+        if (!d->masses) return fail(ODE_ERR_ARG, "n-body masses must be non-NULL");
+        for (int b = 0; b < d->neq / 4; ++b) {
+            if (!(d->masses[b] > 0.0) || !std::isfinite(d->masses[b]))
+                return fail(ODE_ERR_ARG, "body %d: mass must be finite and > 0", b);
+            r->masses[b] = d->masses[b];
+        }
+        return ODE_OK;
+    }
     case ODE_RHS_MASSACTION: {
         const int S = d->neq, R = d->n_reactions;
         if (S < 1 || S > kMaxSpecies) return fail(ODE_ERR_ARG, "mass-action species count must be in [1, %d]", kMaxSpecies);
@@ -174,6 +185,7 @@ int dispatch(const RhsEntry& rhs, int meth, int prec, bool use_jit, const BatchA
         break;
     case ODE_RHS_BRUSS1D: e = launch_bruss(meth, prec, rhs, a, cfg, &supported); break;
     case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, prec, rhs, a, cfg, &supported); break;
+    case ODE_RHS_NBODY: e = launch_nbody(meth, prec, rhs, a, cfg, &supported); break;
     default: supported = false; e = cudaSuccess;
     }
     if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built for this method", rhs.kind, rhs.neq);

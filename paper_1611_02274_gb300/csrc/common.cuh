@@ -69,6 +69,9 @@ enum : int {
     kCarryRejected, kCarryFixed
 };
 
+// Bodies of the largest registered n-body system.
+constexpr int kMaxBodies = 16;
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 

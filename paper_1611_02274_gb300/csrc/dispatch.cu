@@ -13,6 +13,8 @@ cudaError_t launch_bruss_f64(int method, const RhsEntry& r, const BatchArgs& a, 
 cudaError_t launch_bruss_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_nbody_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_nbody_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 namespace {
 inline bool f64(int prec) { return prec == ODE_PREC_FP64; }
@@ -34,6 +36,10 @@ cudaError_t launch_bruss(int method, int prec, const RhsEntry& r, const BatchArg
 
 cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     return f64(prec) ? launch_chain_f64(method, r, a, c, ok) : launch_chain_mixed(method, prec, r, a, c, ok);
+}
+
+cudaError_t launch_nbody(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+    return f64(prec) ? launch_nbody_f64(method, r, a, c, ok) : launch_nbody_mixed(method, prec, r, a, c, ok);
 }
 
 }  // namespace bode

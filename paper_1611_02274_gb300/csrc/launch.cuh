@@ -17,6 +17,7 @@ struct RhsEntry {
     MassActionNet net;
     double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
     double coupling;
+    double masses[kMaxBodies];
 };
 
 // Launch configuration resolved by the API layer.
@@ -58,6 +59,7 @@ cudaError_t launch_vdp(int method, int prec, const RhsEntry& r, const BatchArgs&
 cudaError_t launch_mass(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_bruss(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_nbody(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 // Builds the RKC stage-coefficient tables on the current device.
 cudaError_t build_rkc_tables(double* tab64, float4* tab32, int mmax, cudaStream_t s);

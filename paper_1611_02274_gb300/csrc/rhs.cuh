@@ -268,6 +268,123 @@ struct BrussModel {
     };
 };
 
+struct NbodyCtx {
+    double m[kMaxBodies];  // body masses
+};
+
+// Planar n-body gravity (the Pleiades problem's form), one body per lane
+// (n <= W): slots 0..3 of lane b hold x_b, y_b, u_b, v_b; the other bodies'
+// positions come from shuffles, taken in ascending order j as in the
+// defining sum.  The plain form evaluates m_j d / (r2 sqrt(r2)) as written;
+// the mixed form uses the reciprocal square root.  params [G].
+template <int W_>
+struct NbodyModel {
+    static constexpr int W = W_, PER = 4;
+    using Ctx = NbodyCtx;
+    template <class R>
+    struct Sys {
+        R G;
+        R m[W_];
+        int n, nb;
+        __device__ void load(const Ctx& ctx, const Team<W>&, double g, int neq) {
+            G = (R)g;
+            n = neq;
+            nb = neq / 4;
+#pragma unroll
+            for (int j = 0; j < W_; ++j) m[j] = (R)(j < nb ? ctx.m[j] : 0.0);
+        }
+        __device__ int comp(const Team<W>& tm, int s) const { return tm.lane < nb ? s * nb + tm.lane : -1; }
+        // sum over components in component order (x, then y, u, v)
+        template <class T>
+        __device__ T ordered_sum(const Team<W>& tm, const T* x) const {
+            T acc = T(0);
+#pragma unroll
+            for (int fld = 0; fld < 4; ++fld)
+#pragma unroll
+                for (int l = 0; l < W_; ++l) {
+                    const T v = tm.bcast(x[fld], l);
+                    if (l < nb) acc = acc + v;
+                }
+            return acc;
+        }
+        __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
+            const R x = y[0], yy = y[1];
+            R ax = R(0), ay = R(0);
+#pragma unroll
+            for (int j = 0; j < W_; ++j) {
+                const R xj = tm.bcast(x, j), yj = tm.bcast(yy, j);
+                if (j < nb && j != tm.lane) {
+                    const R dx = xj - x, dy = yj - yy;
+                    const R r2 = dx * dx + dy * dy;
+                    if constexpr (sizeof(R) == 8) {
+                        const R r3 = r2 * sqrt(r2);
+                        ax = ax + m[j] * dx / r3;
+                        ay = ay + m[j] * dy / r3;
+                    } else {
+                        const R ir = rsqrtf(r2);
+                        const R w = m[j] * (ir * ir * ir);
+                        ax = fmaf(w, dx, ax);
+                        ay = fmaf(w, dy, ay);
+                    }
+                }
+            }
+            f[0] = y[2];
+            f[1] = y[3];
+            f[2] = G * ax;
+            f[3] = G * ay;
+        }
+        // (xx, xy, yy) block of d(acceleration of this body)/d(position of
+        // body j): G m_j (I / r^3 - 3 d d^T / r^5), as the Jacobian writes it
+        __device__ void block(R x, R yy, R xj, R yj, int j, R& bxx, R& bxy, R& byy) const {
+            const R dx = xj - x, dy = yj - yy;
+            const R r2 = dx * dx + dy * dy;
+            R r3;
+            if constexpr (sizeof(R) == 8)
+                r3 = r2 * sqrt(r2);
+            else
+                r3 = r2 * sqrtf(r2);
+            const R r5 = r3 * r2;
+            const R gm = G * m[j];
+            bxx = gm * (R(1) / r3 - R(3) * dx * dx / r5);
+            bxy = gm * (R(-3) * dx * dy / r5);
+            byy = gm * (R(1) / r3 - R(3) * dy * dy / r5);
+        }
+        // rows x_i, y_i: one entry 1; rows u_i, v_i over the x columns then
+        // the y columns, the own block being minus the sum of the others
+        // (three passes, the blocks recomputed instead of kept)
+        __device__ R gershgorin(const Team<W>& tm, const R* y) const {
+            const R x = y[0], yy = y[1];
+            const int i = tm.lane;
+            R dxx = R(0), dxy = R(0), dyy = R(0);
+#pragma unroll
+            for (int j = 0; j < W_; ++j) {
+                const R xj = tm.bcast(x, j), yj = tm.bcast(yy, j);
+                if (j < nb && j != i) {
+                    R bxx, bxy, byy;
+                    block(x, yy, xj, yj, j, bxx, bxy, byy);
+                    dxx = dxx - bxx;
+                    dxy = dxy - bxy;
+                    dyy = dyy - byy;
+                }
+            }
+            R ru = R(0), rv = R(0);
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass)  // x columns, then y columns
+#pragma unroll
+                for (int j = 0; j < W_; ++j) {
+                    const R xj = tm.bcast(x, j), yj = tm.bcast(yy, j);
+                    if (j < nb) {
+                        R bxx = dxx, bxy = dxy, byy = dyy;
+                        if (j != i) block(x, yy, xj, yj, j, bxx, bxy, byy);
+                        ru = ru + rabs(pass == 0 ? bxx : bxy);
+                        rv = rv + rabs(pass == 0 ? bxy : byy);
+                    }
+                }
+            return tm.max(i < nb ? rmax(R(1), rmax(ru, rv)) : R(0));
+        }
+    };
+};
+
 // Mass-action kinetics with a registered network (Section 4.2 omega_i at
 // constant T): r_j = k_j prod_{reactants} C, C_s' = sum_j (nu''_sj - nu'_sj) r_j,
 // accumulated over reactions in order, reactants then products.  params [T].

@@ -42,4 +42,10 @@ inline GridCtx grid_ctx(const RhsEntry& r) {
     return GridCtx{r.bruss_A, r.bruss_B, r.bruss_ubc, r.bruss_vbc, r.coupling};
 }
 
+inline NbodyCtx nbody_ctx(const RhsEntry& r) {
+    NbodyCtx c;
+    for (int b = 0; b < kMaxBodies; ++b) c.m[b] = b < r.neq / 4 ? r.masses[b] : 0.0;
+    return c;
+}
+
 }  // namespace bode
