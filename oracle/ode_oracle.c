@@ -102,6 +102,8 @@
 #define KIND_BRUSS1D 3
 #define KIND_MASSACTION 4
 #define KIND_NBODY 5
+#define KIND_KINETICS 6
+#define R_GAS 8.314462618
 #define KIND_LINEAR 100    /* f = A y, A row-major in the params (tests only) */
 #define KIND_TIME 101      /* f_i = t (tests of the stage times only) */
 
@@ -116,6 +118,23 @@
 #define OR_MAX_REAC 64
 #define OR_MAX_BODIES 16
 #define OR_MAX_PARAMS 300
+
+/* A constant-volume gas mechanism (KIND_KINETICS): molecular weights,
+ * polynomial thermodynamics (cp/R = a0 + a1 T + a2 T^2, h/(R T) = a0
+ * + a1 T / 2 + a2 T^2 / 3 + a3 / T) and irreversible reactions. */
+typedef struct {
+    int32_t n_species, n_reactions;
+    const double* W;        /* [S] kg/mol */
+    const double* thermo;   /* [S][4] */
+    const int32_t* n_reac;  /* [R] */
+    const int32_t* reac;    /* [R][2] */
+    const int32_t* n_prod;
+    const int32_t* prod;
+    const double* log10A;   /* [R] */
+    const double* beta;
+    const double* Ea;       /* Kelvin */
+    double kmin, kmax;
+} or_mech;
 
 typedef struct {
     int32_t kind;
@@ -134,6 +153,7 @@ typedef struct {
     double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
     double coupling;
     double masses[OR_MAX_BODIES];
+    const or_mech* mech;  /* KIND_KINETICS */
 } or_model;
 
 /* One system: the model, its dimension, its parameters and (mass-action)
@@ -234,6 +254,54 @@ static void rhs_nbody(const or_sys* s, const double* y, double* f) {
         f[2 * n + i] = G * ax;
         f[3 * n + i] = G * ay;
     }
+}
+
+/* Constant-volume kinetics (Section 4.2), state (T, Y_1..Y_S), density
+ * rho the system's parameter:
+ *   C_i = rho Y_i / W_i,  k_j = clip(A_j T^beta_j exp(-Ea_j / T)),
+ *   q_j = k_j prod_{reactants} C,  omega_i = sum_j (nu''_ij - nu'_ij) q_j
+ *   (reaction by reaction, reactants then products),
+ *   dY_i/dt = W_i omega_i / rho,
+ *   dT/dt = -(sum_i e_i omega_i W_i) / (rho c_v),  c_v = sum_i Y_i c_v,i,
+ *   c_v,i = (R / W_i)(cp_i/R - 1),  e_i = (R T / W_i)(h_i/(R T) - 1),
+ * species sums in species order. */
+static double or_exp(double x);
+static double or_log(double x);
+
+static double kin_rate(const or_mech* k, int j, double T, double lnT) {
+    const double ln10 = 2.302585092994046;
+    double kk = or_exp(ln10 * k->log10A[j] + k->beta[j] * lnT - k->Ea[j] / T);
+    return fmin(fmax(kk, k->kmin), k->kmax);
+}
+
+static void rhs_kinetics(const or_sys* s, const double* y, double* f) {
+    const or_mech* k = s->m->mech;
+    int S = k->n_species;
+    double rho = s->p[0];
+    double T = y[0];
+    const double* Y = y + 1;
+    double* om = f + 1;
+    double lnT = or_log(T);
+    for (int i = 0; i < S; ++i) om[i] = 0.0;
+    for (int j = 0; j < k->n_reactions; ++j) {
+        double q = kin_rate(k, j, T, lnT);
+        for (int r = 0; r < k->n_reac[j]; ++r) {
+            int i = k->reac[2 * j + r];
+            q = q * (rho * Y[i] / k->W[i]);
+        }
+        for (int r = 0; r < k->n_reac[j]; ++r) om[k->reac[2 * j + r]] -= q;
+        for (int r = 0; r < k->n_prod[j]; ++r) om[k->prod[2 * j + r]] += q;
+    }
+    double cv = 0.0, heat = 0.0;
+    for (int i = 0; i < S; ++i) {
+        const double* a = k->thermo + 4 * i;
+        double cvi = (R_GAS / k->W[i]) * (a[0] + a[1] * T + a[2] * T * T - 1.0);
+        double ei = (R_GAS * T / k->W[i]) * (a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] / T - 1.0);
+        cv = cv + Y[i] * cvi;
+        heat = heat + ei * om[i] * k->W[i];
+    }
+    f[0] = -heat / (rho * cv);
+    for (int i = 0; i < S; ++i) om[i] = k->W[i] * om[i] / rho;
 }
 
 static void rhs_linear(const or_sys* s, const double* y, double* f) {
@@ -405,6 +473,7 @@ static void dydt(const or_sys* s, double t, const double* y, double* f) {
     case KIND_BRUSS1D: rhs_bruss(s, y, f); break;
     case KIND_MASSACTION: rhs_massaction(s, y, f); break;
     case KIND_NBODY: rhs_nbody(s, y, f); break;
+    case KIND_KINETICS: rhs_kinetics(s, y, f); break;
     case KIND_LINEAR: rhs_linear(s, y, f); break;
     case KIND_TIME:
         for (int i = 0; i < s->neq; ++i) f[i] = t;

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 MAX_REAC = 64
-KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION, KIND_NBODY = 1, 2, 3, 4, 5
+KIND_VDP, KIND_VDP_CHAIN, KIND_BRUSS1D, KIND_MASSACTION, KIND_NBODY, KIND_KINETICS = 1, 2, 3, 4, 5, 6
 MAX_BODIES = 16
 KIND_LINEAR, KIND_TIME = 100, 101
 ST_OK, ST_H_UNDERFLOW, ST_MAX_ATTEMPTS, ST_NONFINITE, ST_SPECRAD_NOCONV = 0, 1, 2, 3, 256
@@ -36,6 +36,18 @@ class Model(C.Structure):
         ("Ea", C.c_double * MAX_REAC), ("kmin", C.c_double), ("kmax", C.c_double),
         ("bruss_A", C.c_double), ("bruss_B", C.c_double), ("bruss_ubc", C.c_double),
         ("bruss_vbc", C.c_double), ("coupling", C.c_double), ("masses", C.c_double * MAX_BODIES),
+        ("mech", C.c_void_p),
+    ]
+
+
+class Mech(C.Structure):
+    """A kinetics mechanism for KIND_KINETICS (pointers into numpy arrays
+    that the owning Model keeps alive)."""
+    _fields_ = [
+        ("n_species", C.c_int32), ("n_reactions", C.c_int32),
+        ("W", C.c_void_p), ("thermo", C.c_void_p), ("n_reac", C.c_void_p), ("reac", C.c_void_p),
+        ("n_prod", C.c_void_p), ("prod", C.c_void_p), ("log10A", C.c_void_p), ("beta", C.c_void_p),
+        ("Ea", C.c_void_p), ("kmin", C.c_double), ("kmax", C.c_double),
     ]
 
 
@@ -85,12 +97,27 @@ def _f64(a) -> np.ndarray:
 
 
 def model(kind: int, neq: int, n_params: int = 1, network=None, bruss=(1.0, 3.0, 1.0, 3.0),
-          coupling: float = 0.1, masses=None) -> Model:
+          coupling: float = 0.1, masses=None, mechanism=None) -> Model:
     assert n_params <= 300, "the oracle stores at most 300 parameters per system"
     m = Model()
     m.kind, m.neq, m.n_params = kind, neq, n_params
     m.bruss_A, m.bruss_B, m.bruss_ubc, m.bruss_vbc = bruss
     m.coupling = coupling
+    if mechanism is not None:
+        assert kind == KIND_KINETICS and neq == mechanism.n_species + 1
+        mk = mechanism
+        arrs = {"W": _f64(mk.W), "thermo": _f64(mk.thermo), "n_reac": np.ascontiguousarray(mk.n_reac, np.int32),
+                "reac": np.ascontiguousarray(np.where(mk.reac < 0, 0, mk.reac), np.int32),
+                "n_prod": np.ascontiguousarray(mk.n_prod, np.int32),
+                "prod": np.ascontiguousarray(np.where(mk.prod < 0, 0, mk.prod), np.int32),
+                "log10A": _f64(mk.log10A), "beta": _f64(mk.beta), "Ea": _f64(mk.Ea)}
+        me = Mech()
+        me.n_species, me.n_reactions = mk.n_species, mk.n_reactions
+        for k, a in arrs.items():
+            setattr(me, k, a.ctypes.data)
+        me.kmin, me.kmax = mk.kmin, mk.kmax
+        m.mech = C.addressof(me)
+        m._keep = (me, arrs)     # the model owns the mechanism's memory
     if masses is not None:
         assert len(masses) <= MAX_BODIES and kind == KIND_NBODY and neq == 4 * len(masses)
         for i, mi in enumerate(masses):
@@ -114,7 +141,8 @@ def model(kind: int, neq: int, n_params: int = 1, network=None, bruss=(1.0, 3.0,
 
 def model_for(w) -> Model:
     """The oracle model of a ``workloads.Workload``."""
-    return model(w.kind, w.neq, w.params.shape[0], network=w.network, masses=w.aux.get("masses"))
+    return model(w.kind, w.neq, w.params.shape[0], network=w.network, masses=w.aux.get("masses"),
+                 mechanism=w.aux.get("mechanism"))
 
 
 @dataclass

@@ -41,6 +41,9 @@ RHS_VDP_CHAIN = 2
 RHS_BRUSS1D = 3
 RHS_MASSACTION = 4
 RHS_NBODY = 5
+RHS_KINETICS = 6
+
+R_GAS = 8.314462618  # J / (mol K)
 
 METHOD_RKCK = 0
 METHOD_RKC = 1
@@ -110,6 +113,110 @@ def vdp(nsys: int = 4096, seed: int = 0) -> Workload:
     y0 = rng.uniform(-2.0, 2.0, size=(2, nsys))
     return Workload("vdp", RHS_VDP, METHOD_RKCK, nsys, 2, np.ascontiguousarray(y0),
                     mu[None, :].copy(), 0.0, 20.0, 1e-6, 1e-9)
+
+
+@dataclass
+class Mechanism:
+    """A closed constant-volume gas mechanism (Section 4.2's form): species
+    with element counts (C, H, O, N) and molecular weights, polynomial
+    thermodynamics cp/R = a0 + a1 T + a2 T^2 and h/(R T) = a0 + a1 T / 2
+    + a2 T^2 / 3 + a3 / T, and irreversible reactions (1-2 reactants and
+    products, mass and element balanced) with Arrhenius constants
+    k = clip(10^log10A T^beta exp(-Ea / T), kmin, kmax) (Ea in Kelvin)."""
+
+    n_species: int
+    comp: np.ndarray        # int [S, 4]
+    W: np.ndarray           # f64 [S] kg/mol
+    thermo: np.ndarray      # f64 [S, 4] (a0, a1, a2, a3)
+    n_reac: np.ndarray      # int32 [R]
+    reac: np.ndarray        # int32 [R, 2]
+    n_prod: np.ndarray      # int32 [R]
+    prod: np.ndarray        # int32 [R, 2]
+    log10A: np.ndarray
+    beta: np.ndarray
+    Ea: np.ndarray
+    kmin: float = 1e-2
+    kmax: float = 1e7
+
+    @property
+    def n_reactions(self) -> int:
+        return int(self.n_reac.size)
+
+
+ELEMENT_W = np.array([12.011e-3, 1.008e-3, 15.999e-3, 14.007e-3])  # C, H, O, N in kg/mol
+
+
+def make_mechanism(seed: int = 0, n_species: int = 57, n_reactions: int = 766) -> Mechanism:
+    """A synthetic mechanism of the size of the paper's ethanol case (57
+    species, 766 irreversible reactions): species are C/H/O compositions
+    (up to 2 C, 6 H, 3 O, at most 8 atoms, smallest first) plus inert N2;
+    each reaction takes 1-2 reactants and recombines their atoms into 1-2
+    other species (so mass and elements balance); Arrhenius constants are
+    drawn so the clipped rates give a moderately stiff system; formation
+    enthalpies favour oxygenated products (exothermic oxidation)."""
+    rng = _rng(seed)
+    cand = [(c, h, o, 0) for c in range(3) for h in range(7) for o in range(4)
+            if 0 < c + h + o <= 8]
+    cand.sort(key=lambda x: (sum(x), x))
+    comp = cand[:n_species - 1] + [(0, 0, 0, 2)]  # N2 last, inert
+    comp = np.array(comp, dtype=np.int64)
+    S = len(comp)
+    W = comp @ ELEMENT_W
+    atoms = comp[:, :3].sum(axis=1)
+    thermo = np.zeros((S, 4))
+    thermo[:, 0] = 2.5 + 0.8 * (atoms - 1) + rng.uniform(0.0, 0.5, S)   # cp/R at low T
+    thermo[:, 1] = rng.uniform(0.0, 4e-4, S) * (atoms > 1)               # mild rise with T
+    thermo[:, 2] = -rng.uniform(0.0, 5e-8, S) * (atoms > 1)
+    # formation enthalpy / R: oxygen-bearing molecules lower, radicals higher
+    thermo[:, 3] = -6000.0 * comp[:, 2] + 2500.0 * (comp[:, 1] % 2) + rng.uniform(-2000.0, 2000.0, S)
+    thermo[S - 1, 3] = 0.0
+    by_comp = {}
+    for i in range(S - 1):
+        by_comp.setdefault(tuple(comp[i]), []).append((i,))
+    for i in range(S - 1):
+        for j in range(i, S - 1):
+            by_comp.setdefault(tuple(comp[i] + comp[j]), []).append((i, j))
+    reac, prod = [], []
+    while len(reac) < n_reactions:
+        nr = 1 if rng.random() < 0.25 else 2
+        rs = tuple(sorted(rng.integers(0, S - 1, size=nr).tolist()))
+        total = tuple(comp[list(rs)].sum(axis=0))
+        opts = [q for q in by_comp.get(total, []) if tuple(sorted(q)) != rs]
+        if not opts:
+            continue
+        ps = opts[rng.integers(len(opts))]
+        reac.append(list(rs) + [-1] * (2 - len(rs)))
+        prod.append(list(ps) + [-1] * (2 - len(ps)))
+    reac, prod = np.array(reac, np.int32), np.array(prod, np.int32)
+    R = n_reactions
+    return Mechanism(S, comp, W, thermo, (reac >= 0).sum(axis=1).astype(np.int32), reac,
+                     (prod >= 0).sum(axis=1).astype(np.int32), prod,
+                     rng.uniform(4.0, 9.0, R), rng.uniform(-0.5, 0.5, R), rng.uniform(0.0, 15000.0, R))
+
+
+def kinetics(nsys: int = 16384, seed: int = 0, mech_seed: int = 0, tend: float = 1e-5) -> Workload:
+    """Constant-volume ignition-like batches (Section 4.2's form): state
+    (T, Y_1..Y_S), fuel (the largest C2 species with O) / O2 / N2 mixtures
+    with mass fractions varied per system, T0 ~ U[1000, 1300] K at 1 atm;
+    the density (constant in a closed vessel) is the system's parameter.
+    The paper integrates 10 global steps of 1e-6 s."""
+    mech = make_mechanism(mech_seed)
+    S = mech.n_species
+    rng = _rng(seed)
+    fuel = max((i for i in range(S - 1) if mech.comp[i, 0] == 2 and mech.comp[i, 2] >= 1),
+               key=lambda i: (mech.comp[i].sum(), i))
+    o2 = next(i for i in range(S) if tuple(mech.comp[i]) == (0, 0, 2, 0))
+    n2 = S - 1
+    Y = np.zeros((S, nsys))
+    yf = rng.uniform(0.03, 0.08, nsys)
+    yo = rng.uniform(0.18, 0.23, nsys)
+    Y[fuel], Y[o2], Y[n2] = yf, yo, 1.0 - yf - yo
+    T0 = rng.uniform(1000.0, 1300.0, nsys)
+    Wmix = 1.0 / np.sum(Y / mech.W[:, None], axis=0)
+    rho = 101325.0 * Wmix / (R_GAS * T0)
+    y0 = np.concatenate([T0[None, :], Y], axis=0)
+    return Workload("kinetics", RHS_KINETICS, METHOD_RKC, nsys, S + 1, np.ascontiguousarray(y0),
+                    rho[None, :].copy(), 0.0, tend, 1e-6, 1e-10, aux={"mechanism": mech})
 
 
 def pleiades_base(n: int = 7, base_seed: int = 0):
