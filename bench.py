@@ -308,6 +308,10 @@ def run_ours(args):
         pl = pleiades_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
             out["pleiades_rkck"] = pl
+    if args.kinetics_nsys > 0:
+        kn = kinetics_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["kinetics_ignition"] = kn
     if args.specrad_steps > 0:
         sr = specrad_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
@@ -480,6 +484,81 @@ def pleiades_leg(args, B, torch, dev, stream, rank, world, barrier):
             "config": {"nsys_per_gpu": w.nsys, "bodies": n, "neq": w.neq, "eps": w.rtol,
                        "interval": [w.t0, w.tend], "perturbation": 1e-3,
                        "flops_model": "20 per ordered pair per evaluation + 60 per unknown per attempt"}}
+
+
+def kinetics_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """The paper's RKC case shape (Section 4.2): constant-volume kinetics with
+    a temperature equation on a synthetic 57-species, 766-reaction mechanism,
+    10 global steps of 1e-6 s.  Plain FP64 (the paper's form) and the lean
+    mixed form, with cold restarts (the paper's driver) and with warm
+    RESTART carries; the CPU oracle on a bounded sample."""
+    import torch.distributed as dist
+    import oracle as O
+    w = W.kinetics(nsys=args.kinetics_nsys, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    y = torch.empty_like(y0)
+    carry = B.carry_like(w.neq, w.nsys, dev)
+    cnt = B.counters_like(w.nsys, dev)
+    edges = np.linspace(0.0, 1e-5, 11)
+
+    def chain(prec, warm, total=None):
+        for t_a, t_b in zip(edges[:-1], edges[1:]):
+            kw = dict(carry=carry, carry_mode=B.ODE_CARRY_RESTART) if warm else {}
+            B.integrate("rkc", h, y, p, float(t_a), float(t_b), w.rtol, w.atol, y_out=y, counters=cnt,
+                        precision=prec, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream, **kw)
+            if total is not None:
+                torch.cuda.synchronize()
+                total += cnt.n_rhs.cpu().numpy()
+
+    res = {}
+    for pname, prec in (("fp64", B.ODE_PREC_FP64), ("lean", B.ODE_PREC_MIXED_LEAN)):
+        for warm in (False, True):
+            ms = []
+            for rep in range(1 + args.kinetics_reps):
+                y.copy_(y0)
+                carry.zero_()
+                torch.cuda.synchronize()
+                barrier()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                chain(prec, warm)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    ms.append(e0.elapsed_time(e1))
+            t = float(np.mean(ms))
+            if world > 1:
+                tt = torch.tensor([t], device=dev)
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                t = float(tt.item())
+            y.copy_(y0)
+            carry.zero_()
+            total = np.zeros(w.nsys, np.int64)
+            chain(prec, warm, total)
+            res[f"{pname}_{'warm_restart' if warm else 'cold'}"] = {
+                "systems_per_s": w.nsys * world / (t * 1e-3), "ms_per_chain": t, "mean_rhs": float(total.mean()),
+                "y_sample": y[:, :256].cpu().numpy()}
+    B.release(h)
+    ws = W.subset(w, np.arange(256))
+    ws.aux = w.aux
+    m = O.model_for(ws)
+    t0 = time.perf_counter()
+    ys = ws.y0.copy()
+    for t_a, t_b in zip(edges[:-1], edges[1:]):
+        ys = O.integrate(m, 1, ys, ws.params, float(t_a), float(t_b), ws.rtol, ws.atol).y
+    cpu_s = time.perf_counter() - t0
+    for k, r in res.items():
+        yy = r.pop("y_sample")
+        e = (np.abs(yy - ys) / (np.abs(ys) + w.atol)).max(axis=0)
+        r["err_vs_oracle_cold_chain_p999"] = float(np.quantile(e, 0.999))
+    res["cpu_oracle_cold_chain"] = {"systems_per_s": 256 / cpu_s, "cores": os.cpu_count(), "sample": 256}
+    res["config"] = {"nsys_per_gpu": w.nsys, "species": w.neq - 1, "reactions": w.aux["mechanism"].n_reactions,
+                     "global_steps": 10, "dt": 1e-6, "rtol": w.rtol, "atol": w.atol,
+                     "mapping": "one warp per system, rates and concentrations staged in shared memory"}
+    return res
 
 
 def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
@@ -762,6 +841,8 @@ def main():
     ap.add_argument("--mixed-steps", type=int, default=3)
     ap.add_argument("--specrad-steps", type=int, default=2, help="timed steps per spectral-radius mode (0 skips)")
     ap.add_argument("--pleiades-nsys", type=int, default=262144, help="n-body RKCK leg batch (0 skips)")
+    ap.add_argument("--kinetics-nsys", type=int, default=16384, help="kinetics leg batch (0 skips)")
+    ap.add_argument("--kinetics-reps", type=int, default=1)
     ap.add_argument("--pleiades-steps", type=int, default=3)
     ap.add_argument("--split-steps", type=int, default=10, help="global steps of the outer-loop leg (0 skips it)")
     ap.add_argument("--split-reps", type=int, default=2)

@@ -70,6 +70,12 @@ extern "C" {
 #define ODE_RHS_MASSACTION 4 /* mass-action kinetics (Section 4.2 omega_i with constant T), Arrhenius
                                 k_j = clip(10^log10A_j T^beta_j exp(-Ea_j / T), kmin, kmax);
                                 params [T]; neq = n_species */
+#define ODE_RHS_KINETICS 6   /* constant-volume kinetics with a temperature equation (Section 4.2):
+                                state (T, Y_1..Y_S), C_i = rho Y_i / W_i, irreversible Arrhenius
+                                reactions (the mass-action fields of the descriptor, S species),
+                                dY_i/dt = W_i omega_i / rho, dT/dt = -sum e_i omega_i W_i / (rho c_v)
+                                with polynomial thermodynamics; params [rho]; neq = S + 1 <= 64,
+                                at most 1024 reactions; RKC with the power method only */
 #define ODE_RHS_NBODY 5      /* planar n-body gravity (the Pleiades problem's form, Section 4.1),
                                 [x_1..x_n, y_1..y_n, u_1..u_n, v_1..v_n]: x' = u, y' = v,
                                 (u_i', v_i') = G sum_{j != i} m_j d_ij / |d_ij|^3,
@@ -132,6 +138,12 @@ typedef struct {
     double coupling;
     /* ODE_RHS_NBODY only: neq / 4 body masses (host pointer, copied; > 0) */
     const double* masses;
+    /* ODE_RHS_KINETICS only (with the reaction fields above): molecular
+     * weights [S] in kg/mol and thermodynamic coefficients [S][4]
+     * (cp/R = a0 + a1 T + a2 T^2, h/(R T) = a0 + a1 T/2 + a2 T^2/3 + a3/T);
+     * host pointers, copied to the device at registration */
+    const double* mol_weights;
+    const double* thermo;
 } ode_rhs_desc;
 
 typedef struct {

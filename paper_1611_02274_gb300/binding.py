@@ -22,7 +22,7 @@ ODE_ST_OK, ODE_ST_H_UNDERFLOW, ODE_ST_MAX_ATTEMPTS, ODE_ST_NONFINITE = 0, 1, 2, 
 ODE_ST_SPECRAD_NOCONV = 256
 ODE_ST_PROPOSED = 512
 MLP_HIDDEN, MLP_MAX_IN, MLP_OUT, MLP_NORM_FLOATS = 64, 33, 3, 138
-ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION, ODE_RHS_NBODY = 1, 2, 3, 4, 5
+ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION, ODE_RHS_NBODY, ODE_RHS_KINETICS = 1, 2, 3, 4, 5, 6
 ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN = 0, 1, 2
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
 ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
@@ -47,6 +47,7 @@ class RhsDesc(C.Structure):
         ("kmin", C.c_double), ("kmax", C.c_double),
         ("bruss_A", C.c_double), ("bruss_B", C.c_double), ("bruss_ubc", C.c_double), ("bruss_vbc", C.c_double),
         ("coupling", C.c_double), ("masses", C.POINTER(C.c_double)),
+        ("mol_weights", C.POINTER(C.c_double)), ("thermo", C.POINTER(C.c_double)),
     ]
 
 
@@ -147,7 +148,7 @@ def _f64(a) -> np.ndarray:
 
 
 def register(kind: int, neq: int, network: W.Network | None = None, bruss=(1.0, 3.0, 1.0, 3.0),
-             coupling: float = 0.1, masses=None) -> int:
+             coupling: float = 0.1, masses=None, mechanism: W.Mechanism | None = None) -> int:
     """ode_rhs_register for one family; returns the handle."""
     d = RhsDesc()
     d.kind, d.neq, d.n_params = kind, neq, 1
@@ -163,6 +164,20 @@ def register(kind: int, neq: int, network: W.Network | None = None, bruss=(1.0, 
         d.n_reac, d.reac, d.n_prod, d.prod = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
         d.log10A, d.beta, d.Ea = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in darrs]
         d.kmin, d.kmax = network.kmin, network.kmax
+    if mechanism is not None:
+        mk = mechanism
+        wt, th = _f64(mk.W), _f64(mk.thermo)
+        keep += [wt, th]
+        d.mol_weights = wt.ctypes.data_as(C.POINTER(C.c_double))
+        d.thermo = th.ctypes.data_as(C.POINTER(C.c_double))
+        arrs = [_i32(mk.n_reac), _i32(np.where(mk.reac < 0, 0, mk.reac).reshape(-1)),
+                _i32(mk.n_prod), _i32(np.where(mk.prod < 0, 0, mk.prod).reshape(-1))]
+        darrs = [_f64(mk.log10A), _f64(mk.beta), _f64(mk.Ea)]
+        keep += arrs + darrs
+        d.n_reactions = mk.n_reactions
+        d.n_reac, d.reac, d.n_prod, d.prod = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
+        d.log10A, d.beta, d.Ea = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in darrs]
+        d.kmin, d.kmax = mk.kmin, mk.kmax
     if masses is not None:
         mm = _f64(masses)
         keep.append(mm)
@@ -173,7 +188,8 @@ def register(kind: int, neq: int, network: W.Network | None = None, bruss=(1.0, 
 
 
 def register_workload(w: W.Workload) -> int:
-    return register(w.kind, w.neq, network=w.network, masses=w.aux.get("masses"))
+    return register(w.kind, w.neq, network=w.network, masses=w.aux.get("masses"),
+                    mechanism=w.aux.get("mechanism"))
 
 
 def prepare(handle: int, method: str, precision: int = ODE_PREC_FP64):

@@ -113,6 +113,82 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
         r->bruss_ubc = d->bruss_ubc;
         r->bruss_vbc = d->bruss_vbc;
         return ODE_OK;
+    case ODE_RHS_KINETICS: {
+        const int S = d->neq - 1, R = d->n_reactions;
+        if (S < 1 || S > kKinMaxSpecies) return fail(ODE_ERR_ARG, "kinetics neq must be in [2, %d]", kKinMaxSpecies + 1);
+        if (R < 1 || R > kKinMaxReactions) return fail(ODE_ERR_ARG, "kinetics reaction count must be in [1, %d]", kKinMaxReactions);
+        if (!d->n_reac || !d->reac || !d->n_prod || !d->prod || !d->log10A || !d->beta || !d->Ea || !d->mol_weights ||
+            !d->thermo)
+            return fail(ODE_ERR_ARG, "kinetics mechanism arrays must be non-NULL");
+        if (!(d->kmin > 0.0) || !(d->kmax >= d->kmin)) return fail(ODE_ERR_ARG, "need 0 < kmin <= kmax");
+        for (int i = 0; i < S; ++i) {
+            if (!(d->mol_weights[i] > 0.0) || !std::isfinite(d->mol_weights[i]))
+                return fail(ODE_ERR_ARG, "species %d: molecular weight must be finite and > 0", i);
+            for (int q = 0; q < 4; ++q)
+                if (!std::isfinite(d->thermo[4 * i + q])) return fail(ODE_ERR_ARG, "species %d: non-finite thermo", i);
+        }
+        // incidence lists: per species, (j << 1) | is_product per occurrence, j ascending, reactants first
+        std::vector<std::vector<int>> inc(S);
+        for (int j = 0; j < R; ++j) {
+            const int nr = d->n_reac[j], np = d->n_prod[j];
+            if (nr < 1 || nr > 2 || np < 1 || np > 2) return fail(ODE_ERR_ARG, "reaction %d: 1-2 reactants and products", j);
+            if (!std::isfinite(d->log10A[j]) || !std::isfinite(d->beta[j]) || !std::isfinite(d->Ea[j]))
+                return fail(ODE_ERR_ARG, "reaction %d: non-finite Arrhenius parameter", j);
+            for (int q = 0; q < nr; ++q) {
+                const int i = d->reac[2 * j + q];
+                if (i < 0 || i >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
+                inc[i].push_back(j << 1);
+            }
+            for (int q = 0; q < np; ++q) {
+                const int i = d->prod[2 * j + q];
+                if (i < 0 || i >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
+                inc[i].push_back((j << 1) | 1);
+            }
+        }
+        std::vector<double> dv;
+        dv.insert(dv.end(), d->mol_weights, d->mol_weights + S);
+        dv.insert(dv.end(), d->thermo, d->thermo + 4 * S);
+        dv.insert(dv.end(), d->log10A, d->log10A + R);
+        dv.insert(dv.end(), d->beta, d->beta + R);
+        dv.insert(dv.end(), d->Ea, d->Ea + R);
+        std::vector<int> iv(d->n_reac, d->n_reac + R);
+        for (int j = 0; j < R; ++j) {
+            iv.push_back(d->reac[2 * j]);
+            iv.push_back(d->n_reac[j] == 2 ? d->reac[2 * j + 1] : d->reac[2 * j]);
+        }
+        const size_t off_pos = iv.size();
+        iv.push_back(0);
+        for (int i = 0; i < S; ++i) iv.push_back(iv.back() + (int)inc[i].size());
+        for (int i = 0; i < S; ++i) iv.insert(iv.end(), inc[i].begin(), inc[i].end());
+        const size_t dbytes = sizeof(double) * dv.size(), ibytes = sizeof(int) * iv.size();
+        void* mem = nullptr;
+        cudaError_t e = cudaMalloc(&mem, dbytes + ibytes);
+        if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "mechanism allocation: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(mem, dv.data(), dbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((char*)mem + dbytes, iv.data(), ibytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(mem);
+            return cuda_fail(e, "mechanism copy");
+        }
+        const double* dp = (const double*)mem;
+        const int* ip = (const int*)((char*)mem + dbytes);
+        KinDevice& kd = r->kin;
+        kd.S = S;
+        kd.R = R;
+        kd.kmin = d->kmin;
+        kd.kmax = d->kmax;
+        kd.W = dp;
+        kd.thermo = dp + S;
+        kd.log10A = dp + 5 * S;
+        kd.beta = kd.log10A + R;
+        kd.Ea = kd.beta + R;
+        kd.n_reac = ip;
+        kd.reac = ip + R;
+        kd.inc_off = ip + off_pos;
+        kd.inc = kd.inc_off + S + 1;
+        r->kin_alloc = mem;
+        return ODE_OK;
+    }
     case ODE_RHS_NBODY: {
         if (d->neq < 4 || d->neq > 4 * kMaxBodies || d->neq % 4)
             return fail(ODE_ERR_ARG, "n-body neq must be a multiple of 4 in [4, %d]", 4 * kMaxBodies);
@@ -186,6 +262,7 @@ int dispatch(const RhsEntry& rhs, int meth, int prec, bool use_jit, const BatchA
     case ODE_RHS_BRUSS1D: e = launch_bruss(meth, prec, rhs, a, cfg, &supported); break;
     case ODE_RHS_VDP_CHAIN: e = launch_chain(meth, prec, rhs, a, cfg, &supported); break;
     case ODE_RHS_NBODY: e = launch_nbody(meth, prec, rhs, a, cfg, &supported); break;
+    case ODE_RHS_KINETICS: e = launch_kinetics(meth, prec, rhs, a, cfg, &supported); break;
     default: supported = false; e = cudaSuccess;
     }
     if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built for this method", rhs.kind, rhs.neq);
@@ -404,6 +481,8 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     cfg.team = 0;
     cfg.sm_count = ws->sm_count;
     cfg.stream = stream;
+    if (rhs.kind == ODE_RHS_KINETICS && opts.specrad != ODE_SPECRAD_POWER)
+        return fail(ODE_ERR_UNSUPPORTED, "kinetics right-hand sides take the power method only (no Jacobian bound)");
     const int meth = method == kRkck ? kMethodRkck : kMethodRkc;
     const bool use_jit = rhs.kind == ODE_RHS_MASSACTION &&
                          (opts.codegen == ODE_CODEGEN_ON || (opts.codegen == ODE_CODEGEN_AUTO && jit_available()));
@@ -488,7 +567,10 @@ int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle) {
 int ode_rhs_release(int32_t rhs_handle) {
     g_err.clear();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_reg.erase(rhs_handle) == 0) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    auto it_r = g_reg.find(rhs_handle);
+    if (it_r == g_reg.end()) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
+    if (it_r->second.kin_alloc) cudaFree(it_r->second.kin_alloc);
+    g_reg.erase(it_r);
     for (auto it = g_map_tuned.begin(); it != g_map_tuned.end();)
         it = std::get<0>(it->first) == rhs_handle ? g_map_tuned.erase(it) : std::next(it);
     return ODE_OK;

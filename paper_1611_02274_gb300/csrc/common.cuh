@@ -72,6 +72,28 @@ enum : int {
 // Bodies of the largest registered n-body system.
 constexpr int kMaxBodies = 16;
 
+// Largest kinetics mechanism: species (neq = S + 1 <= 64) and reactions.
+constexpr int kKinMaxSpecies = 63;
+constexpr int kKinMaxReactions = 1024;
+
+// A kinetics mechanism on the device (owned by the registry).  inc_off /
+// inc list, per species, the reactions it takes part in as (j << 1) |
+// is_product, one entry per occurrence, ordered by j and reactants first
+// (the order the oracle accumulates omega_i in).
+struct KinDevice {
+    int S, R;
+    double kmin, kmax;
+    const double* W;        // [S]
+    const double* thermo;   // [S][4]
+    const double* log10A;   // [R]
+    const double* beta;
+    const double* Ea;
+    const int* n_reac;      // [R]
+    const int* reac;        // [R][2]
+    const int* inc_off;     // [S + 1]
+    const int* inc;         // [inc_off[S]]
+};
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 

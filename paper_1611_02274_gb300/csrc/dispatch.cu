@@ -14,6 +14,8 @@ cudaError_t launch_bruss_mixed(int method, int prec, const RhsEntry& r, const Ba
 cudaError_t launch_chain_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_nbody_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_kin_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_kin_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_nbody_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 namespace {
@@ -40,6 +42,10 @@ cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArg
 
 cudaError_t launch_nbody(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     return f64(prec) ? launch_nbody_f64(method, r, a, c, ok) : launch_nbody_mixed(method, prec, r, a, c, ok);
+}
+
+cudaError_t launch_kinetics(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+    return f64(prec) ? launch_kin_f64(method, r, a, c, ok) : launch_kin_mixed(method, prec, r, a, c, ok);
 }
 
 }  // namespace bode

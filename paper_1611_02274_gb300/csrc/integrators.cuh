@@ -32,6 +32,20 @@
 
 namespace bode {
 
+// Floats of shared memory per thread a model asks for (Model::SMEM_FLOATS,
+// 0 if it declares none); the integrators add them to their own and hand
+// the model its part through Sys::bind.
+template <class...>
+using void_t_ = void;
+template <class M, class = void>
+struct ModelSmem {
+    static constexpr int value = 0;
+};
+template <class M>
+struct ModelSmem<M, void_t_<decltype(M::SMEM_FLOATS)>> {
+    static constexpr int value = M::SMEM_FLOATS;
+};
+
 enum : int { PH_DONE = 0, PH_F0, PH_SR, PH_TRIAL, PH_STAGE, PH_FINAL };
 
 // Kahan-compensated state update (hi, lo) += d.
@@ -82,7 +96,10 @@ __device__ __forceinline__ void carry_scalars(const BatchArgs& a, int64_t i, boo
 template <class Model>
 struct RkckF64 {
     static constexpr bool kStepSync = false;  // fixed six stages: lanes stay aligned
-    static constexpr int SMEM_FLOATS = 0;
+    static constexpr int SMEM_FLOATS = ModelSmem<Model>::value;
+    __device__ void bind_smem(float* base, int stride) {
+        if constexpr (SMEM_FLOATS > 0) sys.bind(base, stride);
+    }
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
     using TM = Team<W>;
@@ -268,7 +285,10 @@ struct RkckF64 {
 template <class Model>
 struct RkcF64 {
     static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
-    static constexpr int SMEM_FLOATS = 0;
+    static constexpr int SMEM_FLOATS = ModelSmem<Model>::value;
+    __device__ void bind_smem(float* base, int stride) {
+        if constexpr (SMEM_FLOATS > 0) sys.bind(base, stride);
+    }
     static constexpr int W = Model::W, P = Model::PER;
     using R = double;
     using TM = Team<W>;
@@ -668,7 +688,10 @@ struct SumF2 {
 template <class Model, bool SPEC = true>
 struct RkckMixed {
     static constexpr bool kStepSync = false;  // fixed six stages: lanes stay aligned
-    static constexpr int SMEM_FLOATS = 0;
+    static constexpr int SMEM_FLOATS = ModelSmem<Model>::value;
+    __device__ void bind_smem(float* base, int stride) {
+        if constexpr (SMEM_FLOATS > 0) sys.bind(base, stride);
+    }
     static constexpr int W = Model::W, P = Model::PER;
     using R = float;
     using TM = Team<W>;
@@ -874,16 +897,18 @@ struct RkcMixed {
     // so for small one-thread systems it lives in shared memory (this
     // thread's column of a [P][blockDim] array), which frees P registers
     // for the state the stages use.
-    static constexpr int SMEM_FLOATS = rkc_mixed_smem_floats(W, P);
-    mutable float vreg[SMEM_FLOATS ? 1 : P];
+    static constexpr int V_SMEM = rkc_mixed_smem_floats(W, P);
+    static constexpr int SMEM_FLOATS = V_SMEM + ModelSmem<Model>::value;
+    mutable float vreg[V_SMEM ? 1 : P];
     float* vs;
     int vstride;
     __device__ void bind_smem(float* base, int stride) {
-        vs = base;
+        vs = base + threadIdx.x;  // this thread's column
         vstride = stride;
+        if constexpr (ModelSmem<Model>::value > 0) sys.bind(base + V_SMEM * stride, stride);
     }
     __device__ float& V(int s) const {
-        if constexpr (SMEM_FLOATS > 0)
+        if constexpr (V_SMEM > 0)
             return vs[s * vstride];
         else
             return vreg[s];

@@ -16,14 +16,16 @@
 
 namespace bode {
 
-// Per-thread shared-memory columns of the methods that keep rarely used
-// vectors there (Method::SMEM_FLOATS floats per thread, launched with
-// SMEM_FLOATS * blockDim floats of dynamic shared memory).
-extern __shared__ float bode_dyn_smem[];
+// Dynamic shared memory of the methods (and models) that keep data there:
+// Method::SMEM_FLOATS floats per thread, launched with SMEM_FLOATS *
+// blockDim floats.  bind_smem receives the block's base and blockDim; a
+// per-thread column starts at base + threadIdx.x with stride blockDim, a
+// per-team region is carved from the base by the team's index.
+extern __shared__ __align__(16) float bode_dyn_smem[];
 
 template <class Method>
 __device__ __forceinline__ void bind_method_smem(Method& m) {
-    if constexpr (Method::SMEM_FLOATS > 0) m.bind_smem(bode_dyn_smem + threadIdx.x, (int)blockDim.x);
+    if constexpr (Method::SMEM_FLOATS > 0) m.bind_smem(bode_dyn_smem, (int)blockDim.x);
 }
 
 // Step-end hold (methods with a variable stage count, Method::kStepSync):

@@ -18,6 +18,8 @@ struct RhsEntry {
     double bruss_A, bruss_B, bruss_ubc, bruss_vbc;
     double coupling;
     double masses[kMaxBodies];
+    KinDevice kin;          // device mechanism (ODE_RHS_KINETICS), freed at release
+    void* kin_alloc;        // the one device allocation behind kin
 };
 
 // Launch configuration resolved by the API layer.
@@ -35,6 +37,12 @@ cudaError_t launch_method(const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c
     const int block = c.block;
     const size_t smem = sizeof(float) * Method::SMEM_FLOATS * (size_t)block;
     const int64_t threads = a.nsys * W;
+    if (smem > 48 * 1024) {  // above the default dynamic shared-memory limit: opt in
+        cudaError_t e = cudaFuncSetAttribute(k_static<Method, Ctx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_queue<Method, Ctx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     if (c.mapping == ODE_MAP_QUEUE) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_queue<Method, Ctx>, block, smem);
@@ -60,6 +68,7 @@ cudaError_t launch_mass(int method, int prec, const RhsEntry& r, const BatchArgs
 cudaError_t launch_bruss(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_nbody(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_kinetics(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 // Builds the RKC stage-coefficient tables on the current device.
 cudaError_t build_rkc_tables(double* tab64, float4* tab32, int mmax, cudaStream_t s);

@@ -268,6 +268,124 @@ struct BrussModel {
     };
 };
 
+struct KinCtx {
+    KinDevice k;
+};
+
+// Constant-volume kinetics with a temperature equation (Section 4.2), one
+// warp per system: component c (0 = T, 1 + i = Y_i) in slot c / 32 of lane
+// c % 32.  Per evaluation the team stages the S concentrations
+// C_i = rho Y_i / W_i and the R rate constants in its shared memory; each
+// lane then sums omega_i for its species over their incidence lists
+// (reaction order, reactants first, as the oracle accumulates), and the
+// temperature equation's species sums run in species order by shuffles.
+// The plain form takes the rate constants through the series exponential
+// and logarithm (bitwise equal to the oracle's); the mixed form in FP32.
+// params [rho].
+template <int W_>
+struct KinModel {
+    static_assert(W_ == 32, "one warp per kinetics system");
+    static constexpr int W = W_, PER = 2;
+    using Ctx = KinCtx;
+    // shared memory per thread (floats): a team stages up to 64
+    // concentrations and kKinMaxReactions rate constants in FP64
+    static constexpr int SMEM_FLOATS = (2 * (64 + kKinMaxReactions) + W_ - 1) / W_;
+    static_assert((W_ * SMEM_FLOATS) % 2 == 0, "team regions keep FP64 alignment");
+    template <class R>
+    struct Sys {
+        const KinDevice* k;
+        R rho;
+        int n;
+        R* sC;  // [64] concentrations of this team's system
+        R* sK;  // [kKinMaxReactions] rate constants
+        __device__ void load(const Ctx& ctx, const Team<W>&, double p, int neq) {
+            k = &ctx.k;
+            rho = (R)p;
+            n = neq;
+        }
+        // block_base: this model's part of the block's dynamic shared memory
+        // (16-byte aligned; each team's region is W * SMEM_FLOATS floats, a
+        // multiple of 8 bytes)
+        __device__ void bind(float* block_base, int) {
+            R* team = reinterpret_cast<R*>(block_base + (threadIdx.x / W) * W * SMEM_FLOATS);
+            sC = team;
+            sK = team + 64;
+        }
+        __device__ int comp(const Team<W>& tm, int s) const {
+            const int c = s * W + tm.lane;
+            return c < n ? c : -1;
+        }
+        template <class T>
+        __device__ T ordered_sum(const Team<W>& tm, const T* x) const {
+            T acc = T(0);
+#pragma unroll
+            for (int s = 0; s < PER; ++s)
+#pragma unroll
+                for (int l = 0; l < W; ++l) {
+                    const T v = tm.bcast(x[s], l);
+                    if (s * W + l < n) acc = acc + v;
+                }
+            return acc;
+        }
+        __device__ R rate(int j, R T, R lnT) const {
+            if constexpr (sizeof(R) == 8) {
+                const double kk = xm::exp_series(xm::kLn10 * __ldg(k->log10A + j) + __ldg(k->beta + j) * lnT -
+                                                 __ldg(k->Ea + j) / T);
+                return fmin(fmax(kk, k->kmin), k->kmax);
+            } else {
+                const float l2 = (2.3025851f * (float)__ldg(k->log10A + j) + (float)__ldg(k->beta + j) * lnT -
+                                  (float)__ldg(k->Ea + j) / T) * 1.4426950f;
+                return fminf(fmaxf(exp2f(l2), (float)k->kmin), (float)k->kmax);
+            }
+        }
+        __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
+            const R T = tm.bcast(y[0], 0);
+            R lnT;
+            if constexpr (sizeof(R) == 8)
+                lnT = xm::log_series(T);
+            else
+                lnT = __logf(T);
+#pragma unroll
+            for (int s = 0; s < PER; ++s) {
+                const int c = s * W + tm.lane;
+                if (c >= 1 && c < n) sC[c - 1] = rho * y[s] / (R)__ldg(k->W + c - 1);
+            }
+            for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, T, lnT);
+            __syncwarp();
+            R om[PER], cvy[PER], hw[PER];
+#pragma unroll
+            for (int s = 0; s < PER; ++s) {
+                om[s] = cvy[s] = hw[s] = f[s] = R(0);
+                const int c = s * W + tm.lane;
+                if (c < 1 || c >= n) continue;
+                const int i = c - 1;
+                const int e1 = __ldg(k->inc_off + i + 1);
+                for (int e = __ldg(k->inc_off + i); e < e1; ++e) {
+                    const int word = __ldg(k->inc + e);
+                    const int j = word >> 1;
+                    R q = sK[j] * sC[__ldg(k->reac + 2 * j)];
+                    if (__ldg(k->n_reac + j) == 2) q = q * sC[__ldg(k->reac + 2 * j + 1)];
+                    om[s] = (word & 1) ? om[s] + q : om[s] - q;
+                }
+                const double* a = k->thermo + 4 * i;
+                const R a0 = (R)__ldg(a), a1 = (R)__ldg(a + 1), a2 = (R)__ldg(a + 2), a3 = (R)__ldg(a + 3);
+                const R Wi = (R)__ldg(k->W + i);
+                const R Rg = (R)8.314462618;
+                const R cvi = (Rg / Wi) * (a0 + a1 * T + a2 * T * T - R(1));
+                const R ei = (Rg * T / Wi) * (a0 + a1 * T / R(2) + a2 * T * T / R(3) + a3 / T - R(1));
+                cvy[s] = y[s] * cvi;
+                hw[s] = ei * om[s] * Wi;
+                f[s] = Wi * om[s] / rho;
+            }
+            __syncwarp();  // the staged values are read before the next evaluation writes them
+            const R cv = ordered_sum(tm, cvy);
+            const R heat = ordered_sum(tm, hw);
+            if (tm.lane == 0) f[0] = -heat / (rho * cv);
+        }
+        __device__ R gershgorin(const Team<W>&, const R*) const { return R(0) / R(0); }  // not provided
+    };
+};
+
 struct NbodyCtx {
     double m[kMaxBodies];  // body masses
 };
