@@ -4,9 +4,13 @@ Workload (one step = one pass of the whole hot path over one batch): the
 seeded 13-species / 27-reaction mass-action network, 1,048,576 systems per
 GPU, T ~ U[1000, 2000] K, t in [0, 1e-4], rtol 1e-6, atol 1e-12, integrated
 by RKC through the C ABI.  The metric is ODE systems integrated per second
-by the chosen form (FP32 stages with Kahan-compensated state, FP64
-bookkeeping, persistent work-queue kernel); the plain FP64 form is timed
-beside it on the same inputs, and the CPU oracle on a bounded sample.
+by the chosen form (generated network code; FP32 stages, step size and
+norms with Kahan-compensated state and the remaining interval as an FP32
+pair; thread or queue mapping picked by ODE_MAP_AUTO); the plain FP64 form
+is timed beside it on the same inputs, and the CPU oracle on a bounded
+sample.  Further legs time the learned proposal, ragged batches, the
+spectral-radius modes, the outer global-step loop, the n-body and the
+kinetics families.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -41,10 +45,12 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per system of the chosen kernel, from one ncu
-# capture of k_static<RkcMixed<JitMass, false>> (step-end hold) on 262,144
-# systems of this workload (29.584 MB read + 0.342 MB written); traffic
-# grows with the number of systems (each state is read once, written once)
-NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.584128e6 + 0.34176e6) / 262144
+# capture of k_static<RkcMixed<JitMass, false>> (step-end hold, carry and
+# spectral-radius options, power-method vector in odd-pitch shared-memory
+# rows) on 262,144 systems of this workload (29.822 MB read + 0.917 MB
+# written); traffic grows with the number of systems (each state is read
+# once, written once)
+NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.822464e6 + 0.917248e6) / 262144
 
 
 def dist_env():

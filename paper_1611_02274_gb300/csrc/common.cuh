@@ -58,8 +58,11 @@ struct Pick<false, T, F> {
 
 // Floats of shared memory per thread that the mixed RKC integrator keeps its
 // power-method vector in (one-thread systems of at most 32 unknowns; larger
-// or multi-lane systems keep it in registers).
-__host__ __device__ constexpr int rkc_mixed_smem_floats(int lanes, int per_lane) { return (lanes == 1 && per_lane <= 32) ? per_lane : 0; }
+// or multi-lane systems keep it in registers).  The row is rounded up to an
+// odd length so that a warp's rows fall in distinct banks.
+__host__ __device__ constexpr int rkc_mixed_smem_floats(int lanes, int per_lane) {
+    return (lanes == 1 && per_lane <= 32) ? (per_lane | 1) : 0;
+}
 
 // Warm-restart carry words (see batchode.h): valid flag, time reached, h,
 // sigma, h_old, err_old, accepted-step count, count at the last

@@ -894,22 +894,21 @@ struct RkcMixed {
     typename Model::template Sys<float> sys;
     float yh[P], yl[P], Fn[P], d1[P], d2[P];  // d_j = w_j - y_n (d_0 = 0)
     // Power-method vector v: touched only in the rare power-method phases,
-    // so for small one-thread systems it lives in shared memory (this
-    // thread's column of a [P][blockDim] array), which frees P registers
-    // for the state the stages use.
+    // so for small one-thread systems it lives in shared memory, which frees
+    // P registers for the state the stages use.  Each thread owns one row of
+    // V_SMEM (odd) floats: element s sits at a constant offset from a single
+    // base address, and the odd pitch puts a warp's 32 rows in 32 banks.
     static constexpr int V_SMEM = rkc_mixed_smem_floats(W, P);
     static constexpr int SMEM_FLOATS = V_SMEM + ModelSmem<Model>::value;
     mutable float vreg[V_SMEM ? 1 : P];
     float* vs;
-    int vstride;
     __device__ void bind_smem(float* base, int stride) {
-        vs = base + threadIdx.x;  // this thread's column
-        vstride = stride;
+        vs = base + threadIdx.x * V_SMEM;  // this thread's row
         if constexpr (ModelSmem<Model>::value > 0) sys.bind(base + V_SMEM * stride, stride);
     }
     __device__ float& V(int s) const {
         if constexpr (V_SMEM > 0)
-            return vs[s * vstride];
+            return vs[s];
         else
             return vreg[s];
     }
