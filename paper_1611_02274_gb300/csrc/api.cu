@@ -127,23 +127,21 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
             for (int q = 0; q < 4; ++q)
                 if (!std::isfinite(d->thermo[4 * i + q])) return fail(ODE_ERR_ARG, "species %d: non-finite thermo", i);
         }
-        // incidence lists: per species, (j << 1) | is_product per occurrence, j ascending, reactants first
+        // incidence lists: per species, one packed word per occurrence
+        // (kin_inc_word), j ascending, reactants first
         std::vector<std::vector<int>> inc(S);
         for (int j = 0; j < R; ++j) {
             const int nr = d->n_reac[j], np = d->n_prod[j];
             if (nr < 1 || nr > 2 || np < 1 || np > 2) return fail(ODE_ERR_ARG, "reaction %d: 1-2 reactants and products", j);
             if (!std::isfinite(d->log10A[j]) || !std::isfinite(d->beta[j]) || !std::isfinite(d->Ea[j]))
                 return fail(ODE_ERR_ARG, "reaction %d: non-finite Arrhenius parameter", j);
-            for (int q = 0; q < nr; ++q) {
-                const int i = d->reac[2 * j + q];
+            for (int q = 0; q < nr + np; ++q) {
+                const int i = q < nr ? d->reac[2 * j + q] : d->prod[2 * j + q - nr];
                 if (i < 0 || i >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
-                inc[i].push_back(j << 1);
             }
-            for (int q = 0; q < np; ++q) {
-                const int i = d->prod[2 * j + q];
-                if (i < 0 || i >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
-                inc[i].push_back((j << 1) | 1);
-            }
+            const int r0 = d->reac[2 * j], r1 = nr == 2 ? d->reac[2 * j + 1] : r0;
+            for (int q = 0; q < nr; ++q) inc[d->reac[2 * j + q]].push_back(kin_inc_word(j, false, r0, r1, nr == 2));
+            for (int q = 0; q < np; ++q) inc[d->prod[2 * j + q]].push_back(kin_inc_word(j, true, r0, r1, nr == 2));
         }
         std::vector<double> dv;
         dv.insert(dv.end(), d->mol_weights, d->mol_weights + S);
@@ -151,27 +149,41 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
         dv.insert(dv.end(), d->log10A, d->log10A + R);
         dv.insert(dv.end(), d->beta, d->beta + R);
         dv.insert(dv.end(), d->Ea, d->Ea + R);
-        std::vector<int> iv(d->n_reac, d->n_reac + R);
+        if (dv.size() % 2) dv.push_back(0.0);  // the float4 section starts 16-byte aligned
+        std::vector<float> fv;
+        const double log2_10 = 3.321928094887362, log2_e = 1.4426950408889634, r_gas = 8.314462618;
         for (int j = 0; j < R; ++j) {
-            iv.push_back(d->reac[2 * j]);
-            iv.push_back(d->n_reac[j] == 2 ? d->reac[2 * j + 1] : d->reac[2 * j]);
+            fv.push_back((float)(log2_10 * d->log10A[j]));
+            fv.push_back((float)d->beta[j]);
+            fv.push_back((float)(log2_e * d->Ea[j]));
+            fv.push_back(0.0f);
         }
-        const size_t off_pos = iv.size();
+        for (int i = 0; i < S; ++i) {
+            for (int q = 0; q < 4; ++q) fv.push_back((float)d->thermo[4 * i + q]);
+            fv.push_back((float)(r_gas / d->mol_weights[i]));
+            fv.push_back((float)d->mol_weights[i]);
+            fv.push_back((float)(1.0 / d->mol_weights[i]));
+            fv.push_back(0.0f);
+        }
+        std::vector<int> iv;
         iv.push_back(0);
         for (int i = 0; i < S; ++i) iv.push_back(iv.back() + (int)inc[i].size());
         for (int i = 0; i < S; ++i) iv.insert(iv.end(), inc[i].begin(), inc[i].end());
-        const size_t dbytes = sizeof(double) * dv.size(), ibytes = sizeof(int) * iv.size();
+        const size_t dbytes = sizeof(double) * dv.size(), fbytes = sizeof(float) * fv.size(),
+                     ibytes = sizeof(int) * iv.size();
         void* mem = nullptr;
-        cudaError_t e = cudaMalloc(&mem, dbytes + ibytes);
+        cudaError_t e = cudaMalloc(&mem, dbytes + fbytes + ibytes);
         if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "mechanism allocation: %s", cudaGetErrorString(e));
         e = cudaMemcpy(mem, dv.data(), dbytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy((char*)mem + dbytes, iv.data(), ibytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((char*)mem + dbytes, fv.data(), fbytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy((char*)mem + dbytes + fbytes, iv.data(), ibytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(mem);
             return cuda_fail(e, "mechanism copy");
         }
         const double* dp = (const double*)mem;
-        const int* ip = (const int*)((char*)mem + dbytes);
+        const float4* fp = (const float4*)((char*)mem + dbytes);
+        const int* ip = (const int*)((char*)mem + dbytes + fbytes);
         KinDevice& kd = r->kin;
         kd.S = S;
         kd.R = R;
@@ -182,10 +194,10 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
         kd.log10A = dp + 5 * S;
         kd.beta = kd.log10A + R;
         kd.Ea = kd.beta + R;
-        kd.n_reac = ip;
-        kd.reac = ip + R;
-        kd.inc_off = ip + off_pos;
-        kd.inc = kd.inc_off + S + 1;
+        kd.rate32 = fp;
+        kd.thermo32 = fp + R;
+        kd.inc_off = ip;
+        kd.inc = ip + S + 1;
         r->kin_alloc = mem;
         return ODE_OK;
     }

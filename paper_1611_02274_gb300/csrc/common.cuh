@@ -80,9 +80,14 @@ constexpr int kKinMaxSpecies = 63;
 constexpr int kKinMaxReactions = 1024;
 
 // A kinetics mechanism on the device (owned by the registry).  inc_off /
-// inc list, per species, the reactions it takes part in as (j << 1) |
-// is_product, one entry per occurrence, ordered by j and reactants first
-// (the order the oracle accumulates omega_i in).
+// inc list, per species, the reactions it takes part in, one entry per
+// occurrence, ordered by j and reactants first (the order the oracle
+// accumulates omega_i in).  Each entry packs what the rate-of-progress
+// product needs: bit 0 is_product, bits 1-10 the reaction j, bits 11-16 and
+// 17-22 its first and second reactant species, bit 23 set when it has two.
+// The FP32 section serves the mixed forms: per reaction (log2(10) log10 A,
+// beta, Ea log2(e), 0), so that k = 2^(x + beta log2 T - z / T); per species
+// (a0, a1, a2, a3) and (R_gas / W, W, 1 / W, 0).
 struct KinDevice {
     int S, R;
     double kmin, kmax;
@@ -91,11 +96,15 @@ struct KinDevice {
     const double* log10A;   // [R]
     const double* beta;
     const double* Ea;
-    const int* n_reac;      // [R]
-    const int* reac;        // [R][2]
     const int* inc_off;     // [S + 1]
     const int* inc;         // [inc_off[S]]
+    const float4* rate32;   // [R]
+    const float4* thermo32; // [S][2]
 };
+
+__host__ __device__ constexpr int kin_inc_word(int j, bool is_product, int r0, int r1, bool two) {
+    return (is_product ? 1 : 0) | (j << 1) | (r0 << 11) | (r1 << 17) | (two ? 1 << 23 : 0);
+}
 
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};

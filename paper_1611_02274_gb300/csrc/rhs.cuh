@@ -332,50 +332,76 @@ struct KinModel {
                 const double kk = xm::exp_series(xm::kLn10 * __ldg(k->log10A + j) + __ldg(k->beta + j) * lnT -
                                                  __ldg(k->Ea + j) / T);
                 return fmin(fmax(kk, k->kmin), k->kmax);
-            } else {
-                const float l2 = (2.3025851f * (float)__ldg(k->log10A + j) + (float)__ldg(k->beta + j) * lnT -
-                                  (float)__ldg(k->Ea + j) / T) * 1.4426950f;
-                return fminf(fmaxf(exp2f(l2), (float)k->kmin), (float)k->kmax);
+            } else {  // lnT holds log2 T here, and T the reciprocal 1 / T
+                const float4 q = __ldg(k->rate32 + j);
+                return fminf(fmaxf(exp2f(q.x + q.y * lnT - q.z * T), (float)k->kmin), (float)k->kmax);
             }
+        }
+        // omega_i of species i: the signed rates of progress over its
+        // incidence list, in list order
+        __device__ R omega(int i) const {
+            R om = R(0);
+            const int e1 = __ldg(k->inc_off + i + 1);
+            for (int e = __ldg(k->inc_off + i); e < e1; ++e) {
+                const int word = __ldg(k->inc + e);
+                R q = sK[(word >> 1) & 1023] * sC[(word >> 11) & 63];
+                if (word & (1 << 23)) q = q * sC[(word >> 17) & 63];
+                om = (word & 1) ? om + q : om - q;
+            }
+            return om;
         }
         __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
             const R T = tm.bcast(y[0], 0);
-            R lnT;
-            if constexpr (sizeof(R) == 8)
-                lnT = xm::log_series(T);
-            else
-                lnT = __logf(T);
-#pragma unroll
-            for (int s = 0; s < PER; ++s) {
-                const int c = s * W + tm.lane;
-                if (c >= 1 && c < n) sC[c - 1] = rho * y[s] / (R)__ldg(k->W + c - 1);
-            }
-            for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, T, lnT);
-            __syncwarp();
             R om[PER], cvy[PER], hw[PER];
+            if constexpr (sizeof(R) == 8) {
+                const R lnT = xm::log_series(T);
 #pragma unroll
-            for (int s = 0; s < PER; ++s) {
-                om[s] = cvy[s] = hw[s] = f[s] = R(0);
-                const int c = s * W + tm.lane;
-                if (c < 1 || c >= n) continue;
-                const int i = c - 1;
-                const int e1 = __ldg(k->inc_off + i + 1);
-                for (int e = __ldg(k->inc_off + i); e < e1; ++e) {
-                    const int word = __ldg(k->inc + e);
-                    const int j = word >> 1;
-                    R q = sK[j] * sC[__ldg(k->reac + 2 * j)];
-                    if (__ldg(k->n_reac + j) == 2) q = q * sC[__ldg(k->reac + 2 * j + 1)];
-                    om[s] = (word & 1) ? om[s] + q : om[s] - q;
+                for (int s = 0; s < PER; ++s) {
+                    const int c = s * W + tm.lane;
+                    if (c >= 1 && c < n) sC[c - 1] = rho * y[s] / (R)__ldg(k->W + c - 1);
                 }
-                const double* a = k->thermo + 4 * i;
-                const R a0 = (R)__ldg(a), a1 = (R)__ldg(a + 1), a2 = (R)__ldg(a + 2), a3 = (R)__ldg(a + 3);
-                const R Wi = (R)__ldg(k->W + i);
-                const R Rg = (R)8.314462618;
-                const R cvi = (Rg / Wi) * (a0 + a1 * T + a2 * T * T - R(1));
-                const R ei = (Rg * T / Wi) * (a0 + a1 * T / R(2) + a2 * T * T / R(3) + a3 / T - R(1));
-                cvy[s] = y[s] * cvi;
-                hw[s] = ei * om[s] * Wi;
-                f[s] = Wi * om[s] / rho;
+                for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, T, lnT);
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < PER; ++s) {
+                    om[s] = cvy[s] = hw[s] = f[s] = R(0);
+                    const int c = s * W + tm.lane;
+                    if (c < 1 || c >= n) continue;
+                    const int i = c - 1;
+                    om[s] = omega(i);
+                    const double* a = k->thermo + 4 * i;
+                    const R a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3);
+                    const R Wi = __ldg(k->W + i);
+                    const R Rg = 8.314462618;
+                    const R cvi = (Rg / Wi) * (a0 + a1 * T + a2 * T * T - R(1));
+                    const R ei = (Rg * T / Wi) * (a0 + a1 * T / R(2) + a2 * T * T / R(3) + a3 / T - R(1));
+                    cvy[s] = y[s] * cvi;
+                    hw[s] = ei * om[s] * Wi;
+                    f[s] = Wi * om[s] / rho;
+                }
+            } else {  // FP32: reciprocals instead of divisions, coefficients pre-scaled at registration
+                const R invT = R(1) / T, log2T = __log2f(T), inv_rho = R(1) / rho;
+#pragma unroll
+                for (int s = 0; s < PER; ++s) {
+                    const int c = s * W + tm.lane;
+                    if (c >= 1 && c < n) sC[c - 1] = rho * y[s] * __ldg(k->thermo32 + 2 * (c - 1) + 1).z;
+                }
+                for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, invT, log2T);
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < PER; ++s) {
+                    om[s] = cvy[s] = hw[s] = f[s] = R(0);
+                    const int c = s * W + tm.lane;
+                    if (c < 1 || c >= n) continue;
+                    const int i = c - 1;
+                    om[s] = omega(i);
+                    const float4 a = __ldg(k->thermo32 + 2 * i), wv = __ldg(k->thermo32 + 2 * i + 1);
+                    const R cvi = wv.x * (a.x + a.y * T + a.z * T * T - R(1));
+                    const R ei = (wv.x * T) * (a.x + a.y * T * R(0.5) + a.z * T * T * R(1.0 / 3.0) + a.w * invT - R(1));
+                    cvy[s] = y[s] * cvi;
+                    hw[s] = ei * om[s] * wv.y;
+                    f[s] = wv.y * om[s] * inv_rho;
+                }
             }
             __syncwarp();  // the staged values are read before the next evaluation writes them
             const R cv = ordered_sum(tm, cvy);

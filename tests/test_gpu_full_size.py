@@ -1,0 +1,169 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (ODE_MAP_AUTO mapping and block size, one call or one
+graph-captured plan over the whole batch), checked on samples of systems
+that the oracle integrates one by one: systems spread evenly over the batch,
+plus the first and the last 64 (the last block's ragged tail).
+
+Plain FP64: the sampled systems take the oracle's accepted / rejected
+counts -- the >= 99.9 % bar scaled to the sample, at most one mismatch --
+and end within 1e-9 relative; the status words agree.  Chosen (lean mixed)
+forms: no error status anywhere in the batch, and the error against the
+oracle within the bounds of the smaller mixed-form tests.  The sizes are
+those of the paper-shaped workloads: 65,536 64-unknown Brusselator grids,
+1,048,576 mass-action systems, a 262,144-system ragged batch and the
+4,194,304-system batch of the learned proposal.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1611_02274_gb300 import binding as B
+from paper_1611_02274_gb300 import workloads as W
+
+from gpu_util import rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def sample(n, k, seed=0):
+    rng = np.random.default_rng(seed)
+    spread = np.linspace(0, n - 1, k // 2).astype(np.int64)
+    rand = rng.choice(n, k // 2, replace=False)
+    ends = np.concatenate([np.arange(64), np.arange(n - 64, n)])
+    return np.unique(np.concatenate([spread, rand, ends]))
+
+
+def check_fp64_sample(w, g, idx):
+    ref = O.integrate_workload(W.subset(w, idx))
+    same = (g["n_accept"][idx] == ref.n_accept) & (g["n_reject"][idx] == ref.n_reject)
+    assert (~same).sum() <= max(1, int(0.001 * idx.size)), (~same).sum()
+    np.testing.assert_array_equal(g["n_rhs"][idx][same], ref.n_rhs[same])
+    np.testing.assert_array_equal(g["status"][idx], ref.status)
+    assert rel_err(g["y"][:, idx], ref.y, w.atol)[same].max() <= 1e-9
+
+
+def check_chosen_sample(w, g, idx, p99_bound, median_bound):
+    assert ((g["status"] & 0xFF) == 0).all()
+    assert np.isfinite(g["y"]).all()
+    ref = O.integrate_workload(W.subset(w, idx))
+    e = rel_err(g["y"][:, idx], ref.y, w.atol)
+    print(w.name, w.nsys, "chosen vs oracle on", idx.size, "sampled: median", np.median(e),
+          "p99", np.quantile(e, 0.99), "max", e.max())
+    assert np.median(e) <= median_bound
+    assert np.quantile(e, 0.99) <= p99_bound
+
+
+@pytest.fixture(scope="module")
+def massaction_1m():
+    return W.massaction(nsys=1 << 20, seed=31)
+
+
+def test_massaction_1m_fp64(massaction_1m):
+    w = massaction_1m
+    g = run_gpu(w, precision=B.ODE_PREC_FP64)
+    check_fp64_sample(w, g, sample(w.nsys, 8192, seed=1))
+
+
+def test_massaction_1m_chosen_form(massaction_1m):
+    # the benchmark's main step: lean split, generated network code, AUTO
+    w = massaction_1m
+    g = run_gpu(w, precision=B.ODE_PREC_MIXED_LEAN)
+    check_chosen_sample(w, g, sample(w.nsys, 16384, seed=2), p99_bound=2e-3, median_bound=1e-5)
+
+
+@pytest.fixture(scope="module")
+def bruss_65k():
+    return W.bruss(65536, n=32, seed=32)
+
+
+def test_brusselator_65k_fp64(bruss_65k):
+    w = bruss_65k
+    g = run_gpu(w, precision=B.ODE_PREC_FP64)
+    check_fp64_sample(w, g, sample(w.nsys, 4096, seed=3))
+
+
+def test_brusselator_65k_chosen_form(bruss_65k):
+    w = bruss_65k
+    g = run_gpu(w, precision=B.ODE_PREC_MIXED_LEAN)
+    check_chosen_sample(w, g, sample(w.nsys, 4096, seed=4), p99_bound=2e-3, median_bound=1e-4)
+
+
+def mixed_subset(b, idx):
+    """The systems idx of a ragged batch as a batch of their own."""
+    neq = b.neq[idx]
+    off = np.concatenate([[0], np.cumsum(neq)]).astype(np.int64)
+    y0 = np.concatenate([b.y0[b.offset[i]:b.offset[i + 1]] for i in idx])
+    pick = lambda a: np.ascontiguousarray(a[idx])
+    return W.MixedBatch(idx.size, pick(b.kind), pick(b.n), neq, off, y0, pick(b.param), pick(b.method),
+                        pick(b.t0), pick(b.tend), pick(b.rtol), pick(b.atol), coupling=b.coupling)
+
+
+def test_ragged_262k_autotuned_plan():
+    import torch
+    b = W.mixed(nsys=262144, seed=33)
+    hb = B.register(B.ODE_RHS_BRUSS1D, 256)
+    hc = B.register(B.ODE_RHS_VDP_CHAIN, 128, coupling=b.coupling)
+    try:
+        handles = np.where(b.kind == B.ODE_RHS_BRUSS1D, hb, hc)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+        y0 = dev(b.y0)
+        y = torch.empty_like(y0)
+        cnt = B.counters_like(b.nsys, "cuda")
+        plan = B.RaggedPlan(handles, b.method, b.neq, b.offset[:-1], y0, dev(b.param), dev(b.t0), dev(b.tend),
+                            dev(b.rtol), dev(b.atol), y_out=y, counters=cnt, precision=B.ODE_PREC_MIXED_LEAN,
+                            mapping=B.ODE_MAP_AUTO)
+        plan.launch()
+        torch.cuda.synchronize()
+        status = cnt.status.cpu().numpy()
+        yg = y.cpu().numpy()
+        shapes = {(d["lanes"], d["block"]) for d in plan.info()}
+        plan.destroy()
+    finally:
+        B.release(hb)
+        B.release(hc)
+    assert ((status & 0xFF) == 0).all()
+    assert np.isfinite(yg).all()
+    assert len(shapes) > 1          # the tuner chose more than one shape
+    idx = sample(b.nsys, 1024, seed=5)
+    sub = mixed_subset(b, idx)
+    ref = O.integrate_mixed(sub)
+    got = np.concatenate([yg[b.offset[i]:b.offset[i + 1]] for i in idx])
+    e = np.maximum.reduceat(np.abs(got - ref.y) / (np.abs(ref.y) + np.repeat(sub.atol, sub.neq)), sub.offset[:-1])
+    print("ragged 262,144 lean vs oracle on", idx.size, "sampled: median", np.median(e), "max", e.max())
+    assert np.quantile(e, 0.99) < 2e-3
+
+
+def test_learned_proposal_4m():
+    # a proposal network trained briefly on a logged FP64 run, then the
+    # chosen form with the proposed start and the predicted-cost order over
+    # 4,194,304 systems, as in the benchmark's ordered proposal mode
+    import torch
+    wt = W.massaction(nsys=65536, seed=1034)
+    ht = B.register_workload(wt)
+    log = torch.full((wt.nsys, wt.neq + 4), float("nan"), dtype=torch.float32, device="cuda")
+    B.integrate("rkc", ht, torch.from_numpy(wt.y0).cuda(), torch.from_numpy(wt.params).cuda(), wt.t0, wt.tend,
+                wt.rtol, wt.atol, precision=B.ODE_PREC_FP64, log_xy=log, sync=True)
+    B.release(ht)
+    ok = torch.isfinite(log).all(dim=1)
+    X, Y = log[ok, :wt.neq + 1].contiguous(), log[ok, wt.neq + 1:].contiguous()
+    net = B.MLP(wt.neq + 1, seed=0)
+    try:
+        net.fit_normalization(X, Y)
+        net.train(X, Y, epochs=4, batch=4096, lr=2e-3, seed=0)
+        w = W.massaction(nsys=1 << 22, seed=35)
+        h = B.register_workload(w)
+        try:
+            y0 = torch.from_numpy(w.y0).cuda()
+            p = torch.from_numpy(w.params).cuda()
+            h0, s0, c = net.propose(y0, p, with_cost=True)
+            cnt = B.counters_like(w.nsys, "cuda")
+            y = B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, counters=cnt,
+                            precision=B.ODE_PREC_MIXED_LEAN, mapping=B.ODE_MAP_AUTO, h0=h0, sigma0=s0, cost=c,
+                            sync=True)
+            g = {"y": y.cpu().numpy(), "status": cnt.status.cpu().numpy()}
+        finally:
+            B.release(h)
+    finally:
+        net.release()
+    assert np.mean((g["status"] & B.ODE_ST_PROPOSED) != 0) > 0.5
+    check_chosen_sample(w, g, sample(w.nsys, 8192, seed=6), p99_bound=2e-3, median_bound=1e-5)
