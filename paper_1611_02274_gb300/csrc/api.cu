@@ -165,10 +165,28 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
             fv.push_back((float)(1.0 / d->mol_weights[i]));
             fv.push_back(0.0f);
         }
+        // omega schedule: species by descending list length, each to the
+        // lane with the least work so far (ties: the lowest lane)
+        std::vector<int> by_len(S);
+        for (int i = 0; i < S; ++i) by_len[i] = i;
+        std::stable_sort(by_len.begin(), by_len.end(),
+                         [&](int x, int y) { return inc[x].size() > inc[y].size(); });
+        std::vector<std::vector<int>> lane_sp(32);
+        std::vector<size_t> load(32, 0);
+        for (int i : by_len) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            lane_sp[l].push_back(i);
+            load[l] += inc[i].size() + 1;  // the +1 keeps empty lists spread too
+        }
+        int sched_k = 0;
+        for (const auto& v : lane_sp) sched_k = std::max(sched_k, (int)v.size());
         std::vector<int> iv;
         iv.push_back(0);
         for (int i = 0; i < S; ++i) iv.push_back(iv.back() + (int)inc[i].size());
         for (int i = 0; i < S; ++i) iv.insert(iv.end(), inc[i].begin(), inc[i].end());
+        const size_t sched_pos = iv.size();
+        for (int k = 0; k < sched_k; ++k)
+            for (int l = 0; l < 32; ++l) iv.push_back(k < (int)lane_sp[l].size() ? lane_sp[l][k] : -1);
         const size_t dbytes = sizeof(double) * dv.size(), fbytes = sizeof(float) * fv.size(),
                      ibytes = sizeof(int) * iv.size();
         void* mem = nullptr;
@@ -198,6 +216,8 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
         kd.thermo32 = fp + R;
         kd.inc_off = ip;
         kd.inc = ip + S + 1;
+        kd.sched = ip + sched_pos;
+        kd.sched_k = sched_k;
         r->kin_alloc = mem;
         return ODE_OK;
     }

@@ -100,6 +100,11 @@ struct KinDevice {
     const int* inc;         // [inc_off[S]]
     const float4* rate32;   // [R]
     const float4* thermo32; // [S][2]
+    // omega schedule: lane l of a team sums the incidence lists of species
+    // sched[k * 32 + l], k < sched_k (-1: none), assigned longest list
+    // first to the least-loaded lane, so the lanes' loops are about equal
+    const int* sched;       // [sched_k][32]
+    int sched_k;
 };
 
 __host__ __device__ constexpr int kin_inc_word(int j, bool is_product, int r0, int r1, bool two) {

@@ -276,9 +276,11 @@ struct KinCtx {
 // warp per system: component c (0 = T, 1 + i = Y_i) in slot c / 32 of lane
 // c % 32.  Per evaluation the team stages the S concentrations
 // C_i = rho Y_i / W_i and the R rate constants in its shared memory; each
-// lane then sums omega_i for its species over their incidence lists
-// (reaction order, reactants first, as the oracle accumulates), and the
-// temperature equation's species sums run in species order by shuffles.
+// lane then sums omega_i over the incidence lists of the species the
+// mechanism's schedule gives it (balanced by list length; each list in
+// reaction order, reactants first, as the oracle accumulates), the owners
+// read omega_i back, and the temperature equation's species sums run in
+// species order by shuffles.
 // The plain form takes the rate constants through the series exponential
 // and logarithm (bitwise equal to the oracle's); the mixed form in FP32.
 // params [rho].
@@ -288,16 +290,17 @@ struct KinModel {
     static constexpr int W = W_, PER = 2;
     using Ctx = KinCtx;
     // shared memory per thread (floats): a team stages up to 64
-    // concentrations and kKinMaxReactions rate constants in FP64
-    static constexpr int SMEM_FLOATS = (2 * (64 + kKinMaxReactions) + W_ - 1) / W_;
+    // concentrations, 64 omega_i and kKinMaxReactions rate constants in FP64
+    static constexpr int SMEM_FLOATS = (2 * (64 + 64 + kKinMaxReactions) + W_ - 1) / W_;
     static_assert((W_ * SMEM_FLOATS) % 2 == 0, "team regions keep FP64 alignment");
     template <class R>
     struct Sys {
         const KinDevice* k;
         R rho;
         int n;
-        R* sC;  // [64] concentrations of this team's system
-        R* sK;  // [kKinMaxReactions] rate constants
+        R* sC;   // [64] concentrations of this team's system
+        R* sOm;  // [64] omega_i, summed on the schedule's lanes
+        R* sK;   // [kKinMaxReactions] rate constants
         __device__ void load(const Ctx& ctx, const Team<W>&, double p, int neq) {
             k = &ctx.k;
             rho = (R)p;
@@ -309,7 +312,8 @@ struct KinModel {
         __device__ void bind(float* block_base, int) {
             R* team = reinterpret_cast<R*>(block_base + (threadIdx.x / W) * W * SMEM_FLOATS);
             sC = team;
-            sK = team + 64;
+            sOm = team + 64;
+            sK = team + 128;
         }
         __device__ int comp(const Team<W>& tm, int s) const {
             const int c = s * W + tm.lane;
@@ -350,6 +354,16 @@ struct KinModel {
             }
             return om;
         }
+        // every omega_i into sOm, each on its scheduled lane (reads the
+        // staged sC / sK; the warp synchronises before and after)
+        __device__ void omegas(const Team<W>& tm) const {
+            __syncwarp();
+            for (int kk = 0; kk < k->sched_k; ++kk) {
+                const int i = __ldg(k->sched + kk * 32 + tm.lane);
+                if (i >= 0) sOm[i] = omega(i);
+            }
+            __syncwarp();
+        }
         __device__ void rhs(const Team<W>& tm, R, const R* y, R* f) const {
             const R T = tm.bcast(y[0], 0);
             R om[PER], cvy[PER], hw[PER];
@@ -361,14 +375,14 @@ struct KinModel {
                     if (c >= 1 && c < n) sC[c - 1] = rho * y[s] / (R)__ldg(k->W + c - 1);
                 }
                 for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, T, lnT);
-                __syncwarp();
+                omegas(tm);
 #pragma unroll
                 for (int s = 0; s < PER; ++s) {
                     om[s] = cvy[s] = hw[s] = f[s] = R(0);
                     const int c = s * W + tm.lane;
                     if (c < 1 || c >= n) continue;
                     const int i = c - 1;
-                    om[s] = omega(i);
+                    om[s] = sOm[i];
                     const double* a = k->thermo + 4 * i;
                     const R a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3);
                     const R Wi = __ldg(k->W + i);
@@ -387,14 +401,14 @@ struct KinModel {
                     if (c >= 1 && c < n) sC[c - 1] = rho * y[s] * __ldg(k->thermo32 + 2 * (c - 1) + 1).z;
                 }
                 for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, invT, log2T);
-                __syncwarp();
+                omegas(tm);
 #pragma unroll
                 for (int s = 0; s < PER; ++s) {
                     om[s] = cvy[s] = hw[s] = f[s] = R(0);
                     const int c = s * W + tm.lane;
                     if (c < 1 || c >= n) continue;
                     const int i = c - 1;
-                    om[s] = omega(i);
+                    om[s] = sOm[i];
                     const float4 a = __ldg(k->thermo32 + 2 * i), wv = __ldg(k->thermo32 + 2 * i + 1);
                     const R cvi = wv.x * (a.x + a.y * T + a.z * T * T - R(1));
                     const R ei = (wv.x * T) * (a.x + a.y * T * R(0.5) + a.z * T * T * R(1.0 / 3.0) + a.w * invT - R(1));
