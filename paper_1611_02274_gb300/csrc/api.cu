@@ -139,9 +139,9 @@ int validate_desc(const ode_rhs_desc* d, RhsEntry* r) {
                 const int i = q < nr ? d->reac[2 * j + q] : d->prod[2 * j + q - nr];
                 if (i < 0 || i >= S) return fail(ODE_ERR_ARG, "reaction %d: species index out of range", j);
             }
-            const int r0 = d->reac[2 * j], r1 = nr == 2 ? d->reac[2 * j + 1] : r0;
-            for (int q = 0; q < nr; ++q) inc[d->reac[2 * j + q]].push_back(kin_inc_word(j, false, r0, r1, nr == 2));
-            for (int q = 0; q < np; ++q) inc[d->prod[2 * j + q]].push_back(kin_inc_word(j, true, r0, r1, nr == 2));
+            const int r0 = d->reac[2 * j], r1 = nr == 2 ? d->reac[2 * j + 1] : kKinOne;
+            for (int q = 0; q < nr; ++q) inc[d->reac[2 * j + q]].push_back(kin_inc_word(j, false, r0, r1));
+            for (int q = 0; q < np; ++q) inc[d->prod[2 * j + q]].push_back(kin_inc_word(j, true, r0, r1));
         }
         std::vector<double> dv;
         dv.insert(dv.end(), d->mol_weights, d->mol_weights + S);

@@ -83,8 +83,10 @@ constexpr int kKinMaxReactions = 1024;
 // inc list, per species, the reactions it takes part in, one entry per
 // occurrence, ordered by j and reactants first (the order the oracle
 // accumulates omega_i in).  Each entry packs what the rate-of-progress
-// product needs: bit 0 is_product, bits 1-10 the reaction j, bits 11-16 and
-// 17-22 its first and second reactant species, bit 23 set when it has two.
+// product needs, one field per instruction to extract: bits 0-9 the reaction
+// j, bit 10 is_product, bits 16-21 its first reactant species, bits 24-29
+// the second (kKinOne when it has one reactant: the staged concentrations
+// keep 1 there, and the product's extra factor 1 is exact).
 // The FP32 section serves the mixed forms: per reaction (log2(10) log10 A,
 // beta, Ea log2(e), 0), so that k = 2^(x + beta log2 T - z / T); per species
 // (a0, a1, a2, a3) and (R_gas / W, W, 1 / W, 0).
@@ -107,8 +109,11 @@ struct KinDevice {
     int sched_k;
 };
 
-__host__ __device__ constexpr int kin_inc_word(int j, bool is_product, int r0, int r1, bool two) {
-    return (is_product ? 1 : 0) | (j << 1) | (r0 << 11) | (r1 << 17) | (two ? 1 << 23 : 0);
+// staged-concentration slot that holds 1 (species indices stop at 62)
+constexpr int kKinOne = 63;
+
+__host__ __device__ constexpr int kin_inc_word(int j, bool is_product, int r0, int r1) {
+    return j | (is_product ? 1 << 10 : 0) | (r0 << 16) | (r1 << 24);
 }
 
 // Kernel context of right-hand sides that need none.

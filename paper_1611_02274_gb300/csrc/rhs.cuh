@@ -347,10 +347,14 @@ struct KinModel {
             R om = R(0);
             const int e1 = __ldg(k->inc_off + i + 1);
             for (int e = __ldg(k->inc_off + i); e < e1; ++e) {
-                const int word = __ldg(k->inc + e);
-                R q = sK[(word >> 1) & 1023] * sC[(word >> 11) & 63];
-                if (word & (1 << 23)) q = q * sC[(word >> 17) & 63];
-                om = (word & 1) ? om + q : om - q;
+                const unsigned word = (unsigned)__ldg(k->inc + e);
+                R q = sK[word & 1023u] * sC[__byte_perm(word, 0u, 0x4442)];
+                if constexpr (sizeof(R) == 8) {  // FP64 pipe bound: skip the factor 1
+                    if ((word >> 24) != (unsigned)kKinOne) q = q * sC[word >> 24];
+                } else {
+                    q = q * sC[word >> 24];
+                }
+                om = (word & (1u << 10)) ? om + q : om - q;
             }
             return om;
         }
@@ -374,6 +378,7 @@ struct KinModel {
                     const int c = s * W + tm.lane;
                     if (c >= 1 && c < n) sC[c - 1] = rho * y[s] / (R)__ldg(k->W + c - 1);
                 }
+                if (tm.lane == 0) sC[kKinOne] = R(1);
                 for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, T, lnT);
                 omegas(tm);
 #pragma unroll
@@ -400,6 +405,7 @@ struct KinModel {
                     const int c = s * W + tm.lane;
                     if (c >= 1 && c < n) sC[c - 1] = rho * y[s] * __ldg(k->thermo32 + 2 * (c - 1) + 1).z;
                 }
+                if (tm.lane == 0) sC[kKinOne] = R(1);
                 for (int j = tm.lane; j < k->R; j += W) sK[j] = rate(j, invT, log2T);
                 omegas(tm);
 #pragma unroll
