@@ -116,6 +116,10 @@ __host__ __device__ constexpr int kin_inc_word(int j, bool is_product, int r0, i
     return j | (is_product ? 1 << 10 : 0) | (r0 << 16) | (r1 << 24);
 }
 
+// Detection idiom helper (member traits of models and methods).
+template <class...>
+using void_t_ = void;
+
 // Kernel context of right-hand sides that need none.
 struct NoCtx {};
 

@@ -35,8 +35,6 @@ namespace bode {
 // Floats of shared memory per thread a model asks for (Model::SMEM_FLOATS,
 // 0 if it declares none); the integrators add them to their own and hand
 // the model its part through Sys::bind.
-template <class...>
-using void_t_ = void;
 template <class M, class = void>
 struct ModelSmem {
     static constexpr int value = 0;
@@ -900,6 +898,11 @@ struct RkcMixed {
     // base address, and the odd pitch puts a warp's 32 rows in 32 banks.
     static constexpr int V_SMEM = rkc_mixed_smem_floats(W, P);
     static constexpr int SMEM_FLOATS = V_SMEM + ModelSmem<Model>::value;
+    // register budget of the kernels (255: the launch bounds alone decide).
+    // Lean warp-team systems of >= 8 values per lane (the 129-256-unknown
+    // Brusselator grids) otherwise take ~200 registers and 4 blocks of 64
+    // per SM; at 168 they keep 6.
+    static constexpr int kMaxRegs = (!SPEC && W == 32 && P >= 8) ? 168 : 255;
     mutable float vreg[V_SMEM ? 1 : P];
     float* vs;
     __device__ void bind_smem(float* base, int stride) {

@@ -47,13 +47,25 @@ __device__ __forceinline__ bool step_hold(const Method& m, bool live) {
     }
 }
 
+// Register budget of a method's kernels: Method::kMaxRegs when it declares
+// one, else 255 (the launch bounds alone decide).  Every block size stays
+// launchable (168 registers x 256 threads fit in an SM's register file).
+template <class M, class = void>
+struct KernelRegs {
+    static constexpr int value = 255;
+};
+template <class M>
+struct KernelRegs<M, void_t_<decltype(M::kMaxRegs)>> {
+    static constexpr int value = M::kMaxRegs;
+};
+
 // One system per team, one launch over the batch (the paper's intDriver
 // mapping when the team is one thread), grid rounded up.  Each iteration
 // evaluates the right-hand side once, at the point the system's phase needs.
 // Lanes past the end of the batch stay in the loop (inactive) so that the
 // warp votes see every lane.
 template <class Method, class Ctx>
-__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__(KernelRegs<Method>::value) k_static(const BatchArgs a, const __grid_constant__ Ctx ctx) {
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
@@ -98,7 +110,7 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_static(co
 // (the divergence tail of the static mapping).  The only inter-thread
 // interaction is the atomic cursor.
 template <class Method, class Ctx>
-__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) k_queue(const BatchArgs a, const __grid_constant__ Ctx ctx) {
+__global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__(KernelRegs<Method>::value) k_queue(const BatchArgs a, const __grid_constant__ Ctx ctx) {
     constexpr int W = Method::W, P = Method::P;
     using R = typename Method::R;
     const Team<W> tm = Team<W>::make();
