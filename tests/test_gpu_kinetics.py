@@ -119,3 +119,44 @@ def test_unsupported_spectral_bound_is_refused():
         assert e.value.code == B.ODE_ERR_UNSUPPORTED
     finally:
         B.release(h)
+
+
+def one_reaction_workload(nsys, seed):
+    """A -> B with a constant rate (beta = Ea = 0), equal weights and constant
+    heat capacities: Y_A = Y_A0 exp(-k t), and the heat of reaction warms
+    the gas in proportion to the A converted (as in the oracle's pins)."""
+    k, dh, Wt = 2.0e4, 3000.0, 0.03
+    mech = W.Mechanism(2, np.array([[0, 1, 1, 0], [0, 1, 1, 0]]), np.array([Wt, Wt]),
+                       np.array([[3.5, 0.0, 0.0, dh], [3.5, 0.0, 0.0, 0.0]]),
+                       np.array([1], np.int32), np.array([[0, -1]], np.int32),
+                       np.array([1], np.int32), np.array([[1, -1]], np.int32),
+                       np.array([np.log10(k)]), np.array([0.0]), np.array([0.0]), kmin=1e-30, kmax=1e30)
+    rng = np.random.default_rng(seed)
+    ya = rng.uniform(0.5, 1.0, nsys)
+    y0 = np.stack([rng.uniform(1000.0, 1500.0, nsys), ya, 1.0 - ya])
+    rho = rng.uniform(0.2, 1.0, (1, nsys))
+    w = W.Workload("kin_one", W.RHS_KINETICS, W.METHOD_RKC, nsys, 3, np.ascontiguousarray(y0), rho, 0.0, 1e-4,
+                   1e-8, 1e-14, aux={"mechanism": mech})
+    return w, k, dh, Wt
+
+
+@pytest.mark.parametrize("method", ["rkc", "rkck"])
+def test_single_reaction_mechanism(method):
+    # two species, one single-reactant reaction: most lanes of each warp hold
+    # nothing, and the rate-of-progress product takes the unit slot
+    w, k, dh, Wt = one_reaction_workload(256, seed=25)
+    edges = np.array([w.t0, w.tend])
+    mid = 1 if method == "rkc" else 0
+    yg, tg, sg = gpu_chain(w, B.ODE_PREC_FP64, edges, method=method)
+    yo, to = oracle_chain(w, edges, method=mid)
+    assert ((sg & 0xFF) == 0).all()
+    check_same(w, yg, tg, yo, to)
+    ya = w.y0[1] * np.exp(-k * w.tend)
+    T = w.y0[0] + dh * (w.y0[1] - ya) / (3.5 - 1.0)   # (R/W) dh dY / ((R/W)(3.5 - 1))
+    tol = 1e-6 if method == "rkck" else 1e-4
+    np.testing.assert_allclose(yg[1], ya, rtol=tol)
+    np.testing.assert_allclose(yg[0], T, rtol=tol)
+    yl, _, sl = gpu_chain(w, B.ODE_PREC_MIXED_LEAN, edges, method=method)
+    assert ((sl & 0xFF) == 0).all()
+    np.testing.assert_allclose(yl[1], ya, rtol=1e-3)
+    np.testing.assert_allclose(yl[1:].sum(axis=0), 1.0, rtol=1e-5)
