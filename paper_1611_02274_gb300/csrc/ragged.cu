@@ -2,7 +2,7 @@
 // methods in one plan.
 //
 // A plan groups the systems into buckets (family, method, size class =
-// smallest of 8/16/32/64/128/256 unknowns that holds them), orders each
+// smallest of 8/16/32/64/128/192/256 unknowns that holds them), orders each
 // bucket's queue by size, largest first, picks for each bucket a kernel
 // shape -- lanes per system (1, 8, 16 or 32), grid points per lane, block
 // size and mapping -- and captures every bucket's cursor reset and
@@ -58,7 +58,9 @@ int fail(int code, const char* fmt, ...) {
 
 int cuda_fail(cudaError_t e, const char* what) { return fail(ODE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e)); }
 
-const int kClasses[] = {8, 16, 32, 64, 128, 256};
+// 192 splits the largest grids: 65-96 points fill a 32-lane x 3-point team
+// instead of padding a 4-point one to 128
+const int kClasses[] = {8, 16, 32, 64, 128, 192, 256};
 
 // A kernel shape: lanes per system and grid points per lane (team = 0: the
 // family's default kernels, which pick their own shape by size).
@@ -68,7 +70,7 @@ struct Shape {
 
 // extra shapes, built for the lean mixed form with each family's own method
 // (Brusselator grids: RKC, oscillator chains: RKCK)
-const Shape kBrussShapes[] = {{1, 4, 8}, {8, 1, 16}, {16, 1, 32}, {32, 2, 128}, {1, 128, 256}};
+const Shape kBrussShapes[] = {{1, 4, 8}, {8, 1, 16}, {16, 1, 32}, {32, 2, 128}, {32, 3, 192}, {1, 128, 256}};
 const Shape kChainShapes[] = {{1, 4, 8}, {8, 1, 16}, {16, 1, 32}, {1, 64, 128}};
 
 bool tuned_method(int family, int method) {
@@ -95,7 +97,8 @@ std::vector<Shape> candidates(int family, int method, int prec, int cls, bool th
     if (!thread_only) out.push_back({0, 0, def_max});
     if (prec == ODE_PREC_MIXED_LEAN && tuned_method(family, method)) {
         const Shape* s = family == ODE_RHS_BRUSS1D ? kBrussShapes : kChainShapes;
-        const int n = family == ODE_RHS_BRUSS1D ? 5 : 4;
+        const int n = family == ODE_RHS_BRUSS1D ? (int)(sizeof(kBrussShapes) / sizeof(Shape))
+                                                : (int)(sizeof(kChainShapes) / sizeof(Shape));
         for (int k = 0; k < n; ++k) {
             if (s[k].max_neq < cls) continue;
             if (thread_only != (s[k].team == 1)) continue;
