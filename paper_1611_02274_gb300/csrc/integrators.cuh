@@ -1022,8 +1022,13 @@ struct RkcMixed {
             for (int s = 0; s < P; ++s) x[s] = yh[s] + hf * Fn[s];
             break;
         default:  // stages and F_{n+1}: w = y_n + d
+            if constexpr (SPEC) {
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) x[s] = yh[s] + (yl[s] + d1[s]);
+                for (int s = 0; s < P; ++s) x[s] = yh[s] + (yl[s] + d1[s]);
+            } else {  // lean: the compensation word is below half an ulp of yh, so it moves no point
+#pragma unroll(P <= 64 ? P : 4)
+                for (int s = 0; s < P; ++s) x[s] = yh[s] + d1[s];
+            }
         }
     }
 
