@@ -45,12 +45,11 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per system of the chosen kernel, from one ncu
-# capture of k_static<RkcMixed<JitMass, false>> (step-end hold, carry and
-# spectral-radius options, power-method vector in odd-pitch shared-memory
-# rows) on 262,144 systems of this workload (29.822 MB read + 0.917 MB
-# written); traffic grows with the number of systems (each state is read
-# once, written once)
-NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.822464e6 + 0.917248e6) / 262144
+# capture of k_static<RkcMixed<JitMass, false>> (step-end hold, stage points
+# without the compensation word) on 262,144 systems of this workload
+# (29.883 MB read + 0.899 MB written); traffic grows with the number of
+# systems (each state is read once, written once)
+NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.88288e6 + 0.89856e6) / 262144
 
 
 def dist_env():
