@@ -56,6 +56,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (a step time: the job is as slow as its
+    slowest rank); x itself on one rank.  device holds the reduction
+    tensor: the rank's GPU under NCCL, the CPU under gloo."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed (each rank its
+    own batch of units_per_rank, weak scaling) over the slowest rank's step
+    time in milliseconds."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 # ------------------------------------------------------------ flop accounting
 
 def rhs_flops(w: W.Workload) -> int:
@@ -189,10 +209,7 @@ def run_ours(args):
         barrier()
         ms = [a.elapsed_time(b) for a, b in evs]
         total = sum(ms)
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(total, world, dev)
         return total / steps, ms
 
     gpu_id = None
@@ -247,13 +264,9 @@ def run_ours(args):
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
     e2e_step = float(np.mean(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(e2e_step, world, dev)
 
-    total_sys = w.nsys * world
-    value = total_sys / (ms_chosen * 1e-3)
+    value = aggregate_rate(w.nsys, world, ms_chosen)
     achieved = flops_mixed / (ms_chosen * 1e-3) / 1e12
     achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12 if ms_plain else None
 
@@ -274,13 +287,13 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
             "rhs_evals_per_s": float(np.sum(c_mixed["n_rhs"])) * world / (ms_chosen * 1e-3),
             "plain_fp64": None if not ms_plain else {
-                "value": total_sys / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                "value": aggregate_rate(w.nsys, world, ms_plain), "ms_per_step": ms_plain,
                 "rhs_evals_per_s": float(np.sum(c_plain["n_rhs"])) * world / (ms_plain * 1e-3),
                 "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
                 "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
             "speedup_chosen_vs_plain": ms_plain / ms_chosen if ms_plain else None,
             "mixed_spec_split": None if not ms_mixed64 else {
-                "value": total_sys / (ms_mixed64 * 1e-3), "ms_per_step": ms_mixed64,
+                "value": aggregate_rate(w.nsys, world, ms_mixed64), "ms_per_step": ms_mixed64,
                 "form": "FP32 stages + Kahan state; FP64 time, step size, error-norm accumulation"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
@@ -292,7 +305,7 @@ def run_ours(args):
                          "peak_measured_fma": peak32 / 1e3, "frac_of_measured": achieved / (peak32 / 1e3),
                          "flops_per_launch": flops_mixed},
             "fp64_fma_measured_tflops": peak64 / 1e3,
-            "e2e": {"value": total_sys / (e2e_step * 1e-3), "unit": UNIT,
+            "e2e": {"value": aggregate_rate(w.nsys, world, e2e_step), "unit": UNIT,
                     "h2d_bytes_per_step": int(w.y0.nbytes + w.params.nbytes), "d2h_bytes_per_step": int(w.y0.nbytes)},
             "gpu_launches": args.steps,
             "clocks": clocks,
@@ -457,10 +470,7 @@ def pleiades_leg(args, B, torch, dev, stream, rank, world, barrier):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.pleiades_steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, dev)
     step(cnt)
     torch.cuda.synchronize()
     c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "status")}
@@ -535,10 +545,7 @@ def kinetics_leg(args, B, torch, dev, stream, rank, world, barrier):
                 if rep > 0:
                     ms.append(e0.elapsed_time(e1))
             t = float(np.mean(ms))
-            if world > 1:
-                tt = torch.tensor([t], device=dev)
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                t = float(tt.item())
+            t = max_over_ranks(t, world, dev)
             y.copy_(y0)
             carry.zero_()
             total = np.zeros(w.nsys, np.int64)
@@ -598,10 +605,7 @@ def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.specrad_steps
-        if world > 1:
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, world, dev)
         step(cnt)
         torch.cuda.synchronize()
         yy = y.cpu().numpy()
@@ -669,10 +673,7 @@ def split_leg(args, B, torch, dev, stream, rank, world, barrier):
             if rep > 0:
                 ms.append(e0.elapsed_time(e1))
         t = float(np.mean(ms))
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(t, world, dev)
         # counts and the final state of one more chain
         y.copy_(y0)
         carry.zero_()
