@@ -249,7 +249,9 @@ typedef struct {
  * network arrays) is validated and copied; *rhs_handle receives a positive
  * handle.  Errors: ODE_ERR_ARG for an unknown kind, neq out of range
  * (VDP: 2; chain: even, 2..128; Brusselator: even, 2..256; mass-action: 1..32 species,
- * 1..64 reactions; n-body: multiple of 4, 4..64) or bad indices / masses. */
+ * 1..64 reactions; n-body: multiple of 4, 4..64; kinetics: 2..64, i.e. T and
+ * up to 63 species, 1..1024 reactions) or bad indices / masses / mechanism
+ * data. */
 int ode_rhs_register(const ode_rhs_desc* desc, int32_t* rhs_handle);
 
 /* Release a handle.  ODE_ERR_HANDLE if it is not registered. */
@@ -260,6 +262,10 @@ int ode_rhs_release(int32_t rhs_handle);
  * so that the first integrate call (or a CUDA graph capture) does not pay
  * the compilation.  Kernels are cached in memory per device and as cubins
  * on disk (directory BATCHODE_CACHE_DIR, else $HOME/.cache/batchode).
+ * BATCHODE_JIT_MINBLOCKS overrides the register budget of the generated
+ * kernels (that many 128-thread blocks resident per SM; defaults 2 for
+ * ODE_PREC_FP64, 3 for the mixed forms) and BATCHODE_JIT_VERBOSE=1 prints
+ * the compiler's resource report to stderr.
  * Without a visible device only the compilation (and disk cache) happens.
  * Other families need no preparation and return ODE_OK.  Errors:
  * ODE_ERR_HANDLE, ODE_ERR_ARG, ODE_ERR_UNSUPPORTED (NVRTC missing or the
