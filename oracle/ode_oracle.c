@@ -437,6 +437,81 @@ static void jac_nbody(const or_sys* s, const double* y, double* J) {
     }
 }
 
+/* Kinetics (state T, Y_1..Y_S): with C_i = rho Y_i / W_i, q_j = k_j(T)
+ * prod over reactant occurrences of C, omega_i = sum_j nu_ij q_j,
+ * H = sum_i e_i W_i omega_i and f_T = -H / (rho c_v):
+ *   dq_j/dY_l: product rule over the reactant occurrences of species l,
+ *              each giving k_j (prod of the other occurrences) rho / W_l;
+ *   dq_j/dT  = q_j (beta_j / T + Ea_j / T^2) where k_j is not clipped, else 0;
+ *   row Y_i  = (W_i / rho) d omega_i;
+ *   row T    = -(dH c_v - H dc_v) / (rho c_v^2), dH/dT taking de_i/dT =
+ *              c_v,i and dc_v/dT = sum_i Y_i (R / W_i)(a1 + 2 a2 T).
+ * The omega_i derivatives are summed reaction by reaction, reactants before
+ * products, as omega_i is. */
+static void jac_kinetics(const or_sys* s, const double* y, double* J) {
+    const or_mech* k = s->m->mech;
+    const double ln10 = 2.302585092994046;
+    int S = k->n_species, N = s->neq;
+    double rho = s->p[0];
+    double T = y[0];
+    const double* Y = y + 1;
+    double lnT = or_log(T);
+    double om[S > 0 ? S : 1];
+    for (int z = 0; z < N * N; ++z) J[z] = 0.0;
+    for (int i = 0; i < S; ++i) om[i] = 0.0;
+    for (int j = 0; j < k->n_reactions; ++j) {
+        double raw = or_exp(ln10 * k->log10A[j] + k->beta[j] * lnT - k->Ea[j] / T);
+        double kj = fmin(fmax(raw, k->kmin), k->kmax);
+        int nr = k->n_reac[j], np = k->n_prod[j];
+        double c[2];
+        for (int r = 0; r < nr; ++r) c[r] = rho * Y[k->reac[2 * j + r]] / k->W[k->reac[2 * j + r]];
+        double q = kj;
+        for (int r = 0; r < nr; ++r) q = q * c[r];
+        double dT = (raw > k->kmin && raw < k->kmax) ? q * (k->beta[j] / T + k->Ea[j] / (T * T)) : 0.0;
+        for (int r = 0; r < nr; ++r) J[(1 + k->reac[2 * j + r]) * N] -= dT;
+        for (int r = 0; r < np; ++r) J[(1 + k->prod[2 * j + r]) * N] += dT;
+        for (int o = 0; o < nr; ++o) {  /* the o-th reactant occurrence */
+            int l = k->reac[2 * j + o];
+            double d = kj;
+            for (int r = 0; r < nr; ++r)
+                if (r != o) d = d * c[r];
+            d = d * rho / k->W[l];
+            for (int r = 0; r < nr; ++r) J[(1 + k->reac[2 * j + r]) * N + 1 + l] -= d;
+            for (int r = 0; r < np; ++r) J[(1 + k->prod[2 * j + r]) * N + 1 + l] += d;
+        }
+        for (int r = 0; r < nr; ++r) om[k->reac[2 * j + r]] -= q;
+        for (int r = 0; r < np; ++r) om[k->prod[2 * j + r]] += q;
+    }
+    double cv = 0.0, H = 0.0, dcv_dT = 0.0, dH_dT_e = 0.0;
+    for (int i = 0; i < S; ++i) {
+        const double* a = k->thermo + 4 * i;
+        double cvi = (R_GAS / k->W[i]) * (a[0] + a[1] * T + a[2] * T * T - 1.0);
+        double ei = (R_GAS * T / k->W[i]) * (a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] / T - 1.0);
+        cv = cv + Y[i] * cvi;
+        H = H + ei * om[i] * k->W[i];
+        dcv_dT = dcv_dT + Y[i] * (R_GAS / k->W[i]) * (a[1] + 2.0 * a[2] * T);
+        dH_dT_e = dH_dT_e + cvi * om[i] * k->W[i];
+    }
+    for (int l = 0; l < N; ++l) {
+        double dH = (l == 0) ? dH_dT_e : 0.0;
+        for (int i = 0; i < S; ++i) {
+            const double* a = k->thermo + 4 * i;
+            double ei = (R_GAS * T / k->W[i]) * (a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] / T - 1.0);
+            dH = dH + ei * k->W[i] * J[(1 + i) * N + l];
+        }
+        double dcv;
+        if (l == 0) {
+            dcv = dcv_dT;
+        } else {
+            const double* a = k->thermo + 4 * (l - 1);
+            dcv = (R_GAS / k->W[l - 1]) * (a[0] + a[1] * T + a[2] * T * T - 1.0);
+        }
+        J[l] = -(dH * cv - H * dcv) / (rho * cv * cv);
+    }
+    for (int i = 0; i < S; ++i)
+        for (int l = 0; l < N; ++l) J[(1 + i) * N + l] = J[(1 + i) * N + l] * k->W[i] / rho;
+}
+
 static void jacobian(const or_sys* s, const double* y, double* J) {
     int N = s->neq;
     switch (s->m->kind) {
@@ -445,6 +520,7 @@ static void jacobian(const or_sys* s, const double* y, double* J) {
     case KIND_BRUSS1D: jac_bruss(s, y, J); break;
     case KIND_MASSACTION: jac_massaction(s, y, J); break;
     case KIND_NBODY: jac_nbody(s, y, J); break;
+    case KIND_KINETICS: jac_kinetics(s, y, J); break;
     case KIND_LINEAR:
         for (int k = 0; k < N * N; ++k) J[k] = s->p[k];
         break;

@@ -105,3 +105,86 @@ def test_integration_keeps_invariants(wk):
         u0 = np.sum(y0[1:] * thermo(mech, y0[0])[1])
         u1 = np.sum(y1[1:] * thermo(mech, y1[0])[1])
         assert abs(u1 - u0) <= 1e-5 * np.abs(y1[1:] * thermo(mech, y1[0])[1]).sum()
+
+
+def dcv_dT(mech, T):
+    a = mech.thermo
+    return (R / mech.W) * (a[:, 1] + 2.0 * a[:, 2] * T)
+
+
+def test_jacobian_against_central_differences(wk):
+    m = O.model_for(wk)
+    for y, rho in random_states(wk, n=3, seed=7):
+        J = O.jacobian(m, [rho], y)
+        fd = np.zeros_like(J)
+        for l in range(y.size):
+            h = 1e-6 * max(abs(y[l]), 1e-6)
+            yp, ym = y.copy(), y.copy()
+            yp[l] += h
+            ym[l] -= h
+            fd[:, l] = (O.rhs(m, [rho], yp) - O.rhs(m, [rho], ym)) / (2.0 * h)
+        scale = np.abs(J).max(axis=1)
+        live = scale > 0                     # species in no reaction have zero rows
+        assert (np.abs(J - fd)[live] / scale[live, None]).max() < 1e-4
+        assert np.abs(fd[~live]).max(initial=0.0) == 0.0
+
+
+def test_jacobian_conserves_mass_elements_and_energy(wk):
+    # the invariants hold for every state, so their derivatives vanish:
+    # sum_i dY_i/dt = 0, sum_i comp_ie / W_i dY_i/dt = 0 and
+    # sum_i e_i dY_i/dt + c_v dT/dt = 0 differentiated by each component
+    m, mech = O.model_for(wk), wk.aux["mechanism"]
+    for y, rho in random_states(wk, n=4, seed=8):
+        J = O.jacobian(m, [rho], y)
+        f = O.rhs(m, [rho], y)
+        JY = J[1:]
+        assert np.abs(JY.sum(axis=0)).max() <= 1e-12 * np.abs(JY).sum(axis=0).max()
+        for e in range(4):
+            g = (mech.comp[:, e] / mech.W) @ JY
+            assert np.abs(g).max() <= 1e-11 * (np.abs(mech.comp[:, e] / mech.W) @ np.abs(JY)).max() + 1e-300
+        T, Y = y[0], y[1:]
+        cv_i, e_i = thermo(mech, T)
+        cv = np.sum(Y * cv_i)
+        dcv = np.concatenate([[np.sum(Y * dcv_dT(mech, T))], cv_i])
+        total = e_i @ JY + dcv * f[0] + cv * J[0]
+        total[0] += np.sum(cv_i * f[1:])                    # de_i/dT = c_v,i
+        scale = np.abs(e_i) @ np.abs(JY) + np.abs(dcv * f[0]) + np.abs(cv * J[0])
+        scale[0] += np.sum(np.abs(cv_i * f[1:]))
+        assert (np.abs(total) / scale).max() < 1e-10
+
+
+def test_single_reaction_jacobian_closed_form():
+    # A -> B, constant k, equal weights, constant heat capacities:
+    # dY_A/dt = -k Y_A, dY_B/dt = k Y_A, dT/dt = dh k Y_A / (2.5 (Y_A + Y_B))
+    k, dh = 2.0e4, 3000.0
+    mech = one_reaction_mechanism(k, dh)
+    mod = O.model(O.KIND_KINETICS, 3, 1, mechanism=mech)
+    T, ya, yb, rho = 1300.0, 0.7, 0.25, 0.4
+    J = O.jacobian(mod, [rho], np.array([T, ya, yb]))
+    s = ya + yb
+    exact = np.array([[0.0, dh * k / (2.5 * s) - dh * k * ya / (2.5 * s * s), -dh * k * ya / (2.5 * s * s)],
+                      [0.0, -k, 0.0],
+                      [0.0, k, 0.0]])
+    np.testing.assert_allclose(J, exact, rtol=1e-13, atol=1e-9)
+    assert O.gershgorin(mod, [rho], np.array([T, ya, yb])) == pytest.approx(np.abs(exact).sum(axis=1).max(), rel=1e-14)
+
+
+def test_gershgorin_bounds_the_spectrum(wk):
+    m = O.model_for(wk)
+    for y, rho in random_states(wk, n=3, seed=9):
+        J = O.jacobian(m, [rho], y)
+        G = O.gershgorin(m, [rho], y)
+        assert G == pytest.approx(np.abs(J).sum(axis=1).max(), rel=1e-12)
+        assert np.abs(np.linalg.eigvals(J)).max() <= G * (1.0 + 1e-12)
+
+
+def test_rkc_with_the_gershgorin_bound_follows_the_closed_form():
+    k, dh, T0, rho, tend = 2.0e4, 3000.0, 1200.0, 0.5, 1e-4
+    mech = one_reaction_mechanism(k, dh)
+    mod = O.model(O.KIND_KINETICS, 3, 1, mechanism=mech)
+    y0 = np.array([[T0], [0.9], [0.1]])
+    r = O.integrate(mod, 1, y0, np.array([[rho]]), 0.0, tend, 1e-10, 1e-14, specrad=O.SPECRAD_GERSHGORIN)
+    assert r.status[0] == 0 and r.n_specrad_iter[0] == 0
+    YA = 0.9 * np.exp(-k * tend)
+    T = T0 + dh * (0.9 - YA) / 2.5
+    np.testing.assert_allclose(r.y[:, 0], [T, YA, 1.0 - YA], rtol=1e-6)
