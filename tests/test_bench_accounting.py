@@ -1,0 +1,49 @@
+"""The benchmark's algorithmic flop model, the numerator of its roofline
+figure, on a hand-built network: one mass-action evaluation costs |R|
+multiplications per reaction (rate constant times each reactant
+occurrence) plus one accumulation per reactant and product occurrence;
+the RKC total is linear in the per-system counters and charges every
+evaluation that price."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+from paper_1611_02274_gb300 import workloads as W  # noqa: E402
+
+
+def tiny_network():
+    # A -> B, A + B -> C, 2A -> B + C
+    return W.Network(3, np.array([1, 2, 2], np.int32), np.array([[0, -1], [0, 1], [0, 0]], np.int32),
+                     np.array([1, 1, 2], np.int32), np.array([[1, -1], [2, -1], [1, 2]], np.int32),
+                     np.zeros(3), np.zeros(3), np.zeros(3))
+
+
+def test_rhs_flops_counts_the_mass_action_law():
+    w = W.Workload("tiny", W.RHS_MASSACTION, W.METHOD_RKC, 1, 3, np.ones((3, 1)), np.ones((1, 1)),
+                   0.0, 1.0, 1e-6, 1e-12, network=tiny_network())
+    # k C_A, then -r to A, +r to B            : 1 + 2 = 3
+    # k C_A C_B, then -r to A and B, +r to C  : 2 + 3 = 5
+    # k C_A C_A, then -r twice to A, +r to B, C: 2 + 4 = 6
+    assert bench.rhs_flops(w) == 3 + 5 + 6
+
+
+def test_rkc_flops_is_linear_in_the_counters_and_prices_each_evaluation():
+    w = W.massaction(nsys=4, seed=0)
+    rng = np.random.default_rng(0)
+    acc = rng.integers(500, 1500, 4)
+    rej = rng.integers(0, 3, 4)
+    sr = rng.integers(10, 90, 4)
+    rhs = 2 + sr + 2 * (acc + rej)                      # m = 2 on every attempt
+    total = bench.rkc_flops(w, acc, rej, rhs, sr)
+    per = [bench.rkc_flops(w, acc[i:i + 1], rej[i:i + 1], rhs[i:i + 1], sr[i:i + 1]) for i in range(4)]
+    assert total == sum(per)                             # a sum over systems
+    one_more = bench.rkc_flops(w, acc[:1], rej[:1], rhs[:1] + 1, sr[:1] + 1)   # one more power iteration
+    assert one_more - per[0] == bench.rhs_flops(w) + 6 * w.neq
+
+
+def test_aggregate_rate_is_all_ranks_units_over_the_slowest_time():
+    assert bench.aggregate_rate(1 << 20, 1, 52.0) == (1 << 20) / 0.052
+    assert bench.aggregate_rate(1 << 20, 8, 52.0) == 8 * (1 << 20) / 0.052
