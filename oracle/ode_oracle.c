@@ -74,6 +74,11 @@
  *       POWER (the Appendix method), GERSHGORIN (sigma = G at every point
  *       the power method would run, no right-hand-side evaluations),
  *       POWER_CAPPED (the power method's 1.2 sigma, capped at G).
+ *   R26 Jacobian of a clipped rate constant (the kinetics family bounds
+ *       k_j to [kmin, kmax]; the paper's mechanism has no such bound): the
+ *       clipped value does not vary with T, so dk_j/dT = 0 wherever the
+ *       unclipped value lies outside the open interval (kmin, kmax),
+ *       including exactly at a bound.
  */
 #include <math.h>
 #include <stdint.h>
