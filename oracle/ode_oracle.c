@@ -45,6 +45,8 @@
  *   R10 Powers in the step-size rules and the Arrhenius rate use the series
  *       logarithm / exponential below, a fixed sequence of correctly
  *       rounded operations, so their values are reproducible bit for bit.
+ *       Compiled with -DORACLE_LIBM the C library's log / exp / pow are
+ *       used instead (a build that tests compare with this one).
  *   R21 Warm restart (the outer global-step loop of Section 3, where the
  *       paper notes that carrying step information from one global step to
  *       the next could help but restarts every call): an optional carry
@@ -586,6 +588,9 @@ static void dydt(const or_sys* s, double t, const double* y, double* f) {
 #define SQRT_HALF 0.7071067811865476
 
 static double or_log(double x) {
+#ifdef ORACLE_LIBM
+    return log(x);  /* R10 off: the C library's function (a comparison build) */
+#endif
     if (!(x > 0.0)) return (x == 0.0) ? -INFINITY : NAN;
     if (isinf(x)) return x;
     int k;
@@ -614,6 +619,9 @@ static double or_log(double x) {
 }
 
 static double or_exp(double x) {
+#ifdef ORACLE_LIBM
+    return exp(x);
+#endif
     if (isnan(x)) return x;
     if (x > 709.0) return INFINITY;
     if (x < -745.0) return 0.0;
@@ -638,6 +646,9 @@ static double or_exp(double x) {
 }
 
 static double or_pow(double x, double y) {
+#ifdef ORACLE_LIBM
+    return pow(x, y);
+#endif
     if (x == 0.0) return (y > 0.0) ? 0.0 : INFINITY;
     return or_exp(y * or_log(x));
 }

@@ -51,13 +51,14 @@ class Mech(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(libm: bool = False):
+    """The oracle library (libm=True: the variant with the C library's
+    powers in place of the series of reading R10, for comparison)."""
+    if libm not in _libs:
+        path = _build.build(libm=libm)
         L = C.CDLL(path)
         P = C.c_void_p
         L.oracle_integrate.argtypes = [P, C.c_int, C.c_int64, P, P, C.c_double, C.c_double,
@@ -84,8 +85,8 @@ def lib():
         L.oracle_exp.argtypes = [C.c_double]
         L.oracle_log.argtypes = [C.c_double]
         assert L.oracle_model_size() == C.sizeof(Model)
-        _lib = L
-    return _lib
+        _libs[libm] = L
+    return _libs[libm]
 
 
 def _p(a: np.ndarray | None):
@@ -159,7 +160,7 @@ class Result:
 def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: float, atol: float,
               max_attempts: int = 1_000_000, nthreads: int = 0, carry_in=None,
               carry_out: bool = False, carry_mode: int = CARRY_CONTINUE,
-              specrad: int = SPECRAD_POWER) -> Result:
+              specrad: int = SPECRAD_POWER, libm: bool = False) -> Result:
     """Integrate a uniform SoA batch y0[neq, nsys]; method 0 = RKCK, 1 = RKC.
     carry_in (SoA [carry_words(neq), nsys]) resumes a previous call's
     controller state (carry_mode CARRY_CONTINUE or CARRY_RESTART); carry_out
@@ -175,7 +176,7 @@ def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: f
     if cin is not None:
         assert cin.shape == (carry_words(m.neq), nsys)
     cout = np.zeros((carry_words(m.neq), nsys)) if carry_out else None
-    rc = lib().oracle_integrate(C.byref(m), method, nsys, _p(y0), _p(params), t0, tend, rtol,
+    rc = lib(libm).oracle_integrate(C.byref(m), method, nsys, _p(y0), _p(params), t0, tend, rtol,
                                 atol, max_attempts, _p(y), *[_p(a) for a in c], nthreads,
                                 _p(cin) if cin is not None else None, _p(cout) if cout is not None else None,
                                 carry_mode, specrad)
@@ -184,9 +185,9 @@ def integrate(m: Model, method: int, y0, params, t0: float, tend: float, rtol: f
     return Result(y, *c, carry=cout)
 
 
-def integrate_workload(w, nthreads: int = 0, max_attempts: int = 1_000_000) -> Result:
+def integrate_workload(w, nthreads: int = 0, max_attempts: int = 1_000_000, libm: bool = False) -> Result:
     return integrate(model_for(w), w.method, w.y0, w.params, w.t0, w.tend, w.rtol, w.atol,
-                     max_attempts, nthreads)
+                     max_attempts, nthreads, libm=libm)
 
 
 def integrate_mixed(b, nthreads: int = 0, max_attempts: int = 1_000_000) -> Result:
