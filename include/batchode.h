@@ -92,6 +92,17 @@ extern "C" {
                                 -- the time t -- and for the Chebyshev coefficients.  The FP64 pipe
                                 of this GPU runs at 1/64 of the FP32 rate, so every FP64 instruction
                                 of the step-size bookkeeping costs as much as ~64 FP32 ones */
+#define ODE_PREC_F2 3        /* RKC only: state, stages, evaluation points and right-hand side in
+                                two-float arithmetic (each value an unevaluated sum of two FP32
+                                words, ~48 significant bits, FP32 instructions only); FP64 time,
+                                step size, spectral radius and error-norm accumulation; Chebyshev
+                                coefficients from the FP64 table as word pairs.  Follows the FP64
+                                form's step sequence, where FP32 evaluation points do not: at
+                                rtol 1e-6 their rounding is several percent of the error estimate
+                                of Eq. E:rmsE.  Families: van der Pol, Brusselator, mass-action */
+#define ODE_PREC_F2_LEAN 4   /* as ODE_PREC_F2 with FP32 step size, spectral radius and error norm
+                                and the remaining interval as an FP32 pair (no FP64 instruction in
+                                the step loop) */
 
 /* how systems map onto the GPU */
 #define ODE_MAP_AUTO 0       /* uniform batches: the first call with >= 32768 systems times the
@@ -302,12 +313,17 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
  * loads this library holds until the process exits.  The paper has no
  * counterpart; it is a packaging of the same integrator.
  *
- * Same arguments and results as rkc_integrate, except: y0, params, y_out
- * and the stats arrays are HOST pointers (pinned memory gives asynchronous
- * copies; y_out may alias y0); opts->io and opts->codegen are ignored (the
- * built-in kernels are used, never run-time generated ones, since loading
- * generated code allocates), and so are opts->h0, sigma0, log_xy, cost and
- * carry.  A batch whose staged arrays need more than the
+ * Same arguments and results as rkc_integrate (every built-in family;
+ * opts->specrad as there, kinetics with the power method only), except: y0,
+ * params, y_out and the stats arrays are HOST pointers (pinned memory gives
+ * asynchronous copies; y_out may alias y0); precisions ODE_PREC_FP64,
+ * ODE_PREC_MIXED and ODE_PREC_MIXED_LEAN only (others: ODE_ERR_ARG);
+ * opts->mapping ODE_MAP_THREAD runs one launch over the batch and any other
+ * value the persistent queue (no tuning runs: they would need scratch
+ * output); opts->io and opts->codegen are ignored (the built-in kernels
+ * are used, never run-time generated ones, since loading generated code
+ * allocates), and so are opts->h0, sigma0, log_xy, cost, carry and
+ * carry_mode.  A batch whose staged arrays need more than the
  * scratch offers -- nsys * 8 * (neq + n_params) bytes plus 4 * nsys per
  * requested counter array, each rounded up to 256 bytes, against 16 MiB
  * minus the cursor and table -- is rejected with ODE_ERR_ARG before any GPU
@@ -320,7 +336,8 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
  * contents there: the cursor is cleared on every call, and every staged or
  * output element is rewritten.  Calls that overlapped on the GPU would race
  * on the array; this entry point serialises its own calls with a process-wide
- * lock and synchronises the stream before returning. */
+ * lock and synchronises the stream before returning -- on error returns too,
+ * once anything was queued. */
 #define ODE_NOALLOC_SCRATCH_BYTES 16777216 /* 16 MiB */
 int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
                           double tend, double rtol, double atol, const ode_opts* opts, double* y_out,

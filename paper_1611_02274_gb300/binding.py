@@ -23,7 +23,7 @@ ODE_ST_SPECRAD_NOCONV = 256
 ODE_ST_PROPOSED = 512
 MLP_HIDDEN, MLP_MAX_IN, MLP_OUT, MLP_NORM_FLOATS = 64, 33, 3, 138
 ODE_RHS_VDP, ODE_RHS_VDP_CHAIN, ODE_RHS_BRUSS1D, ODE_RHS_MASSACTION, ODE_RHS_NBODY, ODE_RHS_KINETICS = 1, 2, 3, 4, 5, 6
-ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN = 0, 1, 2
+ODE_PREC_FP64, ODE_PREC_MIXED, ODE_PREC_MIXED_LEAN, ODE_PREC_F2, ODE_PREC_F2_LEAN = 0, 1, 2, 3, 4
 ODE_MAP_AUTO, ODE_MAP_THREAD, ODE_MAP_QUEUE = 0, 1, 2
 ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
 ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
@@ -258,7 +258,7 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
 def integrate_noalloc(handle: int, y0: np.ndarray, params: np.ndarray, t0: float, tend: float, rtol: float,
                       atol: float, y_out: np.ndarray | None = None, counters: Counters | None = None,
                       precision: int = ODE_PREC_FP64, mapping: int = ODE_MAP_AUTO, block_size: int = 0,
-                      max_attempts: int = 0, stream=None) -> np.ndarray:
+                      max_attempts: int = 0, stream=None, specrad: int = 0) -> np.ndarray:
     """rkc_integrate_noalloc on host (numpy) arrays: RKC through a static
     device scratch, with no GPU memory allocated by the library."""
     nsys = int(y0.shape[1])
@@ -266,6 +266,7 @@ def integrate_noalloc(handle: int, y0: np.ndarray, params: np.ndarray, t0: float
         y_out = np.empty_like(y0)
     o = Opts()
     o.precision, o.mapping, o.block_size, o.max_attempts = precision, mapping, block_size, max_attempts
+    o.specrad = specrad
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [

@@ -63,6 +63,14 @@ struct Pick<false, T, F> {
 __host__ __device__ constexpr int rkc_mixed_smem_floats(int lanes, int per_lane) {
     return (lanes == 1 && per_lane <= 32) ? (per_lane | 1) : 0;
 }
+// The same for the two-float RKC integrator: leading words in [0, P),
+// trailing words in [P, 2P), the row rounded up to an odd length.
+__host__ __device__ constexpr int rkc_f2_smem_floats(int lanes, int per_lane) {
+    return (lanes == 1 && per_lane <= 32) ? ((2 * per_lane) | 1) : 0;
+}
+
+// Two-float forms (ODE_PREC_F2, ODE_PREC_F2_LEAN).
+__host__ __device__ constexpr bool prec_is_f2(int prec) { return prec == 3 || prec == 4; }
 
 // Warm-restart carry words (see batchode.h): valid flag, time reached, h,
 // sigma, h_old, err_old, accepted-step count, count at the last
@@ -145,7 +153,9 @@ struct BatchArgs {
     unsigned long long* cursor;
     // RKC stage coefficients for m = 2..rkc_tab_max (entry (m, j), j = 1..m,
     // at index m (m - 1) / 2 - 1 + j - 1): FP64 {1 - mu - nu, mu, nu, mu~,
-    // gamma~, c, 0, 0} and FP32 {mu, nu, mu~, gamma~}
+    // gamma~, c, lo} and FP32 {mu, nu, mu~, gamma~}, where the FP32 words
+    // are the leading words of the two-float coefficients and lo (the FP64
+    // entry's last 16 bytes) holds their four trailing words
     const double* rkc_tab64;
     const float4* rkc_tab32;
     int32_t rkc_tab_max;

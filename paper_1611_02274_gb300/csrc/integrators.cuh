@@ -1389,3 +1389,5 @@ struct RkcMixed {
 };
 
 }  // namespace bode
+
+#include "integrators_f2.cuh"

@@ -1,0 +1,535 @@
+// integrators_f2.cuh -- RKC (Section 2.2, rkcDriver of Section 3.2 with the
+// Appendix power method) with the state, the stages, the evaluation points
+// and the right-hand side in two-float arithmetic (f2.cuh).
+//
+// Why: at rtol 1e-6 the RKC error estimate of Eq. E:rmsE is a difference of
+// terms of size h f that cancel down to ~rtol |y|.  With FP32 evaluation
+// points and right-hand sides, their rounding (~6e-8 relative) shows up in
+// the estimate as noise of several percent; the step-size rule of
+// Eqs. dtnp1 / rkc-f turns that noise into a different step sequence, and
+// the final state drifts from the FP64 solution by up to ~1e-5 relative.
+// Two-float words carry ~48 bits, so the estimate -- and with it the step
+// sequence -- follows the FP64 method; the arithmetic stays on the FP32
+// pipe, which on this GPU is 64 times faster than the FP64 pipe.
+//
+// Scalars: step size, spectral radius and error norm in FP32 (their own
+// rounding perturbs the step sequence by ~1e-7 relative, far below the
+// controller's sensitivity), the remaining interval as an FP32 pair; with
+// BK64 the time, step size and spectral radius are FP64 and the error norm
+// is accumulated in FP64, as the spec split keeps bookkeeping.
+// Chebyshev coefficients come from the FP64-built table as two-float pairs.
+// The power method runs in two-float arithmetic with the FP64 perturbation
+// size sqrt(uround) (the difference quotient keeps ~7 digits).
+#pragma once
+
+#include "f2.cuh"
+
+namespace bode {
+
+// sqrt(2.22e-16): the power method's relative perturbation (Appendix)
+constexpr float kSqrtUround = 1.4899664e-8f;
+
+// Floats of shared memory per thread a system asks for to hold its
+// constants (Sys::CONST_SMEM, 0 if it declares none).
+template <class S, class = void>
+struct ConstSmem {
+    static constexpr int value = 0;
+};
+template <class S>
+struct ConstSmem<S, void_t_<decltype(S::CONST_SMEM)>> {
+    static constexpr int value = S::CONST_SMEM;
+};
+
+template <class Model, bool BK64 = false>
+struct RkcF2 {
+    static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
+    static constexpr int W = Model::W, P = Model::PER;
+    using R = F2;
+    using TM = Team<W>;
+    using HT = typename Pick<BK64, double, float>::type;
+    typename Model::template Sys<F2> sys;
+    F2 y[P], Fn[P], d1[P];  // d_j = w_j - y_n (d_0 = 0); d_{j-2} below
+    static constexpr int V_SMEM = rkc_f2_smem_floats(W, P);
+    // the system's constants, one row per thread after the V rows (an even
+    // offset: 8-byte aligned pairs, since blocks are a multiple of 32 threads)
+    static constexpr int C_SMEM = ConstSmem<typename Model::template Sys<F2>>::value;
+    // d_{j-2}, needed only from the third stage on: for one-thread systems a
+    // row of pairs in shared memory (an odd number of pairs per row), so a
+    // two-stage step -- the common case at tight tolerances -- touches it
+    // never and holds no registers for it
+    static constexpr int D2_SMEM = (W == 1 && P <= 32) ? 2 * (P | 1) : 0;
+    static constexpr int SMEM_FLOATS = V_SMEM + C_SMEM + D2_SMEM + ModelSmem<Model>::value;
+    mutable F2 vreg[V_SMEM ? 1 : P];
+    mutable F2 d2reg[D2_SMEM ? 1 : P];
+    float* vs;
+    F2* d2s;
+    __device__ void bind_smem(float* base, int stride) {
+        vs = base + threadIdx.x * V_SMEM;  // this thread's row
+        if constexpr (C_SMEM > 0) sys.bind_consts(base + V_SMEM * stride + threadIdx.x * C_SMEM);
+        if constexpr (D2_SMEM > 0)
+            d2s = reinterpret_cast<F2*>(base + (V_SMEM + C_SMEM) * stride + threadIdx.x * D2_SMEM);
+        if constexpr (ModelSmem<Model>::value > 0) sys.bind(base + (V_SMEM + C_SMEM + D2_SMEM) * stride, stride);
+    }
+    __device__ F2 D2g(int s) const {
+        if constexpr (D2_SMEM > 0)
+            return d2s[s];
+        else
+            return d2reg[s];
+    }
+    __device__ void D2s(int s, F2 v) const {
+        if constexpr (D2_SMEM > 0)
+            d2s[s] = v;
+        else
+            d2reg[s] = v;
+    }
+    __device__ F2 Vg(int s) const {
+        if constexpr (V_SMEM > 0)
+            return F2(vs[s], vs[P + s]);
+        else
+            return vreg[s];
+    }
+    __device__ void Vs(int s, F2 v) const {
+        if constexpr (V_SMEM > 0) {
+            vs[s] = v.hi;
+            vs[P + s] = v.lo;
+        } else {
+            vreg[s] = v;
+        }
+    }
+    double t, tend;                   // BK64
+    float remf, reml, tendf;          // FP32 scalars: remaining interval as a pair
+    HT hmax, hmin, h, h_old, sigma;
+    F2 hh;                            // the step size as a pair (exact for an FP32 h)
+    float rtolf, atolf, c3_old, dynrm, sig;
+    float4 chi, clo;                  // (mu_j, nu_j, mu~_j, gamma~_j), leading / trailing words
+    CoefSource cs;
+    int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
+    int32_t phase, m, j, sr_iter;
+    bool have_sigma, rejected, warm;
+
+    __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        n = a.neq_of(i);
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            y[s] = F2(c >= 0 ? a.y0[a.yidx(i, c)] : 0.0);
+        }
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
+        remf = (float)(tend - t);
+        reml = (float)((tend - t) - (double)remf);
+        tendf = (float)tend;
+        rtolf = (float)a.rtol_of(i);
+        atolf = (float)a.atol_of(i);
+        mmax = (int)round(sqrt(a.rtol_of(i) / (10.0 * kUround)));
+        if (mmax < 2) mmax = 2;
+        hmax = (HT)fabs(tend - t);
+        hmin = (HT)(10.0 * kUround * fmax(fabs(t), fabs(tend - t)));
+        n_acc = n_rej = n_sr = status = 0;
+        n_rhs = 1;
+        max_att = a.max_attempts;
+        h = h_old = sigma = (HT)0;
+        c3_old = 0.0f;
+        num_step = 0;
+        sr_step = -1;
+        have_sigma = rejected = false;
+        warm = carry_warm(a, i);
+        if (warm) {  // resume the controller and the spectral-radius schedule
+            h = (HT)a.carry[a.cidx(i, kCarryH)];
+            sigma = (HT)a.carry[a.cidx(i, kCarrySigma)];
+            h_old = (HT)a.carry[a.cidx(i, kCarryHold)];
+            c3_old = fpow((float)a.carry[a.cidx(i, kCarryErrOld)], 1.0f / 3.0f);
+            num_step = (int)a.carry[a.cidx(i, kCarryNumStep)];
+            sr_step = (int)a.carry[a.cidx(i, kCarrySrStep)];
+            rejected = (int)a.carry[a.cidx(i, kCarryRejected)] != 0;
+            have_sigma = true;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                const int c = sys.comp(tm, s);
+                Vs(s, F2(c >= 0 ? a.carry[a.cidx(i, kCarryFixed + c)] : 0.0));
+            }
+            if (a.carry_mode == ODE_CARRY_RESTART) {
+                num_step = 0;
+                sr_step = -1;
+                rejected = false;
+            }
+        } else if (a.h0 != nullptr) {
+            // a proposed start replaces the initial power method and Euler
+            // trial; the first rejection returns the system to the power method
+            const float hp = a.h0[i], sp = a.sigma0[i];
+            if (isfinite(hp) && isfinite(sp) && hp > 0.0f && sp > 0.0f) {
+                h = (HT)hp < hmax ? (HT)hp : hmax;
+                h = h > hmin ? h : hmin;
+                sigma = (HT)sp;
+                have_sigma = true;
+                sr_step = 0;
+                status |= ODE_ST_PROPOSED;
+            }
+        }
+        phase = PH_F0;
+    }
+    __device__ bool done() const { return phase == PH_DONE; }
+    __device__ bool in_stages() const { return phase == PH_STAGE; }
+    __device__ bool at_step_end() const { return phase == PH_FINAL; }
+
+    // sum of squares of the leading words (norms that only scale a vector)
+    template <class X>
+    __device__ float sumsq_hi(const TM& tm, X x_of) const {
+        float acc = 0.0f;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s)
+            if (sys.comp(tm, s) >= 0) {
+                const float v = x_of(s);
+                acc = fmaf(v, v, acc);
+            }
+        return tm.sum(acc);
+    }
+
+    __device__ void point(F2* x, F2& tx) const {
+        if constexpr (BK64)
+            tx = F2(t);
+        else
+            tx = F2(tendf - remf);
+        switch (phase) {
+        case PH_F0:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = y[s];
+            break;
+        case PH_SR:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = Vg(s);
+            break;
+        case PH_TRIAL:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = y[s] + hh * Fn[s];
+            break;
+        default:  // stages and F_{n+1}: w = y_n + d (left unnormalised: it feeds products)
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = add_lazy(y[s], d1[s]);
+        }
+    }
+
+    __device__ bool consume(const BatchArgs& a, const TM& tm, const F2* x, const F2* f) {
+        switch (phase) {
+        case PH_F0:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                Fn[s] = f[s];
+                if (!warm) Vs(s, f[s]);  // first eigenvector guess
+            }
+            loop_top(a, tm);
+            break;
+        case PH_SR: sr_consume(a, tm, f); break;
+        case PH_TRIAL: trial_consume(a, tm, f); break;
+        case PH_STAGE: stage_consume(f); break;
+        default: final_consume(a, tm, x, f);
+        }
+        return done();
+    }
+
+    __device__ void loop_top(const BatchArgs& a, const TM& tm) {
+        if constexpr (BK64) {
+            if (!(t < tend)) {
+                phase = PH_DONE;
+                return;
+            }
+        } else {
+            if (!(remf > 0.0f)) {
+                phase = PH_DONE;
+                return;
+            }
+        }
+        if (n_acc + n_rej >= max_att) {
+            status |= ODE_ST_MAX_ATTEMPTS;
+            phase = PH_DONE;
+            return;
+        }
+        if constexpr (BK64) {
+            if (1.1 * h >= fabs(tend - t)) h = fabs(tend - t);
+        } else {
+            if (1.1f * h >= remf) h = remf;
+        }
+        if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
+            if (a.specrad == ODE_SPECRAD_GERSHGORIN) {  // the bound replaces the power method
+                sigma = (HT)to_double(sys.gershgorin(tm, y));
+                have_sigma = true;
+                sr_step = num_step;
+                after_sr(a);
+                return;
+            }
+            sr_begin(tm);
+            return;
+        }
+        after_sr(a);
+    }
+
+    // power method (Appendix) with the FP64 perturbation size
+    __device__ void sr_begin(const TM& tm) {
+        const float nrm1 = sqrtf(sumsq_hi(tm, [&](int s) { return y[s].hi; }));
+        const float nrm2 = sqrtf(sumsq_hi(tm, [&](int s) { return Vg(s).hi; }));
+        if (nrm1 != 0.0f && nrm2 != 0.0f) {
+            dynrm = nrm1 * kSqrtUround;
+            const float sc = dynrm / nrm2;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, y[s] + Vg(s) * sc);
+        } else if (nrm1 != 0.0f) {
+            dynrm = nrm1 * kSqrtUround;
+            const F2 sc(1.0 + (double)kSqrtUround);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, y[s] * sc);
+        } else if (nrm2 != 0.0f) {
+            dynrm = (float)kUround;
+            const float sc = dynrm / nrm2;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, Vg(s) * sc);
+        } else {
+            dynrm = (float)kUround;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, F2(dynrm));
+        }
+        sig = 0.0f;
+        sr_iter = 0;
+        phase = PH_SR;
+    }
+
+    __device__ void sr_consume(const BatchArgs& a, const TM& tm, const F2* Fv) {
+        sr_iter += 1;
+        n_sr += 1;
+        F2 df[P];
+        float acc = 0.0f;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            df[s] = Fv[s] - Fn[s];
+            if (sys.comp(tm, s) >= 0) acc = fmaf(df[s].hi, df[s].hi, acc);
+        }
+        const float d = sqrtf(tm.sum(acc));
+        const float sig_prev = sig;
+        sig = d / dynrm;
+        if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - y[s]);
+            sr_end(a, tm);
+            return;
+        }
+        if (d != 0.0f) {
+            const float sc = dynrm / d;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, y[s] + df[s] * sc);
+        } else {
+            const int ind = sr_iter % n;
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s)
+                if (opaque(sys.comp(tm, s)) == ind) Vs(s, y[s] - (Vg(s) - y[s]));
+        }
+        if (sr_iter == kSpecradItmax) {
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - y[s]);
+            status |= ODE_ST_SPECRAD_NOCONV;
+            sr_end(a, tm);
+        }
+    }
+
+    __device__ void sr_end(const BatchArgs& a, const TM& tm) {
+        sigma = (HT)1.2 * (HT)sig;
+        if (a.specrad == ODE_SPECRAD_POWER_CAPPED) {
+            const HT g = (HT)to_double(sys.gershgorin(tm, y));
+            sigma = sigma < g ? sigma : g;
+        }
+        have_sigma = true;
+        sr_step = num_step;
+        after_sr(a);
+    }
+
+    __device__ void after_sr(const BatchArgs& a) {
+        if (h < (HT)kUround) {
+            h = hmax;
+            if (sigma * h > (HT)1) h = (HT)1 / sigma;
+            h = h > hmin ? h : hmin;
+            hh = F2(h);
+            phase = PH_TRIAL;
+            return;
+        }
+        stage_begin(a);
+    }
+
+    // weighted sum of squares, FP64 (BK64) or FP32
+    template <class E>
+    __device__ HT weighted_ssq(const TM& tm, E e_of) const {
+        HT acc = (HT)0;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s)
+            if (sys.comp(tm, s) >= 0) {
+                const float e = e_of(s);
+                if constexpr (BK64)
+                    acc = fma((double)e, (double)e, acc);
+                else
+                    acc = fmaf(e, e, acc);
+            }
+        return tm.sum(acc);
+    }
+
+    __device__ void trial_consume(const BatchArgs& a, const TM& tm, const F2* f) {
+        n_rhs += 1;
+        const HT ssq = weighted_ssq(tm, [&](int s) {
+            return to_float(f[s] - Fn[s]) / (atolf + rtolf * fabsf(y[s].hi));
+        });
+        const HT est = h * sqrt(ssq / (HT)n);
+        if ((HT)kP1 * h < hmax * sqrt(est)) {
+            h = (HT)kP1 * h / sqrt(est);
+            h = h > hmin ? h : hmin;
+        } else {
+            h = hmax;
+        }
+        stage_begin(a);
+    }
+
+    __device__ void stage_begin(const BatchArgs& a) {
+        m = 1 + (int)sqrt((HT)1.54 * h * sigma + (HT)1);
+        if (m > mmax) {
+            m = mmax;
+            h = (HT)(m * m - 1) / ((HT)1.54 * sigma);
+        }
+        hh = F2(h);
+        cs.start(m, a);
+        const F2 mut1h = cs.mut1f2() * hh;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) d1[s] = mut1h * Fn[s];
+        j = 2;
+        cs.stagef2(2, chi, clo);
+        phase = PH_STAGE;
+    }
+
+    // d_j = mu_j d_{j-1} + nu_j d_{j-2} + mu~_j h f_{j-1} + gamma~_j h F_n
+    // (at j = 2, d_0 = 0 and the nu term is an exact zero: skipped).  The
+    // products stay unnormalised and the three- or four-term sum is lazy,
+    // with one renormalisation per component.
+    __device__ void stage_consume(const F2* f) {
+        const F2 mu(chi.x, clo.x), nu(chi.y, clo.y);
+        const F2 muth = F2(chi.z, clo.z) * hh, gth = F2(chi.w, clo.w) * hh;
+        const bool keep = j < m;  // d_{j-1} is the next stage's d_{j-2}
+        if (j == 2) {
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                const F2 dj = normalize(add_lazy(add_lazy(mul_lazy(mu, d1[s]), mul_lazy(muth, f[s])),
+                                                 mul_lazy(gth, Fn[s])));
+                if (keep) D2s(s, d1[s]);
+                d1[s] = dj;
+            }
+        } else {
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) {
+                const F2 dj = normalize(add_lazy(
+                    add_lazy(add_lazy(mul_lazy(mu, d1[s]), mul_lazy(nu, D2g(s))), mul_lazy(muth, f[s])),
+                    mul_lazy(gth, Fn[s])));
+                if (keep) D2s(s, d1[s]);
+                d1[s] = dj;
+            }
+        }
+        j += 1;
+        if (j <= m)
+            cs.stagef2(j, chi, clo);
+        else
+            phase = PH_FINAL;
+    }
+
+    // x = w_m (the point F_{n+1} was evaluated at), f = F_{n+1}.
+    // Eq. E:rmsE's 0.8 (y_n - y_{n+1}) + 0.4 h (F_n + F_{n+1}) is computed as
+    // 0.4 (h (F_n + F_{n+1}) - 2 d_m): the two terms cancel, so the leading
+    // product h a is formed exactly (two_prod) and the difference taken
+    // before the single rounding to FP32.
+    __device__ void final_consume(const BatchArgs& a, const TM& tm, const F2* x, const F2* f) {
+        n_rhs += m;
+        const HT ms = weighted_ssq(tm, [&](int s) {
+            const F2 sum = Fn[s] + f[s];
+            const float p = hh.hi * sum.hi;
+            float e = fmaf(hh.hi, sum.hi, -p);
+            e = fmaf(hh.hi, sum.lo, e);
+            e = fmaf(hh.lo, sum.hi, e);
+            const float D = fmaf(-2.0f, d1[s].hi, p) + fmaf(-2.0f, d1[s].lo, e);
+            return 0.4f * D / (atolf + rtolf * fmaxf(fabsf(x[s].hi), fabsf(y[s].hi)));
+        }) / (HT)n;  // err^2
+        if (isnan(ms)) {
+            n_rej += 1;
+            status |= ODE_ST_NONFINITE;
+            phase = PH_DONE;
+            return;
+        }
+        const float err = sqrtf((float)ms);
+        const float c3 = fpow(err, 1.0f / 3.0f);
+        if (ms > (HT)1) {
+            n_rej += 1;
+            h = h * (HT)(0.8f / c3);
+            rejected = true;
+            if (h < hmin) {
+                status |= ODE_ST_H_UNDERFLOW;
+                phase = PH_DONE;
+                return;
+            }
+            loop_top(a, tm);
+            return;
+        }
+        n_acc += 1;
+        rejected = false;
+        num_step += 1;
+        float fac = 10.0f;
+        if (h_old < (HT)kUround) {
+            if (0.8f < fac * c3) fac = 0.8f / c3;
+        } else {
+            const float temp1 = 0.8f * (float)h * c3_old;
+            const float temp2 = (float)h_old * (c3 * c3);
+            if (temp1 < fac * temp2) fac = temp1 / temp2;
+        }
+        c3_old = c3;
+        h_old = h;
+        if constexpr (BK64) {
+            t = t + h;
+        } else if (h >= remf * 0.999999f) {
+            remf = reml = 0.0f;  // the step covered what was left
+        } else {
+            df_sub(remf, reml, h);
+        }
+        float chk = 0.0f;  // one finiteness test of a sum per system
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            y[s] = y[s] + d1[s];
+            Fn[s] = f[s];
+            chk += (sys.comp(tm, s) >= 0) ? y[s].hi - y[s].hi : 0.0f;
+        }
+        const bool bad = !(chk == 0.0f);
+        h = h * (HT)fmaxf((float)kP1, fac);
+        h = h < hmax ? h : hmax;
+        h = h > hmin ? h : hmin;
+        if (tm.any(bad)) {
+            status |= ODE_ST_NONFINITE;
+            phase = PH_DONE;
+            return;
+        }
+        loop_top(a, tm);
+    }
+
+    __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            if (c >= 0) a.y_out[a.yidx_out(i, c)] = to_double(y[s]);
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = to_double(Vg(s));
+        }
+        if (a.carry != nullptr && tm.lane == 0) {
+            const int st = status & 0xFF;
+            const double t_end = BK64 ? t : tend - ((double)remf + (double)reml);
+            carry_scalars(a, i, (st == ODE_ST_OK || st == ODE_ST_MAX_ATTEMPTS) && have_sigma, t_end, (double)h,
+                          (double)sigma, (double)h_old, (double)c3_old * (double)c3_old * (double)c3_old, num_step,
+                          sr_step, rejected);
+        }
+        if (tm.lane == 0) {
+            if (a.n_accept) a.n_accept[i] = n_acc;
+            if (a.n_reject) a.n_reject[i] = n_rej;
+            if (a.n_rhs) a.n_rhs[i] = n_rhs + n_sr;
+            if (a.n_specrad) a.n_specrad[i] = n_sr;
+            if (a.status) a.status[i] = status;
+        }
+    }
+};
+
+}  // namespace bode

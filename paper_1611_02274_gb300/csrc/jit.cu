@@ -106,7 +106,8 @@ Nvrtc& nvrtc() {
 // for (a register budget of 65536 / (128 n) per thread).  Measured on the
 // 13-species network: the mixed forms run best at 3 (168 registers; 2 and
 // 4 are slower), the plain FP64 form at 2 (its FP64 state spills at 168
-// registers).  BATCHODE_JIT_MINBLOCKS overrides both (1 = no budget).
+// registers); the two-float forms, with their rate constants and d_{j-2} in
+// shared memory, at 3 (168 registers, ~130 B spilled).  BATCHODE_JIT_MINBLOCKS overrides both (1 = no budget).
 int jit_min_blocks(int prec) {
     const int def = prec == ODE_PREC_FP64 ? 2 : 3;
     const char* v = getenv("BATCHODE_JIT_MINBLOCKS");
@@ -133,7 +134,9 @@ std::string model_source(const RhsEntry& r) {
       << "  static constexpr int W = 1, PER = " << S << ";\n"
       << "  using Ctx = bode::NoCtx;\n"
       << "  template <class R> struct Sys {\n"
-      << "    R k[" << NR << "];\n"
+      << "    bode::ConstStore<R, " << NR << "> k;  // registers, or a shared-memory row (two-float forms)\n"
+      << "    static constexpr int CONST_SMEM = bode::ConstStore<R, " << NR << ">::SMEM_FLOATS;\n"
+      << "    __device__ void bind_consts(float* row) { k.bind(row); }\n"
       << "    int n;\n"
       << "    __device__ static double clip(double k) { return fmin(fmax(k, " << lit(net.kmin) << "), " << lit(net.kmax)
       << "); }\n"
@@ -159,15 +162,36 @@ std::string model_source(const RhsEntry& r) {
     o << "      return acc;\n"
       << "    }\n"
       << "    __device__ void rhs(const bode::Team<1>&, R, const R* y, R* f) const {\n";
-    for (int s = 0; s < S; ++s) o << "      R a" << s << " = R(0);\n";
+    // each species' accumulator starts from its first term (0 - r or 0 + r,
+    // the values an accumulator started at zero takes); the products and
+    // sums go through the lazy two-float forms (the plain operations for
+    // float and double), normalised once per species at the end
+    std::vector<int> seen(S, 0);
+    for (int s = 0; s < S; ++s) o << "      R a" << s << ";\n";
     for (int j = 0; j < NR; ++j) {
         o << "      { R r = k[" << j << "];";
-        for (int q = 0; q < net.n_reac[j]; ++q) o << " r = r * y[" << (int)net.reac[j][q] << "];";
-        for (int q = 0; q < net.n_reac[j]; ++q) o << " a" << (int)net.reac[j][q] << " = a" << (int)net.reac[j][q] << " - r;";
-        for (int q = 0; q < net.n_prod[j]; ++q) o << " a" << (int)net.prod[j][q] << " = a" << (int)net.prod[j][q] << " + r;";
+        for (int q = 0; q < net.n_reac[j]; ++q) o << " r = bode::mul_lazy(r, y[" << (int)net.reac[j][q] << "]);";
+        for (int q = 0; q < net.n_reac[j]; ++q) {
+            const int sp = net.reac[j][q];
+            if (!seen[sp])
+                o << " a" << sp << " = bode::acc_first_sub(r);";
+            else
+                o << " a" << sp << " = bode::acc_sub(a" << sp << ", r);";
+            seen[sp] = 1;
+        }
+        for (int q = 0; q < net.n_prod[j]; ++q) {
+            const int sp = net.prod[j][q];
+            if (!seen[sp])
+                o << " a" << sp << " = bode::acc_first_add(r);";
+            else
+                o << " a" << sp << " = bode::acc_add(a" << sp << ", r);";
+            seen[sp] = 1;
+        }
         o << " }\n";
     }
-    for (int s = 0; s < S; ++s) o << "      f[" << s << "] = a" << s << ";\n";
+    for (int s = 0; s < S; ++s)
+        if (!seen[s]) o << "      a" << s << " = R(0);\n";
+    for (int s = 0; s < S; ++s) o << "      f[" << s << "] = bode::acc_value(a" << s << ");\n";
     o << "    }\n";
     // Gershgorin bound, row by row: J_sl accumulates reaction by reaction
     // -dr_j/dC_l per reactant occurrence of s, +dr_j/dC_l per product
@@ -261,12 +285,15 @@ void write_file(const std::string& dir, const std::string& path, const std::vect
 struct JitKernels {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kstatic = nullptr, kqueue = nullptr;
+    int smem_floats = 0;  // dynamic shared memory per thread, as the integrator declares it
 };
 
 std::mutex g_jit_mu;
 std::map<std::string, JitKernels> g_cache;  // key: device + source hash + form
 
 std::string method_type(int method, int prec) {
+    if (prec == ODE_PREC_F2) return "bode::RkcF2<JitMass, true>";
+    if (prec == ODE_PREC_F2_LEAN) return "bode::RkcF2<JitMass, false>";
     if (method == kMethodRkck)
         return prec == ODE_PREC_FP64 ? "bode::RkckF64<JitMass>"
                : prec == ODE_PREC_MIXED ? "bode::RkckMixed<JitMass, true>" : "bode::RkckMixed<JitMass, false>";
@@ -285,7 +312,10 @@ int compile_image(const RhsEntry& r, int method, int prec, JitImage* img, std::s
     const std::string nstatic = "bode::k_static<" + meth + ", bode::NoCtx>";
     const std::string nqueue = "bode::k_queue<" + meth + ", bode::NoCtx>";
     // the two kernels are instantiated through their name expressions
-    std::string src = "#include \"rhs.cuh\"\n#include \"integrators.cuh\"\n#include \"kernels.cuh\"\n" + model;
+    // the module also exports the integrator's shared-memory need per thread,
+    // which the launcher reads back instead of restating the layout
+    std::string src = "#include \"rhs.cuh\"\n#include \"integrators.cuh\"\n#include \"kernels.cuh\"\n" + model +
+                      "extern \"C\" __device__ const int bode_jit_smem_floats = " + meth + "::SMEM_FLOATS;\n";
     std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo",
                                      prec == ODE_PREC_FP64 ? "--fmad=false" : "--fmad=true"};
     // occupancy tuning: blocks of at most 128 threads with a register budget
@@ -392,6 +422,12 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
     cudaError_t e = cudaLibraryLoadData(&out->lib, img.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kstatic, out->lib, img.low_static.c_str());
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kqueue, out->lib, img.low_queue.c_str());
+    void* dptr = nullptr;
+    size_t bytes = 0;
+    if (e == cudaSuccess) e = cudaLibraryGetGlobal(&dptr, &bytes, out->lib, "bode_jit_smem_floats");
+    if (e == cudaSuccess && bytes != sizeof(int)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMemcpy(&out->smem_floats, dptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && (out->smem_floats < 0 || out->smem_floats > 4096)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         *err = std::string("loading generated kernels: ") + cudaGetErrorString(e);
         return ODE_ERR_CUDA;
@@ -452,10 +488,18 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
     void* params[] = {&args, &ctx};
     const int block = jit_min_blocks(prec) > 1 && c.block > 128 ? 128 : c.block;
     // the generated model is one thread per system with PER = species count
-    const int smem_floats = method == kMethodRkc && prec != ODE_PREC_FP64 ? rkc_mixed_smem_floats(1, r.net.n_species) : 0;
-    const size_t smem = sizeof(float) * smem_floats * (size_t)block;
+    const size_t smem = sizeof(float) * (size_t)k.smem_floats * (size_t)block;
     const int64_t threads = a.nsys;  // one thread per system
     cudaError_t e;
+    if (smem > 48 * 1024) {  // above the default dynamic shared-memory limit: opt in
+        e = cudaFuncSetAttribute((const void*)k.kstatic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)k.kqueue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            *err = std::string("shared-memory opt-in: ") + cudaGetErrorString(e);
+            return ODE_ERR_CUDA;
+        }
+    }
     if (c.mapping == ODE_MAP_QUEUE) {
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.kqueue, block, smem);

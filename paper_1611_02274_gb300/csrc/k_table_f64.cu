@@ -20,6 +20,8 @@ __global__ void k_build_rkc_table(double* tab64, float4* tab32, int mmax) {
     e[6] = 0.0;
     e[7] = 0.0;
     tab32[base] = make_float4(0.0f, 0.0f, (float)g.mut1, 0.0f);
+    // trailing words of the two-float coefficients in the entry's last 16 bytes
+    reinterpret_cast<float4*>(e + 6)[0] = make_float4(0.0f, 0.0f, F2(g.mut1).lo, 0.0f);
     for (int j = 2; j <= m; ++j) {
         const StageCoef s = g.next();
         e = tab64 + 8 * (base + j - 1);
@@ -29,9 +31,8 @@ __global__ void k_build_rkc_table(double* tab64, float4* tab32, int mmax) {
         e[3] = s.mut;
         e[4] = s.gt;
         e[5] = s.cprev;
-        e[6] = 0.0;
-        e[7] = 0.0;
         tab32[base + j - 1] = make_float4((float)s.mu, (float)s.nu, (float)s.mut, (float)s.gt);
+        reinterpret_cast<float4*>(e + 6)[0] = make_float4(F2(s.mu).lo, F2(s.nu).lo, F2(s.mut).lo, F2(s.gt).lo);
     }
 }
 

@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "f2.cuh"
 
 namespace bode {
 
@@ -148,6 +149,25 @@ struct CoefSource {
             return StageCoef{a.x, a.y, b.x, b.y, c.x, c.y};
         }
         return recompute(j);
+    }
+    // two-float mu~_1 and stage coefficients: leading words from the FP32
+    // table, trailing words from the FP64 entry's last 16 bytes
+    __device__ F2 mut1f2() const {
+        if (e32) return F2(__ldg(e32).z, __ldg(reinterpret_cast<const float4*>(e64 + 6)).z);
+        RkcStageGen g;
+        g.start(m);
+        return F2(g.mut1);
+    }
+    __device__ void stagef2(int j, float4& hi, float4& lo) const {
+        if (e32) {
+            hi = __ldg(e32 + (j - 1));
+            lo = __ldg(reinterpret_cast<const float4*>(e64 + 8 * (j - 1) + 6));
+            return;
+        }
+        const StageCoef s = recompute(j);
+        const F2 mu(s.mu), nu(s.nu), mut(s.mut), gt(s.gt);
+        hi = make_float4(mu.hi, nu.hi, mut.hi, gt.hi);
+        lo = make_float4(mu.lo, nu.lo, mut.lo, gt.lo);
     }
     __device__ float4 stage32(int j) const {
         if (e32) return __ldg(e32 + (j - 1));

@@ -1,4 +1,4 @@
-// run_model.cuh -- instantiate the four integrator forms for one model.
+// run_model.cuh -- instantiate the integrator forms for one model.
 #pragma once
 #include "integrators.cuh"
 #include "launch.cuh"
@@ -26,6 +26,15 @@ template <class Model, class Ctx>
 cudaError_t run_model_mixed(int method, int prec, const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c) {
     if (prec == ODE_PREC_MIXED) return run_model_prec<Model, ODE_PREC_MIXED>(method, a, ctx, c);
     return run_model_prec<Model, ODE_PREC_MIXED_LEAN>(method, a, ctx, c);
+}
+
+// two-float forms: RKC only
+template <class Model, class Ctx>
+cudaError_t run_model_f2(int method, int prec, const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c, bool* ok) {
+    *ok = method == kMethodRkc;
+    if (!*ok) return cudaSuccess;
+    if (prec == ODE_PREC_F2) return launch_method<RkcF2<Model, true>>(a, ctx, c);
+    return launch_method<RkcF2<Model, false>>(a, ctx, c);
 }
 
 template <class Model, class Ctx>

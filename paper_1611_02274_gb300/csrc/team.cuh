@@ -7,7 +7,21 @@
 #pragma once
 #include <cstdint>
 
+#include "f2.cuh"
+
 namespace bode {
+
+// shuffles and maxima through overloadable names (f2.cuh adds the two-float pair)
+template <class T>
+__device__ __forceinline__ T shfl_xor(unsigned m, T v, int o, int w) { return __shfl_xor_sync(m, v, o, w); }
+template <class T>
+__device__ __forceinline__ T shfl_idx(unsigned m, T v, int s, int w) { return __shfl_sync(m, v, s, w); }
+template <class T>
+__device__ __forceinline__ T shfl_up(unsigned m, T v, int d, int w) { return __shfl_up_sync(m, v, d, w); }
+template <class T>
+__device__ __forceinline__ T shfl_down(unsigned m, T v, int d, int w) { return __shfl_down_sync(m, v, d, w); }
+template <class T>
+__device__ __forceinline__ T vmax(T a, T b) { return fmax(a, b); }
 
 template <int W_>
 struct Team {
@@ -27,7 +41,7 @@ struct Team {
     __device__ T sum(T x) const {
         if constexpr (W > 1) {
 #pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) x = x + __shfl_xor_sync(mask, x, o, W);
+            for (int o = W / 2; o > 0; o >>= 1) x = x + shfl_xor(mask, x, o, W);
         }
         return x;
     }
@@ -35,7 +49,7 @@ struct Team {
     __device__ T max(T x) const {
         if constexpr (W > 1) {
 #pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(mask, x, o, W));
+            for (int o = W / 2; o > 0; o >>= 1) x = vmax(x, shfl_xor(mask, x, o, W));
         }
         return x;
     }
@@ -45,18 +59,18 @@ struct Team {
     }
     template <class T>
     __device__ T bcast(T x, int src) const {
-        if constexpr (W > 1) return __shfl_sync(mask, x, src, W);
+        if constexpr (W > 1) return shfl_idx(mask, x, src, W);
         return x;
     }
     // value held by lane - 1 (own value on lane 0) and lane + 1 (own value on the last lane)
     template <class T>
     __device__ T from_left(T x) const {
-        if constexpr (W > 1) return __shfl_up_sync(mask, x, 1, W);
+        if constexpr (W > 1) return shfl_up(mask, x, 1, W);
         return x;
     }
     template <class T>
     __device__ T from_right(T x) const {
-        if constexpr (W > 1) return __shfl_down_sync(mask, x, 1, W);
+        if constexpr (W > 1) return shfl_down(mask, x, 1, W);
         return x;
     }
 };
