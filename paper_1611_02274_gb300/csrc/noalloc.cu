@@ -84,7 +84,20 @@ extern "C" int rkc_integrate_noalloc(int32_t handle, int64_t nsys, const double*
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
     if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_LEAN)
-        return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
+        return fail(ODE_ERR_ARG, "precision %d is not built for the allocation-free entry point", opts.precision);
+    if (opts.specrad < ODE_SPECRAD_POWER || opts.specrad > ODE_SPECRAD_POWER_CAPPED)
+        return fail(ODE_ERR_ARG, "unknown specrad mode %d", opts.specrad);
+    switch (rhs.kind) {  // every built-in family; decided before any GPU work
+    case ODE_RHS_VDP:
+    case ODE_RHS_MASSACTION:
+    case ODE_RHS_BRUSS1D:
+    case ODE_RHS_VDP_CHAIN:
+    case ODE_RHS_NBODY:
+    case ODE_RHS_KINETICS: break;
+    default: return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d is not built", rhs.kind);
+    }
+    if (rhs.kind == ODE_RHS_KINETICS && opts.specrad != ODE_SPECRAD_POWER)
+        return fail(ODE_ERR_UNSUPPORTED, "kinetics right-hand sides take the power method only (no Jacobian bound)");
     if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
     if (opts.block_size != 0 && (opts.block_size < 32 || opts.block_size > 256 || opts.block_size % 32))
         return fail(ODE_ERR_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
@@ -160,11 +173,19 @@ extern "C" int rkc_integrate_noalloc(int32_t handle, int64_t nsys, const double*
     a.rkc_tab64 = (const double*)(base + kCursorBytes);
     a.rkc_tab32 = (const float4*)(base + kCursorBytes + kTab64Bytes);
     a.rkc_tab_max = kTabMax;
+    a.specrad = opts.specrad;
 
+    // From the first queued operation on, every return waits for the
+    // stream: the copies may still read the caller's arrays, and the next
+    // call (under the lock, perhaps on another stream) reuses the scratch.
+    auto fail_after_queue = [&](int code, const char* what, cudaError_t err) {
+        cudaStreamSynchronize(stream);  // its own status is not the error to report
+        return fail(code, "%s: %s", what, cudaGetErrorString(err));
+    };
     e = cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), stream);  // the queue starts at system 0
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, y0, sizeof(double) * ny, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, params, sizeof(double) * np, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return fail(ODE_ERR_CUDA, "staging copy: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail_after_queue(ODE_ERR_CUDA, "staging copy", e);
 
     LaunchCfg cfg;
     cfg.mapping = opts.mapping == ODE_MAP_THREAD ? ODE_MAP_THREAD : ODE_MAP_QUEUE;
@@ -178,15 +199,20 @@ extern "C" int rkc_integrate_noalloc(int32_t handle, int64_t nsys, const double*
     case ODE_RHS_MASSACTION: e = launch_mass(kMethodRkc, opts.precision, rhs, a, cfg, &supported); break;
     case ODE_RHS_BRUSS1D: e = launch_bruss(kMethodRkc, opts.precision, rhs, a, cfg, &supported); break;
     case ODE_RHS_VDP_CHAIN: e = launch_chain(kMethodRkc, opts.precision, rhs, a, cfg, &supported); break;
-    default: supported = false;
+    case ODE_RHS_NBODY: e = launch_nbody(kMethodRkc, opts.precision, rhs, a, cfg, &supported); break;
+    default: e = launch_kinetics(kMethodRkc, opts.precision, rhs, a, cfg, &supported); break;
     }
-    if (!supported) return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built", rhs.kind, rhs.neq);
-    if (e != cudaSuccess) return fail(ODE_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    if (!supported) {
+        cudaStreamSynchronize(stream);
+        return fail(ODE_ERR_UNSUPPORTED, "rhs kind %d with neq %d is not built", rhs.kind, rhs.neq);
+    }
+    if (e != cudaSuccess) return fail_after_queue(ODE_ERR_CUDA, "kernel launch", e);
 
     e = cudaMemcpyAsync(y_out, d_y, sizeof(double) * ny, cudaMemcpyDeviceToHost, stream);
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         if (host_cnt[k]) e = cudaMemcpyAsync(host_cnt[k], d_cnt[k], sizeof(int32_t) * nsys, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the next call may reuse the array
-    if (e != cudaSuccess) return fail(ODE_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail_after_queue(ODE_ERR_CUDA, "result copy", e);
+    e = cudaStreamSynchronize(stream);  // the next call may reuse the array
+    if (e != cudaSuccess) return fail(ODE_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
     return ODE_OK;
 }
