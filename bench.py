@@ -38,18 +38,46 @@ from paper_1611_02274_gb300 import workloads as W  # noqa: E402
 NSYS = 1 << 20
 METRIC = "ODE systems integrated/s at rtol 1e-6, chosen vs plain FP64 form; % of FP peak"
 UNIT = "systems/s"
-# nominal ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
-# FP32 128 lanes x 2 flops per SM per clock; FP64 the part's rated 1.25 TFLOP/s
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# The chosen form must reach this final-state error against the FP64 oracle
+# (p99.9 over systems of max_i |y - y_ref| / (|y_ref| + atol)) at this
+# multiple of the plain FP64 form's throughput.
+TARGET_P999, TARGET_SPEEDUP = 1e-5, 2.0
+# nominal ALU peaks from unit counts and the maximum SM clock: FP32 128 lanes
+# x 2 flops per SM per clock (the SM count read from the device); FP64 the
+# part's rated 1.25 TFLOP/s
+SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = 1.25
+
+
+def fp32_peak_tflops(sm_count: int) -> float:
+    return sm_count * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per system of the chosen kernel, from one ncu
-# capture of k_static<RkcMixed<JitMass, false>> (step-end hold, stage points
-# without the compensation word) on 262,144 systems of this workload
-# (29.883 MB read + 0.899 MB written); traffic grows with the number of
-# systems (each state is read once, written once)
-NCU_TRAFFIC_BYTES_PER_SYSTEM = (29.88288e6 + 0.89856e6) / 262144
+
+# The precision forms of rkc_integrate (ODE_PREC_*), their kernels and the
+# arithmetic each computes in.
+FORMS = {"f2_lean": 4, "f2": 3, "mixed_lean": 2, "mixed_spec_split": 1, "plain_fp64": 0}
+FORM_KERNELS = {"f2_lean": "RkcF2<JitMass, false>", "f2": "RkcF2<JitMass, true>",
+                "mixed_lean": "RkcMixed<JitMass, false>", "mixed_spec_split": "RkcMixed<JitMass, true>",
+                "plain_fp64": "RkcF64<JitMass>"}
+FORM_DTYPES = {"f2_lean": "f32x2", "f2": "f32x2+f64", "mixed_lean": "f32", "mixed_spec_split": "f32+f64",
+               "plain_fp64": "f64"}
+FORM_TEXT = {
+    "f2_lean": "two-float (FP32 pair, ~48-bit) state, stages, evaluation points and RHS; FP32 step size, spectral "
+               "radius and error norm; remaining interval as an FP32 pair; FP64-built coefficients as pairs",
+    "f2": "two-float state, stages, evaluation points and RHS; FP64 time, step size, spectral radius and error-norm "
+          "accumulation; FP64-built coefficients as pairs",
+    "mixed_lean": "FP32 RHS, stages, step size, spectral radius and error norms; Kahan-compensated FP32 state; "
+                  "remaining interval as an FP32 pair",
+    "mixed_spec_split": "FP32 RHS and stages, Kahan-compensated FP32 state; FP64 time, step size and error-norm "
+                        "accumulation (the split as the target specifies it)",
+    "plain_fp64": "every operation in FP64 (the paper's form; bitwise equal to the oracle)"}
+# DRAM bytes (read + write) per system of each form's generated kernel, from
+# one ncu capture of k_static on 262,144 systems of this workload; traffic
+# grows with the number of systems (each state is read once, written once).
+# mixed_lean: 29.883 MB read + 0.899 MB written.
+NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144}
+NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
+                      "(null when another kernel ran or no capture of this kernel exists)")
 
 
 def dist_env():
@@ -79,21 +107,39 @@ def aggregate_rate(units_per_rank: int, world: int, ms: float) -> float:
 # ------------------------------------------------------------ flop accounting
 
 def rhs_flops(w: W.Workload) -> int:
-    """Algorithmic flops of one mass-action RHS: per reaction |R| products
-    (rate constant times concentrations) and |R| + |P| accumulations."""
-    n = w.network
-    return int(np.sum(2 * n.n_reac + n.n_prod))
+    """Algorithmic flops of one right-hand side (an FMA counts 2).
+    Mass-action: per reaction (|R| - 1) products of concentrations, one
+    product with k_j and 2 (|R| + |P|) for the stoichiometric scatter
+    updates, i.e. 3 |R| + 2 |P|.  Van der Pol: 5.  Brusselator: 17 per grid
+    point."""
+    if w.kind == W.RHS_MASSACTION:
+        n = w.network
+        return int(np.sum(3 * n.n_reac + 2 * n.n_prod))
+    if w.kind == W.RHS_VDP:
+        return 5
+    if w.kind == W.RHS_BRUSS1D:
+        return 17 * (w.neq // 2)
+    raise ValueError(f"no flop model for kind {w.kind}")
 
 
 def rkc_flops(w: W.Workload, n_acc, n_rej, n_rhs, n_sr) -> float:
     """Algorithmic flops of RKC runs from the per-system counters: every RHS
-    evaluation, plus per attempt N (2 + 9 (m - 1) + 11) vector flops, per
-    power iteration 6 N and 8 N for the initial step (FMA = 2 flops)."""
+    evaluation, plus per m-stage attempt N (2 + 9 (m - 1) + 11) vector flops
+    and 15 (m - 1) for the stage coefficients, per power iteration 6 N and
+    5 N for the initial step."""
     N = w.neq
     A = n_acc.astype(np.float64) + n_rej
     sum_m = n_rhs.astype(np.float64) - n_sr - 2.0      # minus F(t0) and the initial trial step
-    vec = N * (13.0 * A + 9.0 * (sum_m - A)) + 6.0 * N * n_sr + 8.0 * N
+    vec = N * (13.0 * A + 9.0 * (sum_m - A)) + 15.0 * (sum_m - A) + 6.0 * N * n_sr + 5.0 * N
     return float(np.sum(n_rhs.astype(np.float64) * rhs_flops(w) + vec))
+
+
+def rkck_flops(w: W.Workload, n_acc, n_rej) -> float:
+    """Algorithmic flops of RKCK runs: per attempt six RHS evaluations and
+    60 N vector flops (stage sums, the fifth-order solution, the error
+    vector, its scaling and maximum)."""
+    A = n_acc.astype(np.float64) + n_rej
+    return float(np.sum(A * (6.0 * rhs_flops(w) + 60.0 * w.neq)))
 
 
 # ------------------------------------------------------------------- clocks
@@ -186,8 +232,8 @@ def run_ours(args):
         B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
                     precision=prec, mapping=MAPPING, block_size=args.block, stream=stream.cuda_stream)
 
-    CHOSEN = B.ODE_PREC_MIXED_LEAN
-    for prec in (CHOSEN, B.ODE_PREC_MIXED, B.ODE_PREC_FP64):
+    CHOSEN = FORMS[args.chosen]
+    for prec in FORMS.values():
         B.prepare(h, "rkc", prec)       # generated network kernels compiled before any timing
 
     def timed(prec, steps, warmup):
@@ -212,6 +258,12 @@ def run_ours(args):
         total = max_over_ranks(total, world, dev)
         return total / steps, ms
 
+    def counted(prec):
+        step(prec, cnt)
+        torch.cuda.synchronize()
+        c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+        return c, yout.cpu().numpy()
+
     gpu_id = None
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -222,33 +274,24 @@ def run_ours(args):
     with ClockSampler(gpu_id) as clk:
         ms_chosen, per_step = timed(CHOSEN, args.steps, args.warmup)
     clocks = clk.summary()
-    # counters of one chosen-form pass (for the flop count) and its output
-    step(CHOSEN, cnt)
-    torch.cuda.synchronize()
-    c_mixed = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
-    y_mixed = yout.cpu().numpy()
-    flops_mixed = rkc_flops(w, c_mixed["n_accept"], c_mixed["n_reject"], c_mixed["n_rhs"], c_mixed["n_specrad_iter"])
+    runs = {}
+    c_ch, y_ch = counted(CHOSEN)
+    runs[args.chosen] = {"ms": ms_chosen, "c": c_ch, "y": y_ch}
+    if args.plain_steps > 0:
+        # every other form on the same inputs
+        for name, prec in FORMS.items():
+            if name == args.chosen:
+                continue
+            ms, _ = timed(prec, args.plain_steps, 1)
+            c, y = counted(prec)
+            runs[name] = {"ms": ms, "c": c, "y": y}
 
     # the kernel the chosen form ran (ODE_MAP_AUTO's choice unless --mapping fixes it)
     amap, ablock, _ = B.mapping_info(h, "rkc", CHOSEN, block_size=args.block)
     if MAPPING != B.ODE_MAP_AUTO:
         amap, ablock = MAPPING, (args.block or 128)
     kname = ("k_static" if amap == B.ODE_MAP_THREAD else "k_queue") + \
-        f"<RkcMixed<JitMass, false>> (generated network code, lean split; block {ablock})"
-
-    ms_mixed64 = ms_plain = None
-    c_plain = y_plain = None
-    if args.plain_steps > 0:
-        # the mixed form with the split as specified (FP64 time, step, norm accumulation)
-        ms_mixed64, _ = timed(B.ODE_PREC_MIXED, args.plain_steps, 1)
-
-        # plain FP64 form on the same inputs
-        ms_plain, _ = timed(B.ODE_PREC_FP64, args.plain_steps, 1)
-        step(B.ODE_PREC_FP64, cnt)
-        torch.cuda.synchronize()
-        c_plain = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
-        y_plain = yout.cpu().numpy()
-        flops_plain = rkc_flops(w, c_plain["n_accept"], c_plain["n_reject"], c_plain["n_rhs"], c_plain["n_specrad_iter"])
+        f"<{FORM_KERNELS[args.chosen]}> (generated network code; block {ablock})"
 
     # end to end through the C ABI with pinned host buffers
     hy0 = torch.from_numpy(w.y0).pin_memory()
@@ -267,53 +310,92 @@ def run_ours(args):
     e2e_step = max_over_ranks(e2e_step, world, dev)
 
     value = aggregate_rate(w.nsys, world, ms_chosen)
-    achieved = flops_mixed / (ms_chosen * 1e-3) / 1e12
-    achieved_plain = flops_plain / (ms_plain * 1e-3) / 1e12 if ms_plain else None
+    flops = {k: rkc_flops(w, r["c"]["n_accept"], r["c"]["n_reject"], r["c"]["n_rhs"], r["c"]["n_specrad_iter"])
+             for k, r in runs.items()}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak32_nominal = fp32_peak_tflops(sm_count)
 
     out = {}
     if rank == 0:
         peak32, _ = B.fma_peak(False, 1 << 20)
         peak64, _ = B.fma_peak(True, 1 << 14)
+        peak32, peak64 = peak32 / 1e3, peak64 / 1e3
+        achieved = flops[args.chosen] / (ms_chosen * 1e-3) / 1e12
+        two_float = args.chosen.startswith("f2")
+        ms_plain = runs["plain_fp64"]["ms"] if "plain_fp64" in runs else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_chosen, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPES[args.chosen],
             "data": "synthetic (seeded mass-action network and states; no dataset)",
             "config": {"workload": "massaction-13sp-27rx RKC, 1,048,576 systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
-                       "nsys_per_gpu": w.nsys, "method": "rkc",
-                       "form": "chosen: FP32 RHS, stages, step size, spectral radius and error norms, Kahan "
-                               "state, remaining interval as an FP32 pair, FP64 coefficient tables, generated "
-                               "network code, mapping chosen by ODE_MAP_AUTO",
+                       "nsys_per_gpu": w.nsys, "method": "rkc", "form": FORM_TEXT[args.chosen],
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
-            "rhs_evals_per_s": float(np.sum(c_mixed["n_rhs"])) * world / (ms_chosen * 1e-3),
-            "plain_fp64": None if not ms_plain else {
-                "value": aggregate_rate(w.nsys, world, ms_plain), "ms_per_step": ms_plain,
-                "rhs_evals_per_s": float(np.sum(c_plain["n_rhs"])) * world / (ms_plain * 1e-3),
-                "achieved_tflops": achieved_plain, "frac_fp64_peak": achieved_plain / FP64_PEAK_TFLOPS,
-                "frac_fp64_measured": achieved_plain / (peak64 / 1e3)},
-            "speedup_chosen_vs_plain": ms_plain / ms_chosen if ms_plain else None,
-            "mixed_spec_split": None if not ms_mixed64 else {
-                "value": aggregate_rate(w.nsys, world, ms_mixed64), "ms_per_step": ms_mixed64,
-                "form": "FP32 stages + Kahan state; FP64 time, step size, error-norm accumulation"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": NCU_TRAFFIC_BYTES_PER_SYSTEM * w.nsys if amap == B.ODE_MAP_THREAD else None,
-                         "traffic_source": "ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by "
-                                           "the system count (null when another kernel ran)",
+            "rhs_evals_per_s": float(np.sum(runs[args.chosen]["c"]["n_rhs"])) * world / (ms_chosen * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32_nominal, "unit": "TFLOP/s",
+                         "frac": achieved / peak32_nominal,
+                         "traffic": (NCU_TRAFFIC_BYTES_PER_SYSTEM[args.chosen] * w.nsys
+                                     if amap == B.ODE_MAP_THREAD and args.chosen in NCU_TRAFFIC_BYTES_PER_SYSTEM else None),
+                         "traffic_source": NCU_TRAFFIC_SOURCE,
                          "kernel": kname,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                         "peak_measured_fma": peak32 / 1e3, "frac_of_measured": achieved / (peak32 / 1e3),
-                         "flops_per_launch": flops_mixed},
-            "fp64_fma_measured_tflops": peak64 / 1e3,
+                         "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (FP32 pipe, the one "
+                                        "the kernel runs on)",
+                         "peak_measured_fma": peak32, "frac_of_measured": achieved / peak32,
+                         "flops_per_launch": flops[args.chosen],
+                         "flops_model": "method flops (3|R| + 2|P| per mass-action evaluation, N (13 + 9 (m - 1)) + "
+                                        "15 (m - 1) per attempt, 6 N per power iteration, 5 N for the start)"},
+            "fp64_fma_measured_tflops": peak64, "fp32_fma_measured_tflops": peak32,
             "e2e": {"value": aggregate_rate(w.nsys, world, e2e_step), "unit": UNIT,
                     "h2d_bytes_per_step": int(w.y0.nbytes + w.params.nbytes), "d2h_bytes_per_step": int(w.y0.nbytes)},
             "gpu_launches": args.steps,
             "clocks": clocks,
-            "status_ok_frac": float(np.mean((c_mixed["status"] & 0xFF) == 0)),
+            "status_ok_frac": float(np.mean((runs[args.chosen]["c"]["status"] & 0xFF) == 0)),
         }
-        if not args.no_cpu and c_plain is not None:
-            out["cpu_baseline"], acc = cpu_baseline(w, args, y_mixed, y_plain, c_plain)
+        if two_float:
+            # the two-float form computes the FP64 method's arithmetic to ~48 bits on the FP32 pipe:
+            # its method flops against the FP64 pipe's peak (above 1: beyond any FP64 kernel)
+            out["roofline"]["method_tflops_vs_fp64_peak"] = {
+                "achieved": achieved, "peak_rated": FP64_PEAK_TFLOPS, "peak_measured_fma": peak64,
+                "frac_rated": achieved / FP64_PEAK_TFLOPS, "frac_measured": achieved / peak64}
+        forms = {}
+        for name, r in runs.items():
+            fl = flops[name]
+            ach = fl / (r["ms"] * 1e-3) / 1e12
+            peak_kind = "fp64" if name == "plain_fp64" else "fp32"
+            forms[name] = {"value": aggregate_rate(w.nsys, world, r["ms"]), "ms_per_step": r["ms"],
+                           "rhs_evals_per_s": float(np.sum(r["c"]["n_rhs"])) * world / (r["ms"] * 1e-3),
+                           "achieved_tflops": ach,
+                           "frac_peak": ach / (FP64_PEAK_TFLOPS if peak_kind == "fp64" else peak32_nominal),
+                           "frac_peak_measured": ach / (peak64 if peak_kind == "fp64" else peak32),
+                           "peak": peak_kind, "form": FORM_TEXT[name],
+                           "speedup_vs_plain": (ms_plain / r["ms"]) if ms_plain else None,
+                           "status_ok_frac": float(np.mean((r["c"]["status"] & 0xFF) == 0))}
+        out["forms"] = forms
+        if ms_plain:
+            out["plain_fp64"] = forms["plain_fp64"]
+            out["speedup_chosen_vs_plain"] = ms_plain / ms_chosen
+        if not args.no_cpu and "plain_fp64" in runs:
+            out["cpu_baseline"], acc = cpu_baseline(w, args, runs)
             out["accuracy_vs_oracle"] = acc
+            for name in forms:
+                forms[name]["err_vs_fp64_oracle_p999"] = acc["forms"][name]["p999_rel_err"]
+                forms[name]["err_vs_fp64_oracle_max"] = acc["forms"][name]["max_rel_err"]
+                forms[name]["meets_target"] = bool(
+                    acc["forms"][name]["p999_rel_err"] <= TARGET_P999 and
+                    (name == "plain_fp64" or (forms[name]["speedup_vs_plain"] or 0.0) >= TARGET_SPEEDUP))
+            qual = [n for n in forms if n != "plain_fp64" and forms[n]["meets_target"]]
+            out["target"] = {"bar": f"p99.9 error <= {TARGET_P999:g} vs the FP64 oracle at >= {TARGET_SPEEDUP:g}x "
+                                    "the plain FP64 form's systems/s",
+                             "chosen": args.chosen, "chosen_meets": forms[args.chosen]["meets_target"],
+                             "fastest_qualifying": max(qual, key=lambda n: forms[n]["value"]) if qual else None}
+    if args.c0_steps > 0:
+        c0 = c0_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["c0_vdp_rkck"] = c0
+    if args.c1_steps > 0:
+        c1 = c1_leg(args, B, torch, dev, stream, rank, world, barrier)
+        if rank == 0:
+            out["c1_bruss_rkc"] = c1
     if args.proposal_nsys > 0:
         prop = proposal_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
@@ -375,7 +457,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     y0 = torch.from_numpy(w.y0).to(dev)
     p = torch.from_numpy(w.params).to(dev)
     yout = torch.empty_like(y0)
-    CH = B.ODE_PREC_MIXED_LEAN
+    CH = FORMS[args.chosen]
     B.prepare(h, "rkc", CH)
     true_cost = None
 
@@ -584,7 +666,7 @@ def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
     p = torch.from_numpy(w.params).to(dev)
     y = torch.empty_like(y0)
     cnt = B.counters_like(w.nsys, dev)
-    CH = B.ODE_PREC_MIXED_LEAN
+    CH = FORMS[args.chosen]
     B.prepare(h, "rkc", CH)
     res = {}
     ref = None
@@ -637,7 +719,7 @@ def split_leg(args, B, torch, dev, stream, rank, world, barrier):
     y = torch.empty_like(y0)
     carry = B.carry_like(w.neq, w.nsys, dev)
     cnt = B.counters_like(w.nsys, dev)
-    CH = B.ODE_PREC_MIXED_LEAN
+    CH = FORMS[args.chosen]
     B.prepare(h, "rkc", CH)
     edges = np.linspace(w.t0, w.tend, args.split_steps + 1)
 
@@ -742,52 +824,222 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
                      "buckets": [{k: d[k] for k in ("family", "method", "size_class", "systems", "lanes",
                                                      "points_per_lane", "block", "mapping")} for d in plan.info()]}
         plan.destroy()
+        if name == "autotuned":
+            torch.cuda.synchronize()
+            y_auto = y.cpu().numpy()
     B.release(hb)
     B.release(hc)
     res["speedup_autotuned_vs_fixed"] = res["fixed_thread_per_system"]["ms_per_step"] / res["autotuned"]["ms_per_step"]
     res["config"] = {"nsys_per_gpu": b.nsys, "unknowns_total": int(b.offset[-1]), "precision": "mixed lean",
                      "graph": "one CUDA graph launch per step (all buckets on parallel branches)"}
+    if rank == 0 and not args.no_cpu:
+        # the error against the FP64 oracle on a sample (half grids, half chains)
+        import oracle as O
+        rng = np.random.default_rng(7)
+        idx = np.sort(rng.choice(b.nsys, args.mixed_sample, replace=False))
+        sub = W.mixed_subset(b, idx)
+        t0 = time.perf_counter()
+        ref = O.integrate_mixed(sub)
+        cpu_s = time.perf_counter() - t0
+        acc = {"sample": int(idx.size), "cpu_oracle_systems_per_s": idx.size / cpu_s, "cores": os.cpu_count()}
+        for fam, kind in (("brusselator_rkc", W.RHS_BRUSS1D), ("vdp_chain_rkck", W.RHS_VDP_CHAIN)):
+            e = []
+            for k, i in enumerate(idx):
+                if b.kind[i] != kind:
+                    continue
+                yg = y_auto[b.offset[i]:b.offset[i] + b.neq[i]]
+                yr = ref.y[sub.offset[k]:sub.offset[k] + sub.neq[k]]
+                e.append(float(np.max(np.abs(yg - yr) / (np.abs(yr) + b.atol[i]))))
+            e = np.array(e)
+            acc[fam] = {"systems": int(e.size), "median_rel_err": float(np.median(e)),
+                        "p999_rel_err": float(np.quantile(e, 0.999)), "max_rel_err": float(e.max())}
+        res["accuracy_vs_oracle"] = acc
     return res
 
 
-def cpu_baseline(w, args, y_mixed, y_plain, c_plain):
-    """Time the oracle (as it stands) on a bounded sample of the same batch,
-    and compare both GPU forms with it on that sample."""
+def timed_calls(torch, stream, fn, steps, warmup, barrier):
+    """Mean milliseconds of fn() over `steps` calls after `warmup` untimed
+    ones (CUDA events on the launching stream)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def c0_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """Configuration c0: van der Pol systems by the plain FP64 RKCK (the
+    paper's RKCK path; mu log-uniform in [0.1, 10], t in [0, 20], rtol 1e-6,
+    atol 1e-9).  The configured 4096 systems fill 32 blocks of 128 threads
+    (a fifth of the SMs), so a 1,048,576-system batch of the same
+    distribution is timed too.  Step counts and final states against the
+    oracle (all 4096 systems; a sample of the large batch), the oracle timed
+    on the host cores on the same systems."""
     import oracle as O
-    cores = os.cpu_count() or 1
-    rng = np.random.default_rng(123)
-    probe = np.sort(rng.choice(w.nsys, 2048, replace=False))
+    res = {}
+    for nsys in (4096, args.c0_big):
+        w = W.vdp(nsys, seed=rank)
+        h = B.register_workload(w)
+        y0 = torch.from_numpy(w.y0).to(dev)
+        p = torch.from_numpy(w.params).to(dev)
+        y = torch.empty_like(y0)
+        cnt = B.counters_like(w.nsys, dev)
+
+        def call(counters=None):
+            B.integrate("rkck", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters,
+                        precision=B.ODE_PREC_FP64, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
+
+        ms = timed_calls(torch, stream, call, args.c0_steps, args.warmup, barrier)
+        ms = max_over_ranks(ms, world, dev)
+        call(cnt)
+        torch.cuda.synchronize()
+        c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "status")}
+        yg = y.cpu().numpy()
+        mapping = B.mapping_info(h, "rkck", B.ODE_PREC_FP64)
+        B.release(h)
+        fl = rkck_flops(w, c["n_accept"], c["n_reject"])
+        r = {"systems_per_s": w.nsys * world / (ms * 1e-3), "ms_per_step": ms,
+             "rhs_evals_per_s": float(np.sum(c["n_rhs"])) * world / (ms * 1e-3),
+             "mean_attempts": float(np.mean(c["n_accept"] + c["n_reject"])),
+             "achieved_tflops_fp64": fl / (ms * 1e-3) / 1e12,
+             "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+             "mapping_block_tuned": list(mapping)}
+        if rank == 0 and not args.no_cpu:
+            if nsys <= 4096:
+                idx = np.arange(nsys)
+                t0 = time.perf_counter()
+                ref = O.integrate_workload(w)
+                rate = nsys / (time.perf_counter() - t0)
+            else:
+                idx, ref, rate = oracle_sample(w, args, seed=5)
+            same = (c["n_accept"][idx] == ref.n_accept) & (c["n_reject"][idx] == ref.n_reject)
+            e = (np.abs(yg[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+            r["parity"] = {"systems": int(idx.size), "same_counts_frac": float(same.mean()),
+                           "max_rel_err_same_counts": float(e[same].max()) if same.any() else None,
+                           "max_rel_err": float(e.max()),
+                           "status_equal": bool(np.array_equal(c["status"][idx], ref.status))}
+            r["cpu_oracle"] = {"systems_per_s": rate, "cores": os.cpu_count(), "sample": int(idx.size)}
+        res[f"nsys_{nsys}"] = r
+    res["config"] = {"method": "rkck", "precision": "plain FP64", "rtol": 1e-6, "atol": 1e-9, "interval": [0.0, 20.0],
+                     "flops_model": "6 evaluations x 5 flops + 60 N per attempt"}
+    return res
+
+
+def c1_leg(args, B, torch, dev, stream, rank, world, barrier):
+    """Configuration c1: 1D Brusselator grids of 32 points (64 unknowns,
+    one warp per system), RKC, rtol 1e-5, atol 1e-8, t in [0, 10], 65,536
+    systems: the plain FP64 form against FP32 stages with FP64 bookkeeping
+    (the configured comparison), with the lean and two-float forms beside
+    them; error against the oracle on a sample, the oracle timed on it."""
+    w = W.bruss(args.c1_nsys, n=32, seed=rank)
+    h = B.register_workload(w)
+    y0 = torch.from_numpy(w.y0).to(dev)
+    p = torch.from_numpy(w.params).to(dev)
+    y = torch.empty_like(y0)
+    cnt = B.counters_like(w.nsys, dev)
+    runs = {}
+    for name in ("plain_fp64", "mixed_spec_split", "mixed_lean", "f2", "f2_lean"):
+        prec = FORMS[name]
+
+        def call(counters=None):
+            B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters,
+                        precision=prec, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
+
+        ms = timed_calls(torch, stream, call, args.c1_steps, 1, barrier)
+        ms = max_over_ranks(ms, world, dev)
+        call(cnt)
+        torch.cuda.synchronize()
+        c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+        runs[name] = {"ms": ms, "c": c, "y": y.cpu().numpy()}
+    B.release(h)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    res = {}
+    for name, r in runs.items():
+        fl = rkc_flops(w, r["c"]["n_accept"], r["c"]["n_reject"], r["c"]["n_rhs"], r["c"]["n_specrad_iter"])
+        ach = fl / (r["ms"] * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS if name == "plain_fp64" else fp32_peak_tflops(sm_count)
+        res[name] = {"systems_per_s": w.nsys * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
+                     "rhs_evals_per_s": float(np.sum(r["c"]["n_rhs"])) * world / (r["ms"] * 1e-3),
+                     "mean_rhs": float(np.mean(r["c"]["n_rhs"])), "achieved_tflops": ach,
+                     "frac_peak": ach / peak, "peak": "fp64" if name == "plain_fp64" else "fp32",
+                     "speedup_vs_plain": runs["plain_fp64"]["ms"] / r["ms"],
+                     "status_ok_frac": float(np.mean((r["c"]["status"] & 0xFF) == 0))}
+    if rank == 0 and not args.no_cpu:
+        idx, ref, rate = oracle_sample(w, args, seed=11, min_n=1024)
+        for name, r in runs.items():
+            st = err_stats(r["y"][:, idx], ref.y, w.atol, w.rtol)
+            same = (r["c"]["n_accept"][idx] == ref.n_accept) & (r["c"]["n_reject"][idx] == ref.n_reject)
+            st["same_counts_frac"] = float(same.mean())
+            res[name]["err_vs_fp64_oracle"] = st
+        res["cpu_oracle"] = {"systems_per_s": rate, "cores": os.cpu_count(), "sample": int(idx.size)}
+    res["config"] = {"nsys_per_gpu": w.nsys, "grid_points": 32, "neq": w.neq, "rtol": w.rtol, "atol": w.atol,
+                     "interval": [w.t0, w.tend], "mapping": "one warp per system (ODE_MAP_AUTO block)",
+                     "flops_model": "17 per grid point per evaluation; RKC vector terms as the main leg"}
+    return res
+
+
+def err_stats(y, ref_y, atol, rtol):
+    """Per-system final-state error against the oracle: max_i |y - y_ref| /
+    (|y_ref| + atol), summarised over the systems, and in tolerance units."""
+    e = (np.abs(y - ref_y) / (np.abs(ref_y) + atol)).max(axis=0)
+    tu = (np.abs(y - ref_y) / (atol + rtol * np.abs(ref_y))).max(axis=0)
+    return {"median_rel_err": float(np.median(e)), "p999_rel_err": float(np.quantile(e, 0.999)),
+            "max_rel_err": float(e.max()), "p999_err_in_tolerances": float(np.quantile(tu, 0.999))}
+
+
+def oracle_sample(w, args, seed=123, min_n=4096):
+    """Time the oracle (as it stands, all host cores) on a uniformly drawn
+    sample of the batch sized for about args.cpu_seconds."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    probe = np.sort(rng.choice(w.nsys, min(2048, w.nsys), replace=False))
     t0 = time.perf_counter()
     O.integrate_workload(W.subset(w, probe))
-    rate = 2048 / (time.perf_counter() - t0)
-    n = int(min(w.nsys, max(4096, rate * args.cpu_seconds)))
+    rate = probe.size / (time.perf_counter() - t0)
+    n = int(min(w.nsys, max(min_n, rate * args.cpu_seconds)))
     idx = np.sort(rng.choice(w.nsys, n, replace=False))
-    sub = W.subset(w, idx)
     t0 = time.perf_counter()
-    ref = O.integrate_workload(sub)
-    dt = time.perf_counter() - t0
-    e_m = (np.abs(y_mixed[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
-    e_p = (np.abs(y_plain[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
-    same = (c_plain["n_accept"][idx] == ref.n_accept) & (c_plain["n_reject"][idx] == ref.n_reject)
-    tol_units = (np.abs(y_mixed[:, idx] - ref.y) / (w.atol + w.rtol * np.abs(ref.y))).max(axis=0)
-    base = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    ref = O.integrate_workload(W.subset(w, idx))
+    return idx, ref, n / (time.perf_counter() - t0)
+
+
+def cpu_baseline(w, args, runs):
+    """The oracle timed on a bounded sample of the same batch, and every GPU
+    form compared with it on that sample."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    idx, ref, rate = oracle_sample(w, args)
+    n = idx.size
+    base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} of {w.nsys} systems drawn uniformly (seed 123), full interval, all host cores"}
-    acc = {"sample": n, "chosen_max_rel_err": float(e_m.max()), "chosen_p999_rel_err": float(np.quantile(e_m, 0.999)),
-           "chosen_median_rel_err": float(np.median(e_m)),
-           "chosen_max_err_in_tolerances": float(tol_units.max()),
-           "chosen_p999_err_in_tolerances": float(np.quantile(tol_units, 0.999)),
-           "plain_max_rel_err_same_counts": float(e_p[same].max()) if same.any() else None,
-           "plain_same_counts_frac": float(same.mean())}
-    # both forms against an independent tight reference (RKCK, rtol 1e-12) on
-    # a small sample: the FP32 stages' error next to the method's own
+    acc = {"sample": n, "forms": {}}
+    for name, r in runs.items():
+        st = err_stats(r["y"][:, idx], ref.y, w.atol, w.rtol)
+        same = (r["c"]["n_accept"][idx] == ref.n_accept) & (r["c"]["n_reject"][idx] == ref.n_reject)
+        st["same_counts_frac"] = float(same.mean())
+        if name == "plain_fp64":
+            e = (np.abs(r["y"][:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+            st["max_rel_err_same_counts"] = float(e[same].max()) if same.any() else None
+        acc["forms"][name] = st
+    # every form against an independent tight reference (RKCK, rtol 1e-12)
+    # on a small sample: the forms' rounding next to the method's own error
     k = min(1024, n)
     sub_k = W.subset(w, idx[:k])
     tight = O.integrate(O.model_for(sub_k), 0, sub_k.y0, sub_k.params, sub_k.t0, sub_k.tend, 1e-12, 1e-18)
-    e_ct = (np.abs(y_mixed[:, idx[:k]] - tight.y) / (np.abs(tight.y) + w.atol)).max(axis=0)
+    vt = {"sample": k, "reference": "oracle RKCK rtol 1e-12 atol 1e-18"}
     e_ot = (np.abs(ref.y[:, :k] - tight.y) / (np.abs(tight.y) + w.atol)).max(axis=0)
-    acc["vs_tight_reference"] = {"sample": k, "reference": "oracle RKCK rtol 1e-12 atol 1e-18",
-                                 "chosen_max": float(e_ct.max()), "chosen_median": float(np.median(e_ct)),
-                                 "fp64_oracle_max": float(e_ot.max()), "fp64_oracle_median": float(np.median(e_ot))}
+    vt["fp64_oracle"] = {"max": float(e_ot.max()), "median": float(np.median(e_ot))}
+    for name, r in runs.items():
+        e = (np.abs(r["y"][:, idx[:k]] - tight.y) / (np.abs(tight.y) + w.atol)).max(axis=0)
+        vt[name] = {"max": float(e.max()), "median": float(np.median(e))}
+    acc["vs_tight_reference"] = vt
     return base, acc
 
 
@@ -831,7 +1083,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nsys", type=int, default=NSYS)
-    ap.add_argument("--plain-steps", type=int, default=3, help="0 skips the plain FP64 and specified-split legs")
+    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the forms other than the chosen one "
+                                                               "(0 skips them)")
+    ap.add_argument("--chosen", choices=sorted(FORMS), default="f2_lean",
+                    help="the headline form (the fastest one that meets the accuracy target, as measured)")
     ap.add_argument("--mapping", choices=["auto", "thread", "queue"], default="auto",
                     help="mapping of the main leg (fix it under a profiler, whose overhead distorts the "
                          "timing runs of auto)")
@@ -845,6 +1100,11 @@ def main():
     ap.add_argument("--proposal-epochs", type=int, default=24)
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)
+    ap.add_argument("--mixed-sample", type=int, default=1024, help="ragged systems compared with the oracle")
+    ap.add_argument("--c0-steps", type=int, default=3, help="timed steps of the van der Pol RKCK leg (0 skips)")
+    ap.add_argument("--c0-big", type=int, default=1 << 20, help="systems of the weak-scaled van der Pol batch")
+    ap.add_argument("--c1-steps", type=int, default=2, help="timed steps per form of the Brusselator leg (0 skips)")
+    ap.add_argument("--c1-nsys", type=int, default=65536)
     ap.add_argument("--specrad-steps", type=int, default=2, help="timed steps per spectral-radius mode (0 skips)")
     ap.add_argument("--pleiades-nsys", type=int, default=262144, help="n-body RKCK leg batch (0 skips)")
     ap.add_argument("--kinetics-nsys", type=int, default=16384, help="kinetics leg batch (0 skips)")

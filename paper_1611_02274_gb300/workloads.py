@@ -340,3 +340,16 @@ def subset(w: Workload, idx: np.ndarray) -> Workload:
     return Workload(w.name, w.kind, w.method, int(idx.size), w.neq,
                     np.ascontiguousarray(w.y0[:, idx]), np.ascontiguousarray(w.params[:, idx]),
                     w.t0, w.tend, w.rtol, w.atol, w.network, w.bruss_n, dict(w.aux))
+
+
+def mixed_subset(b: MixedBatch, idx: np.ndarray) -> MixedBatch:
+    """The ragged batch restricted to systems ``idx`` (states repacked)."""
+    idx = np.asarray(idx)
+    neq = b.neq[idx].astype(np.int32)
+    offset = np.zeros(idx.size + 1, dtype=np.int64)
+    np.cumsum(neq, out=offset[1:])
+    y0 = np.concatenate([b.y0[b.offset[i]:b.offset[i] + b.neq[i]] for i in idx]) if idx.size else np.empty(0)
+    return MixedBatch(int(idx.size), b.kind[idx].copy(), b.n[idx].copy(), neq, offset, y0, b.param[idx].copy(),
+                      b.method[idx].copy(), b.t0[idx].copy(), b.tend[idx].copy(), b.rtol[idx].copy(),
+                      b.atol[idx].copy(), b.coupling)
+

@@ -24,10 +24,11 @@ def tiny_network():
 def test_rhs_flops_counts_the_mass_action_law():
     w = W.Workload("tiny", W.RHS_MASSACTION, W.METHOD_RKC, 1, 3, np.ones((3, 1)), np.ones((1, 1)),
                    0.0, 1.0, 1e-6, 1e-12, network=tiny_network())
-    # k C_A, then -r to A, +r to B            : 1 + 2 = 3
-    # k C_A C_B, then -r to A and B, +r to C  : 2 + 3 = 5
-    # k C_A C_A, then -r twice to A, +r to B, C: 2 + 4 = 6
-    assert bench.rhs_flops(w) == 3 + 5 + 6
+    # k C_A, then -r to A, +r to B                  : 1 + 2 (1 + 1) = 5
+    # k C_A C_B, then -r to A and B, +r to C        : 2 + 2 (2 + 1) = 8
+    # k C_A C_A, then -r twice to A, +r to B and C  : 2 + 2 (2 + 2) = 10
+    # (each scatter update a multiply-add with the stoichiometric sign: 2 flops)
+    assert bench.rhs_flops(w) == 5 + 8 + 10
 
 
 def test_rkc_flops_is_linear_in_the_counters_and_prices_each_evaluation():
@@ -42,6 +43,23 @@ def test_rkc_flops_is_linear_in_the_counters_and_prices_each_evaluation():
     assert total == sum(per)                             # a sum over systems
     one_more = bench.rkc_flops(w, acc[:1], rej[:1], rhs[:1] + 1, sr[:1] + 1)   # one more power iteration
     assert one_more - per[0] == bench.rhs_flops(w) + 6 * w.neq
+    # one more accepted two-stage step: two evaluations, N (2 + 9 + 11) vector flops, 15 coefficient flops
+    one_step = bench.rkc_flops(w, acc[:1] + 1, rej[:1], rhs[:1] + 2, sr[:1])
+    assert one_step - per[0] == 2 * bench.rhs_flops(w) + 22 * w.neq + 15
+
+
+def test_seed0_network_flops():
+    # the benchmark network: 45 reactant and 38 product occurrences
+    w = W.massaction(nsys=1, seed=0)
+    assert int(w.network.n_reac.sum()) == 45 and int(w.network.n_prod.sum()) == 38
+    assert bench.rhs_flops(w) == 3 * 45 + 2 * 38
+
+
+def test_rkck_and_other_families():
+    v = W.vdp(2)
+    assert bench.rhs_flops(v) == 5
+    assert bench.rkck_flops(v, np.array([10]), np.array([2])) == 12 * (6 * 5 + 60 * 2)
+    assert bench.rhs_flops(W.bruss(2, n=32)) == 17 * 32
 
 
 def test_aggregate_rate_is_all_ranks_units_over_the_slowest_time():
