@@ -169,11 +169,13 @@ typedef struct {
     int32_t carry_mode;    /* ODE_CARRY_CONTINUE (default) or ODE_CARRY_RESTART, see `carry` */
     int32_t specrad;       /* RKC spectral radius: ODE_SPECRAD_POWER (default) / _GERSHGORIN / _POWER_CAPPED */
     int32_t reserved[6];   /* must be zero */
-    /* RKC, mixed precisions: optional per-system proposals [nsys] (device
-     * arrays, NaN = none) of the initial step and the spectral-radius bound,
-     * e.g. from ode_mlp_propose.  A system with a finite positive pair skips
-     * the initial power method and Euler trial step and starts from them;
-     * the error test still judges every step and the first rejection hands
+    /* RKC, mixed and two-float precisions: optional per-system proposals
+     * [nsys] (device arrays, NaN = none) of the initial step and the
+     * spectral-radius bound, e.g. from ode_mlp_propose.  A system with a
+     * finite positive sigma0 skips the initial power method; with a finite
+     * positive h0 beside it, the Euler trial step as well (it starts from
+     * h0), otherwise the trial sets the first step as without a proposal.
+     * The error test still judges every step and the first rejection hands
      * the system back to the power method (Appendix). */
     const float* h0;
     const float* sigma0;

@@ -976,12 +976,16 @@ struct RkcMixed {
                 rejected = false;
             }
         } else if (a.h0 != nullptr) {
-            // a proposed start replaces the initial power method and Euler
-            // trial; the first rejection returns the system to the power method
+            // a proposed spectral radius replaces the initial power method; a
+            // proposed step size beside it replaces the Euler trial as well
+            // (without one the trial sets h); the first rejection returns the
+            // system to the power method
             const float hp = a.h0[i], sp = a.sigma0[i];
-            if (isfinite(hp) && isfinite(sp) && hp > 0.0f && sp > 0.0f) {
-                h = (HT)hp < hmax ? (HT)hp : hmax;
-                h = h > hmin ? h : hmin;
+            if (isfinite(sp) && sp > 0.0f) {
+                if (isfinite(hp) && hp > 0.0f) {
+                    h = (HT)hp < hmax ? (HT)hp : hmax;
+                    h = h > hmin ? h : hmin;
+                }
                 sigma = (HT)sp;
                 have_sigma = true;
                 sr_step = 0;

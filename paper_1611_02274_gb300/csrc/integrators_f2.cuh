@@ -155,12 +155,16 @@ struct RkcF2 {
                 rejected = false;
             }
         } else if (a.h0 != nullptr) {
-            // a proposed start replaces the initial power method and Euler
-            // trial; the first rejection returns the system to the power method
+            // a proposed spectral radius replaces the initial power method; a
+            // proposed step size beside it replaces the Euler trial as well
+            // (without one the trial sets h); the first rejection returns the
+            // system to the power method
             const float hp = a.h0[i], sp = a.sigma0[i];
-            if (isfinite(hp) && isfinite(sp) && hp > 0.0f && sp > 0.0f) {
-                h = (HT)hp < hmax ? (HT)hp : hmax;
-                h = h > hmin ? h : hmin;
+            if (isfinite(sp) && sp > 0.0f) {
+                if (isfinite(hp) && hp > 0.0f) {
+                    h = (HT)hp < hmax ? (HT)hp : hmax;
+                    h = h > hmin ? h : hmin;
+                }
                 sigma = (HT)sp;
                 have_sigma = true;
                 sr_step = 0;
@@ -372,7 +376,7 @@ struct RkcF2 {
     __device__ void trial_consume(const BatchArgs& a, const TM& tm, const F2* f) {
         n_rhs += 1;
         const HT ssq = weighted_ssq(tm, [&](int s) {
-            return to_float(f[s] - Fn[s]) / (atolf + rtolf * fabsf(y[s].hi));
+            return __fdividef(to_float(f[s] - Fn[s]), atolf + rtolf * fabsf(y[s].hi));
         });
         const HT est = h * sqrt(ssq / (HT)n);
         if ((HT)kP1 * h < hmax * sqrt(est)) {
@@ -394,7 +398,7 @@ struct RkcF2 {
         cs.start(m, a);
         const F2 mut1h = cs.mut1f2() * hh;
 #pragma unroll(P <= 64 ? P : 4)
-        for (int s = 0; s < P; ++s) d1[s] = mut1h * Fn[s];
+        for (int s = 0; s < P; ++s) d1[s] = mul_lazy(mut1h, Fn[s]);  // a product: its pair stays near-normal
         j = 2;
         cs.stagef2(2, chi, clo);
         phase = PH_STAGE;
@@ -447,7 +451,7 @@ struct RkcF2 {
             e = fmaf(hh.hi, sum.lo, e);
             e = fmaf(hh.lo, sum.hi, e);
             const float D = fmaf(-2.0f, d1[s].hi, p) + fmaf(-2.0f, d1[s].lo, e);
-            return 0.4f * D / (atolf + rtolf * fmaxf(fabsf(x[s].hi), fabsf(y[s].hi)));
+            return __fdividef(0.4f * D, atolf + rtolf * fmaxf(fabsf(x[s].hi), fabsf(y[s].hi)));
         }) / (HT)n;  // err^2
         if (isnan(ms)) {
             n_rej += 1;

@@ -6,9 +6,11 @@ plus the first and the last 64 (the last block's ragged tail).
 
 Plain FP64: the sampled systems take the oracle's accepted / rejected
 counts -- the >= 99.9 % bar scaled to the sample, at most one mismatch --
-and end within 1e-9 relative; the status words agree.  Chosen (lean mixed)
-forms: no error status anywhere in the batch, and the error against the
-oracle within the bounds of the smaller mixed-form tests.  The sizes are
+and end within 1e-9 relative; the status words agree.  Chosen form (the
+two-float form): no error status anywhere in the batch and the final-state
+error against the oracle within the target, p99.9 <= 1e-5, with tighter
+regression guards on the median and p99.  The FP32 forms, which do not
+claim the target, are held to the bounds of the smaller mixed-form tests.  The sizes are
 those of the paper-shaped workloads: 65,536 64-unknown Brusselator grids,
 1,048,576 mass-action systems, a 262,144-system ragged batch and the
 4,194,304-system batch of the learned proposal.
@@ -42,15 +44,20 @@ def check_fp64_sample(w, g, idx):
     assert rel_err(g["y"][:, idx], ref.y, w.atol)[same].max() <= 1e-9
 
 
-def check_chosen_sample(w, g, idx, p99_bound, median_bound):
+TARGET_P999 = 1e-5  # the chosen form's bar against the FP64 oracle
+
+
+def check_chosen_sample(w, g, idx, p99_bound, median_bound, p999_bound=None):
     assert ((g["status"] & 0xFF) == 0).all()
     assert np.isfinite(g["y"]).all()
     ref = O.integrate_workload(W.subset(w, idx))
     e = rel_err(g["y"][:, idx], ref.y, w.atol)
-    print(w.name, w.nsys, "chosen vs oracle on", idx.size, "sampled: median", np.median(e),
-          "p99", np.quantile(e, 0.99), "max", e.max())
+    print(w.name, w.nsys, "vs oracle on", idx.size, "sampled: median", np.median(e),
+          "p99", np.quantile(e, 0.99), "p99.9", np.quantile(e, 0.999), "max", e.max())
     assert np.median(e) <= median_bound
     assert np.quantile(e, 0.99) <= p99_bound
+    if p999_bound is not None:
+        assert np.quantile(e, 0.999) <= p999_bound
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +72,15 @@ def test_massaction_1m_fp64(massaction_1m):
 
 
 def test_massaction_1m_chosen_form(massaction_1m):
-    # the benchmark's main step: lean split, generated network code, AUTO
+    # the benchmark's main step: two-float form, generated network code, AUTO
+    w = massaction_1m
+    g = run_gpu(w, precision=B.ODE_PREC_F2_LEAN)
+    check_chosen_sample(w, g, sample(w.nsys, 16384, seed=2), p99_bound=1e-7, median_bound=1e-8,
+                        p999_bound=TARGET_P999)
+
+
+def test_massaction_1m_lean_form(massaction_1m):
+    # the FP32 lean form (no target claimed): its error stays bounded
     w = massaction_1m
     g = run_gpu(w, precision=B.ODE_PREC_MIXED_LEAN)
     check_chosen_sample(w, g, sample(w.nsys, 16384, seed=2), p99_bound=2e-3, median_bound=1e-5)
@@ -84,7 +99,17 @@ def test_brusselator_65k_fp64(bruss_65k):
 
 def test_brusselator_65k_chosen_form(bruss_65k):
     w = bruss_65k
-    g = run_gpu(w, precision=B.ODE_PREC_MIXED_LEAN)
+    g = run_gpu(w, precision=B.ODE_PREC_F2_LEAN)
+    check_chosen_sample(w, g, sample(w.nsys, 4096, seed=4), p99_bound=1e-7, median_bound=1e-8,
+                        p999_bound=TARGET_P999)
+
+
+@pytest.mark.parametrize("prec", [B.ODE_PREC_MIXED, B.ODE_PREC_MIXED_LEAN])
+def test_brusselator_65k_fp32_stage_forms(bruss_65k, prec):
+    # FP32 stages with FP64 bookkeeping (the configured comparison) and the
+    # lean form: no target claimed, the error stays bounded
+    w = bruss_65k
+    g = run_gpu(w, precision=prec)
     check_chosen_sample(w, g, sample(w.nsys, 4096, seed=4), p99_bound=2e-3, median_bound=1e-4)
 
 
@@ -135,8 +160,9 @@ def test_ragged_262k_autotuned_plan():
 
 def test_learned_proposal_4m():
     # a proposal network trained briefly on a logged FP64 run, then the
-    # chosen form with the proposed start and the predicted-cost order over
-    # 4,194,304 systems, as in the benchmark's ordered proposal mode
+    # chosen form (two-float) with the proposed spectral radius and the
+    # predicted-cost order over 4,194,304 systems, as in the benchmark's
+    # with_sigma_ordered mode: within the target against the FP64 oracle
     import torch
     wt = W.massaction(nsys=65536, seed=1034)
     ht = B.register_workload(wt)
@@ -155,10 +181,11 @@ def test_learned_proposal_4m():
         try:
             y0 = torch.from_numpy(w.y0).cuda()
             p = torch.from_numpy(w.params).cuda()
-            h0, s0, c = net.propose(y0, p, with_cost=True)
+            _, s0, c = net.propose(y0, p, with_cost=True)
+            no_h0 = torch.full_like(s0, float("nan"))
             cnt = B.counters_like(w.nsys, "cuda")
             y = B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, counters=cnt,
-                            precision=B.ODE_PREC_MIXED_LEAN, mapping=B.ODE_MAP_AUTO, h0=h0, sigma0=s0, cost=c,
+                            precision=B.ODE_PREC_F2_LEAN, mapping=B.ODE_MAP_AUTO, h0=no_h0, sigma0=s0, cost=c,
                             sync=True)
             g = {"y": y.cpu().numpy(), "status": cnt.status.cpu().numpy()}
         finally:
@@ -166,4 +193,5 @@ def test_learned_proposal_4m():
     finally:
         net.release()
     assert np.mean((g["status"] & B.ODE_ST_PROPOSED) != 0) > 0.5
-    check_chosen_sample(w, g, sample(w.nsys, 8192, seed=6), p99_bound=2e-3, median_bound=1e-5)
+    check_chosen_sample(w, g, sample(w.nsys, 8192, seed=6), p99_bound=1e-6, median_bound=1e-8,
+                        p999_bound=TARGET_P999)
