@@ -7,10 +7,7 @@ namespace bode {
 
 cudaError_t launch_mass32_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
-    (void)r;
-    if (true) return run_model_prec<MassActionModel<32, 64>, ODE_PREC_FP64>(method, a, r.net, c);
-    *ok = false;
-    return cudaSuccess;
+    return run_model_prec<MassActionModel<32, 64>, ODE_PREC_FP64>(method, a, r.net, c);
 }
 
 }  // namespace bode

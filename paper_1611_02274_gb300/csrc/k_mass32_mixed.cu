@@ -7,10 +7,7 @@ namespace bode {
 
 cudaError_t launch_mass32_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
-    (void)r;
-    if (true) return run_model_mixed<MassActionModel<32, 64>>(method, prec, a, r.net, c);
-    *ok = false;
-    return cudaSuccess;
+    return run_model_mixed<MassActionModel<32, 64>>(method, prec, a, r.net, c);
 }
 
 }  // namespace bode

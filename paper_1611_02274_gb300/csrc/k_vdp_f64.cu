@@ -4,12 +4,9 @@
 
 namespace bode {
 
-cudaError_t launch_vdp_f64(int method, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+cudaError_t launch_vdp_f64(int method, const RhsEntry&, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
-    (void)r;
-    if (true) return run_model_prec<VdpModel, ODE_PREC_FP64>(method, a, NoCtx{}, c);
-    *ok = false;
-    return cudaSuccess;
+    return run_model_prec<VdpModel, ODE_PREC_FP64>(method, a, NoCtx{}, c);
 }
 
 }  // namespace bode

@@ -4,12 +4,9 @@
 
 namespace bode {
 
-cudaError_t launch_vdp_mixed(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
+cudaError_t launch_vdp_mixed(int method, int prec, const RhsEntry&, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
     *ok = true;
-    (void)r;
-    if (true) return run_model_mixed<VdpModel>(method, prec, a, NoCtx{}, c);
-    *ok = false;
-    return cudaSuccess;
+    return run_model_mixed<VdpModel>(method, prec, a, NoCtx{}, c);
 }
 
 }  // namespace bode

@@ -54,8 +54,11 @@ def test_gradient_matches_oracle():
     loss_ref, g_ref = M.loss_and_grad(M.bf16_round(params), norm, X, Y)
     g = g.cpu().numpy()
     assert loss == pytest.approx(loss_ref, rel=1e-4)
-    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
-    # every block of the parameter vector, not just the norm
+    # element by element: every weight's and bias's gradient (FP32 sums of
+    # 700 samples' terms on the GPU against FP64): 1e-3 relative, and an
+    # absolute floor of 1e-5 of the largest gradient for the near-zero ones
+    np.testing.assert_allclose(g, g_ref, rtol=1e-3, atol=1e-5 * np.abs(g_ref).max())
+    # summary per block of the parameter vector (W1, b1, W2, b2 + W3 + b3)
     for lo, hi in [(0, 64 * 14), (64 * 14, 64 * 15), (64 * 15, 64 * 15 + 4096), (params.size - 195, params.size)]:
         assert np.linalg.norm(g[lo:hi] - g_ref[lo:hi]) <= 1e-3 * np.linalg.norm(g_ref[lo:hi]) + 1e-9
     net.release()
