@@ -431,11 +431,14 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     """The learned proposal on the 4,194,304-system mass-action batch:
     trained on records the plain FP64 solver logs on held-out seeds (state
     features -> first step, spectral-radius bound, whole-integration cost),
-    then the chosen form timed without it, with the proposed start, and
-    with the proposed start plus the batch taken longest-first by the
-    predicted cost (the proposal and ordering passes are inside the timed
-    step).  For context, the order from the true costs of an earlier run on
-    the same inputs bounds what any cost predictor can give."""
+    then the chosen form timed without it, with the proposed spectral radius
+    (the Euler trial still sets the first step), with the proposed start
+    (spectral radius and first step), and each of these with the batch
+    taken longest-first by the predicted cost (the proposal and ordering
+    passes are inside the timed step); every mode's error against the FP64
+    oracle on a sample.  For context, the order from the true costs of an
+    earlier run on the same inputs bounds what any cost predictor can
+    give."""
     import oracle as O
     t_start = time.perf_counter()
     wt = W.massaction(nsys=args.proposal_train, seed=1000 + rank)
@@ -461,12 +464,15 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     B.prepare(h, "rkc", CH)
     true_cost = None
 
+    no_h0 = torch.full((w.nsys,), float("nan"), dtype=torch.float32, device=dev)
+
     def step(mode, counters=None):
         kw = {}
-        if mode in ("with_proposal", "with_proposal_ordered"):
+        if mode.startswith("with_"):
             h0, s0, c = net.propose(y0, p, stream=stream.cuda_stream, with_cost=True)
-            kw = dict(h0=h0, sigma0=s0)
-            if mode == "with_proposal_ordered":
+            # with_sigma*: only the spectral radius (the Euler trial sets h0)
+            kw = dict(h0=no_h0 if mode.startswith("with_sigma") else h0, sigma0=s0)
+            if mode.endswith("_ordered"):
                 kw["cost"] = c
         elif mode == "ordered_by_true_cost":
             kw = dict(cost=true_cost)
@@ -474,8 +480,10 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
                     mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream, **kw)
 
     res = {}
-    for mode in ("without", "with_proposal", "with_proposal_ordered", "ordered_by_true_cost"):
-        for _ in range(args.warmup):
+    MODES = ("without", "with_sigma", "with_sigma_ordered", "with_proposal", "with_proposal_ordered",
+             "ordered_by_true_cost")
+    for mode in MODES:
+        for _ in range(1):
             step(mode)
         torch.cuda.synchronize()
         barrier()
@@ -498,7 +506,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
             "reject_rate": float(np.sum(c["n_reject"]) / np.sum(c["n_accept"] + c["n_reject"])),
             "mean_rhs": float(np.mean(c["n_rhs"])), "mean_power_iterations": float(np.mean(c["n_specrad_iter"])),
             "proposal_used": float(np.mean((c["status"] & B.ODE_ST_PROPOSED) != 0)),
-            "y_sample": yout[:, :2048].cpu().numpy()}
+            "y_sample": yout[:, :args.proposal_sample].cpu().numpy()}
         if mode == "with_proposal_ordered":
             pred = np.log(net.propose(y0, p, with_cost=True)[2].cpu().numpy())
             res[mode]["log_cost_corr_pred_vs_true"] = float(np.corrcoef(pred, np.log(c["n_rhs"]))[0, 1])
@@ -506,18 +514,24 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
                                            "same inputs (the previous global step in operator splitting)")
     B.release(h)
     net.release()
-    ref = O.integrate_workload(W.subset(w, np.arange(2048)))
+    ref = O.integrate_workload(W.subset(w, np.arange(args.proposal_sample)))
     for k, r in res.items():
         e = (np.abs(r.pop("y_sample") - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
         r["err_vs_fp64_oracle_max"] = float(e.max())
         r["err_vs_fp64_oracle_p999"] = float(np.quantile(e, 0.999))
+        r["err_vs_fp64_oracle_median"] = float(np.median(e))
+        r["meets_target"] = bool(r["err_vs_fp64_oracle_p999"] <= TARGET_P999)
+    qual = [k for k in MODES if res[k]["meets_target"] and k != "ordered_by_true_cost"]
+    res["fastest_within_target"] = max(qual, key=lambda k: res[k]["systems_per_s"]) if qual else None
     res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": int(ok.sum().item()), "train_seeds": "1000+rank",
                      "eval_seed": "4+rank", "epochs": args.proposal_epochs, "batch": 4096, "final_train_loss": float(hist[-1]),
                      "train_seconds_incl_logging": t_train,
                      "network": "14 -> 64 -> 64 -> 3 SiLU (log h0, log sigma, log cost), BF16 weights, "
                                 "FP32 accumulate"}
-    res["speedup_with_proposal"] = res["without"]["ms_per_step"] / res["with_proposal"]["ms_per_step"]
-    res["speedup_with_proposal_ordered"] = res["without"]["ms_per_step"] / res["with_proposal_ordered"]["ms_per_step"]
+    for k in MODES[1:]:
+        res["speedup_" + k] = res["without"]["ms_per_step"] / res[k]["ms_per_step"]
+    res["config"]["form"] = FORM_TEXT[args.chosen]
+    res["config"]["oracle_sample"] = args.proposal_sample
     return res
 
 
@@ -787,7 +801,8 @@ def split_leg(args, B, torch, dev, stream, rank, world, barrier):
     res["speedup_vs_cold"] = {m: res["cold"]["ms_per_chain"] / res[m]["ms_per_chain"] for m in MODES}
     res["config"] = {"nsys_per_gpu": w.nsys, "global_steps": args.split_steps, "interval": [w.t0, w.tend],
                      "timed": f"{args.split_reps} repetitions of the whole chain after one warm-up repetition",
-                     "precision": "mixed lean", "state": "device resident (the paper copies each global step)"}
+                     "precision": FORM_TEXT[args.chosen],
+                     "state": "device resident (the paper copies each global step)"}
     return res
 
 
@@ -1098,6 +1113,7 @@ def main():
     ap.add_argument("--proposal-train", type=int, default=1 << 20)
     ap.add_argument("--proposal-steps", type=int, default=3)
     ap.add_argument("--proposal-epochs", type=int, default=24)
+    ap.add_argument("--proposal-sample", type=int, default=8192, help="systems of the leg compared with the oracle")
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)
     ap.add_argument("--mixed-sample", type=int, default=1024, help="ragged systems compared with the oracle")
