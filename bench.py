@@ -74,8 +74,10 @@ FORM_TEXT = {
 # DRAM bytes (read + write) per system of each form's generated kernel, from
 # one ncu capture of k_static on 262,144 systems of this workload; traffic
 # grows with the number of systems (each state is read once, written once).
-# mixed_lean: 29.883 MB read + 0.899 MB written.
-NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144}
+# mixed_lean: 29.883 MB read + 0.899 MB written; f2_lean: 30.470 MB read +
+# 0.483 MB written.
+NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
+                                "f2_lean": (30.470144e6 + 0.48256e6) / 262144}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
                       "(null when another kernel ran or no capture of this kernel exists)")
 
@@ -388,6 +390,10 @@ def run_ours(args):
                                     "the plain FP64 form's systems/s",
                              "chosen": args.chosen, "chosen_meets": forms[args.chosen]["meets_target"],
                              "fastest_qualifying": max(qual, key=lambda n: forms[n]["value"]) if qual else None}
+    if args.stoich_reps > 0 and rank == 0:
+        lean = runs.get("mixed_lean")
+        out["stoich_tensor_cores"] = stoich_leg(args, B, float(np.mean(lean["c"]["n_rhs"])) if lean else None,
+                                                lean["ms"] if lean else None)
     if args.c0_steps > 0:
         c0 = c0_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
@@ -872,6 +878,41 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
     return res
 
 
+def stoich_leg(args, B, mean_rhs, lean_ms):
+    """The tensor-core question for the one contraction of the mass-action
+    right-hand side, f = N r (Section 4.2's omega_i sums), measured on the
+    benchmark network: the sparse FP32 form the generated integrators use
+    against a warp-level TF32 tensor-core product with the rates split into
+    two TF32 words (FP32-class accuracy), each timed over `reps` products
+    per system minus a launch with none.  The per-step effect on the FP32
+    lean form follows from its evaluations per system (mean_rhs) and its
+    measured step (lean_ms, 1,048,576 systems)."""
+    w = W.massaction(nsys=8, seed=0)
+    h = B.register_workload(w)
+    n, reps = args.stoich_nsys, args.stoich_reps
+    res = {}
+    for name, v in (("sparse_fp32", 0), ("tensor_tf32x2", 1)):
+        t0, _ = B.stoich_bench(h, v, n, 0)
+        t1, err = B.stoich_bench(h, v, n, reps)
+        per = (t1 - t0) / reps
+        res[name] = {"ms_per_product_over_batch": per, "ns_per_system_product": per * 1e6 / n,
+                     "launch_ms_with_products": t1, "launch_ms_without": t0,
+                     "max_err_vs_fp64_per_sum_of_terms": err}
+    B.release(h)
+    sp, tc = res["sparse_fp32"]["ms_per_product_over_batch"], res["tensor_tf32x2"]["ms_per_product_over_batch"]
+    res["tensor_over_sparse_time"] = tc / sp
+    if mean_rhs and lean_ms:
+        delta = (tc - sp) * mean_rhs * (NSYS / n)
+        res["lean_step_1m"] = {"measured_ms": lean_ms, "products_per_step_ms_sparse": sp * mean_rhs * (NSYS / n),
+                               "estimated_ms_with_tensor_product": lean_ms + delta}
+    res["config"] = {"nsys": n, "reps": reps, "network": "seed-0 mass-action, 13 species x 27 reactions",
+                     "rates": "synthetic, log-uniform in [1e-8, 1e4]",
+                     "tensor": "mma.sync m16n8k8 TF32 (leading + trailing TF32 words of the rates, exact integer "
+                               "coefficients), FP32 accumulation; rates staged through shared memory into the "
+                               "A-fragment layout, results back to one row per lane"}
+    return res
+
+
 def timed_calls(torch, stream, fn, steps, warmup, barrier):
     """Mean milliseconds of fn() over `steps` calls after `warmup` untimed
     ones (CUDA events on the launching stream)."""
@@ -1121,6 +1162,8 @@ def main():
     ap.add_argument("--c0-big", type=int, default=1 << 20, help="systems of the weak-scaled van der Pol batch")
     ap.add_argument("--c1-steps", type=int, default=2, help="timed steps per form of the Brusselator leg (0 skips)")
     ap.add_argument("--c1-nsys", type=int, default=65536)
+    ap.add_argument("--stoich-reps", type=int, default=64, help="products per system of the tensor-core leg (0 skips)")
+    ap.add_argument("--stoich-nsys", type=int, default=1 << 20)
     ap.add_argument("--specrad-steps", type=int, default=2, help="timed steps per spectral-radius mode (0 skips)")
     ap.add_argument("--pleiades-nsys", type=int, default=262144, help="n-body RKCK leg batch (0 skips)")
     ap.add_argument("--kinetics-nsys", type=int, default=16384, help="kinetics leg batch (0 skips)")

@@ -48,7 +48,7 @@ struct RkcF2 {
     using TM = Team<W>;
     using HT = typename Pick<BK64, double, float>::type;
     typename Model::template Sys<F2> sys;
-    F2 y[P], Fn[P], d1[P];  // d_j = w_j - y_n (d_0 = 0); d_{j-2} below
+    F2 Fn[P], d1[P];  // d_j = w_j - y_n (d_0 = 0); y_n and d_{j-2} below
     static constexpr int V_SMEM = rkc_f2_smem_floats(W, P);
     // the system's constants, one row per thread after the V rows (an even
     // offset: 8-byte aligned pairs, since blocks are a multiple of 32 threads)
@@ -58,17 +58,44 @@ struct RkcF2 {
     // two-stage step -- the common case at tight tolerances -- touches it
     // never and holds no registers for it
     static constexpr int D2_SMEM = (W == 1 && P <= 32) ? 2 * (P | 1) : 0;
-    static constexpr int SMEM_FLOATS = V_SMEM + C_SMEM + D2_SMEM + ModelSmem<Model>::value;
+    // the state y_n, read at the evaluation points, the error weights and
+    // the accept only: for one-thread systems a shared-memory row too, so
+    // that no state pair stays live across the right-hand-side evaluation
+    static constexpr int Y_SMEM = (W == 1 && P <= 32) ? 2 * (P | 1) : 0;
+    static constexpr int SMEM_FLOATS = V_SMEM + C_SMEM + D2_SMEM + Y_SMEM + ModelSmem<Model>::value;
     mutable F2 vreg[V_SMEM ? 1 : P];
     mutable F2 d2reg[D2_SMEM ? 1 : P];
+    mutable F2 yreg[Y_SMEM ? 1 : P];
     float* vs;
     F2* d2s;
+    F2* ys;
     __device__ void bind_smem(float* base, int stride) {
         vs = base + threadIdx.x * V_SMEM;  // this thread's row
         if constexpr (C_SMEM > 0) sys.bind_consts(base + V_SMEM * stride + threadIdx.x * C_SMEM);
         if constexpr (D2_SMEM > 0)
             d2s = reinterpret_cast<F2*>(base + (V_SMEM + C_SMEM) * stride + threadIdx.x * D2_SMEM);
-        if constexpr (ModelSmem<Model>::value > 0) sys.bind(base + (V_SMEM + C_SMEM + D2_SMEM) * stride, stride);
+        if constexpr (Y_SMEM > 0)
+            ys = reinterpret_cast<F2*>(base + (V_SMEM + C_SMEM + D2_SMEM) * stride + threadIdx.x * Y_SMEM);
+        if constexpr (ModelSmem<Model>::value > 0)
+            sys.bind(base + (V_SMEM + C_SMEM + D2_SMEM + Y_SMEM) * stride, stride);
+    }
+    __device__ F2 Yg(int s) const {
+        if constexpr (Y_SMEM > 0)
+            return ys[s];
+        else
+            return yreg[s];
+    }
+    __device__ void Ys(int s, F2 v) const {
+        if constexpr (Y_SMEM > 0)
+            ys[s] = v;
+        else
+            yreg[s] = v;
+    }
+    __device__ const F2* yp() const {
+        if constexpr (Y_SMEM > 0)
+            return ys;
+        else
+            return yreg;
     }
     __device__ F2 D2g(int s) const {
         if constexpr (D2_SMEM > 0)
@@ -113,7 +140,7 @@ struct RkcF2 {
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            y[s] = F2(c >= 0 ? a.y0[a.yidx(i, c)] : 0.0);
+            Ys(s, F2(c >= 0 ? a.y0[a.yidx(i, c)] : 0.0));
         }
         t = a.t0_of(i);
         tend = a.tend_of(i);
@@ -198,7 +225,7 @@ struct RkcF2 {
         switch (phase) {
         case PH_F0:
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) x[s] = y[s];
+            for (int s = 0; s < P; ++s) x[s] = Yg(s);
             break;
         case PH_SR:
 #pragma unroll(P <= 64 ? P : 4)
@@ -206,11 +233,11 @@ struct RkcF2 {
             break;
         case PH_TRIAL:
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) x[s] = y[s] + hh * Fn[s];
+            for (int s = 0; s < P; ++s) x[s] = Yg(s) + hh * Fn[s];
             break;
         default:  // stages and F_{n+1}: w = y_n + d (left unnormalised: it feeds products)
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) x[s] = add_lazy(y[s], d1[s]);
+            for (int s = 0; s < P; ++s) x[s] = add_lazy(Yg(s), d1[s]);
         }
     }
 
@@ -256,7 +283,7 @@ struct RkcF2 {
         }
         if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
             if (a.specrad == ODE_SPECRAD_GERSHGORIN) {  // the bound replaces the power method
-                sigma = (HT)to_double(sys.gershgorin(tm, y));
+                sigma = (HT)to_double(sys.gershgorin(tm, yp()));
                 have_sigma = true;
                 sr_step = num_step;
                 after_sr(a);
@@ -270,18 +297,18 @@ struct RkcF2 {
 
     // power method (Appendix) with the FP64 perturbation size
     __device__ void sr_begin(const TM& tm) {
-        const float nrm1 = sqrtf(sumsq_hi(tm, [&](int s) { return y[s].hi; }));
+        const float nrm1 = sqrtf(sumsq_hi(tm, [&](int s) { return Yg(s).hi; }));
         const float nrm2 = sqrtf(sumsq_hi(tm, [&](int s) { return Vg(s).hi; }));
         if (nrm1 != 0.0f && nrm2 != 0.0f) {
             dynrm = nrm1 * kSqrtUround;
             const float sc = dynrm / nrm2;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) Vs(s, y[s] + Vg(s) * sc);
+            for (int s = 0; s < P; ++s) Vs(s, Yg(s) + Vg(s) * sc);
         } else if (nrm1 != 0.0f) {
             dynrm = nrm1 * kSqrtUround;
             const F2 sc(1.0 + (double)kSqrtUround);
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) Vs(s, y[s] * sc);
+            for (int s = 0; s < P; ++s) Vs(s, Yg(s) * sc);
         } else if (nrm2 != 0.0f) {
             dynrm = (float)kUround;
             const float sc = dynrm / nrm2;
@@ -312,23 +339,23 @@ struct RkcF2 {
         sig = d / dynrm;
         if (sr_iter >= 2 && fabsf(sig - sig_prev) <= fmaxf(sig, 1.0f / (float)hmax) * 0.01f) {
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - y[s]);
+            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - Yg(s));
             sr_end(a, tm);
             return;
         }
         if (d != 0.0f) {
             const float sc = dynrm / d;
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) Vs(s, y[s] + df[s] * sc);
+            for (int s = 0; s < P; ++s) Vs(s, Yg(s) + df[s] * sc);
         } else {
             const int ind = sr_iter % n;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s)
-                if (opaque(sys.comp(tm, s)) == ind) Vs(s, y[s] - (Vg(s) - y[s]));
+                if (opaque(sys.comp(tm, s)) == ind) Vs(s, Yg(s) - (Vg(s) - Yg(s)));
         }
         if (sr_iter == kSpecradItmax) {
 #pragma unroll(P <= 64 ? P : 4)
-            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - y[s]);
+            for (int s = 0; s < P; ++s) Vs(s, Vg(s) - Yg(s));
             status |= ODE_ST_SPECRAD_NOCONV;
             sr_end(a, tm);
         }
@@ -337,7 +364,7 @@ struct RkcF2 {
     __device__ void sr_end(const BatchArgs& a, const TM& tm) {
         sigma = (HT)1.2 * (HT)sig;
         if (a.specrad == ODE_SPECRAD_POWER_CAPPED) {
-            const HT g = (HT)to_double(sys.gershgorin(tm, y));
+            const HT g = (HT)to_double(sys.gershgorin(tm, yp()));
             sigma = sigma < g ? sigma : g;
         }
         have_sigma = true;
@@ -376,7 +403,7 @@ struct RkcF2 {
     __device__ void trial_consume(const BatchArgs& a, const TM& tm, const F2* f) {
         n_rhs += 1;
         const HT ssq = weighted_ssq(tm, [&](int s) {
-            return __fdividef(to_float(f[s] - Fn[s]), atolf + rtolf * fabsf(y[s].hi));
+            return __fdividef(to_float(f[s] - Fn[s]), atolf + rtolf * fabsf(Yg(s).hi));
         });
         const HT est = h * sqrt(ssq / (HT)n);
         if ((HT)kP1 * h < hmax * sqrt(est)) {
@@ -451,7 +478,7 @@ struct RkcF2 {
             e = fmaf(hh.hi, sum.lo, e);
             e = fmaf(hh.lo, sum.hi, e);
             const float D = fmaf(-2.0f, d1[s].hi, p) + fmaf(-2.0f, d1[s].lo, e);
-            return __fdividef(0.4f * D, atolf + rtolf * fmaxf(fabsf(x[s].hi), fabsf(y[s].hi)));
+            return __fdividef(0.4f * D, atolf + rtolf * fmaxf(fabsf(x[s].hi), fabsf(Yg(s).hi)));
         }) / (HT)n;  // err^2
         if (isnan(ms)) {
             n_rej += 1;
@@ -496,9 +523,10 @@ struct RkcF2 {
         float chk = 0.0f;  // one finiteness test of a sum per system
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
-            y[s] = y[s] + d1[s];
+            const F2 yn = Yg(s) + d1[s];
+            Ys(s, yn);
             Fn[s] = f[s];
-            chk += (sys.comp(tm, s) >= 0) ? y[s].hi - y[s].hi : 0.0f;
+            chk += (sys.comp(tm, s) >= 0) ? yn.hi - yn.hi : 0.0f;
         }
         const bool bad = !(chk == 0.0f);
         h = h * (HT)fmaxf((float)kP1, fac);
@@ -516,7 +544,7 @@ struct RkcF2 {
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
-            if (c >= 0) a.y_out[a.yidx_out(i, c)] = to_double(y[s]);
+            if (c >= 0) a.y_out[a.yidx_out(i, c)] = to_double(Yg(s));
             if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = to_double(Vg(s));
         }
         if (a.carry != nullptr && tm.lane == 0) {
