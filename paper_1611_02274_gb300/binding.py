@@ -29,7 +29,7 @@ ODE_IO_DEVICE, ODE_IO_HOST = 0, 1
 ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
 
 EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_integrate", "rkc_integrate",
-            "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak",
+            "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak", "bode_stoich_bench",
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
             "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
     L.ode_last_error.restype = C.c_char_p
     L.ode_version.restype = C.c_char_p
     L.bode_fma_peak.argtypes = [C.c_int, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.bode_stoich_bench.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
     L.ode_ragged_plan_create.argtypes = [C.POINTER(RaggedBatch), C.POINTER(Opts), P, C.POINTER(Stats), P,
                                          C.POINTER(C.c_int64)]
     L.ode_ragged_plan_launch.argtypes = [C.c_int64, P]
@@ -284,6 +286,15 @@ def counters_like(nsys: int, device=None) -> Counters:
         return Counters(*[np.zeros(nsys, dtype=np.int32) for _ in range(5)])
     import torch
     return Counters(*[torch.zeros(nsys, dtype=torch.int32, device=device) for _ in range(5)])
+
+
+def stoich_bench(handle: int, variant: int, nsys: int, reps: int):
+    """bode_stoich_bench: (launch ms, max error vs FP64 relative to the sum
+    of |terms|) of the stoichiometry product, variant 0 sparse FP32, 1 TF32
+    tensor cores."""
+    ms, err = C.c_double(0), C.c_double(float("nan"))
+    _check(load().bode_stoich_bench(handle, variant, nsys, reps, C.byref(ms), C.byref(err)))
+    return ms.value, err.value
 
 
 def fma_peak(fp64: bool, iters: int = 1 << 16):

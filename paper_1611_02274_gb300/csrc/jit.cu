@@ -464,7 +464,94 @@ int get_kernels(const RhsEntry& r, int method, int prec, JitKernels* k, std::str
     return rc;
 }
 
+// Compiles a stand-alone device program (the library's device headers
+// available) for sm_103a and loads it on the current device; kernels by
+// name expression.  Cached in memory per device and source.
+struct JitProgram {
+    cudaLibrary_t lib = nullptr;
+    std::vector<cudaKernel_t> kernels;
+};
+std::map<std::string, JitProgram> g_programs;
+
+int compile_program(const std::string& src, const std::vector<std::string>& names, JitProgram* out,
+                    std::string* err) {
+    Nvrtc& nv = nvrtc();
+    if (!nv.ok) {
+        *err = "NVRTC unavailable: " + nv.why;
+        return ODE_ERR_UNSUPPORTED;
+    }
+    std::vector<const char*> hnames, hsrcs;
+    for (int k = 0; k < kJitHeaderCount; ++k) {
+        hnames.push_back(kJitHeaderNames[k]);
+        hsrcs.push_back(kJitHeaderSources[k]);
+    }
+    for (int k = 0; k < 4; ++k) {
+        hnames.push_back(kStubNames[k]);
+        hsrcs.push_back(kStubSources[k]);
+    }
+    nvrtcProgram prog;
+    nvrtcResult rc = nv.create(&prog, src.c_str(), "jit_program.cu", (int)hnames.size(), hsrcs.data(), hnames.data());
+    if (rc != NVRTC_SUCCESS) {
+        *err = std::string("nvrtcCreateProgram: ") + nv.errstr(rc);
+        return ODE_ERR_UNSUPPORTED;
+    }
+    for (const auto& n : names) nv.add_name(prog, n.c_str());
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    rc = nv.compile(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nv.log_size(prog, &ls);
+        std::string logtxt(ls, '\0');
+        nv.log(prog, &logtxt[0]);
+        nv.destroy(&prog);
+        *err = "NVRTC compile failed: " + logtxt.substr(0, 2000);
+        return ODE_ERR_UNSUPPORTED;
+    }
+    std::vector<std::string> lowered;
+    for (const auto& n : names) {
+        const char* l = nullptr;
+        nv.lowered(prog, n.c_str(), &l);
+        lowered.push_back(l ? l : "");
+    }
+    size_t cs = 0;
+    nv.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    nv.cubin(prog, cubin.data());
+    nv.destroy(&prog);
+    cudaError_t e = cudaLibraryLoadData(&out->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    out->kernels.assign(names.size(), nullptr);
+    for (size_t k = 0; k < names.size() && e == cudaSuccess; ++k)
+        e = cudaLibraryGetKernel(&out->kernels[k], out->lib, lowered[k].c_str());
+    if (e != cudaSuccess) {
+        *err = std::string("loading a generated program: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    return ODE_OK;
+}
+
 }  // namespace
+
+int jit_program(const std::string& src, const std::vector<std::string>& names, std::vector<cudaKernel_t>* kernels,
+                std::string* err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    std::string key = std::to_string(dev) + "/" + std::to_string(fnv1a(src));
+    for (const auto& n : names) key += "/" + n;
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    auto it = g_programs.find(key);
+    if (it == g_programs.end()) {
+        JitProgram p;
+        const int rc = compile_program(src, names, &p, err);
+        if (rc) return rc;
+        it = g_programs.emplace(key, p).first;
+    }
+    *kernels = it->second.kernels;
+    return ODE_OK;
+}
 
 bool jit_available() { return nvrtc().ok; }
 

@@ -1,6 +1,7 @@
 // jit.h -- run-time specialised kernels for registered mass-action networks.
 #pragma once
 #include <string>
+#include <vector>
 
 #include "launch.cuh"
 
@@ -19,5 +20,10 @@ int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err);
 
 // The generated model source of network r (for inspection).
 std::string jit_model_source(const RhsEntry& r);
+
+// Compile and load a stand-alone generated device program on the current
+// device (cached); *kernels receives the kernels of the name expressions.
+int jit_program(const std::string& src, const std::vector<std::string>& names, std::vector<cudaKernel_t>* kernels,
+                std::string* err);
 
 }  // namespace bode
