@@ -436,25 +436,38 @@ def run_ours(args):
 def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     """The learned proposal on the 4,194,304-system mass-action batch:
     trained on records the plain FP64 solver logs on held-out seeds (state
-    features -> first step, spectral-radius bound, whole-integration cost),
-    then the chosen form timed without it, with the proposed spectral radius
+    features -> first step, spectral-radius bound, whole-integration cost;
+    and state features -> spectral-radius bound at later estimates), then
+    the chosen form timed without it, with the proposed spectral radius
     (the Euler trial still sets the first step), with the proposed start
-    (spectral radius and first step), and each of these with the batch
-    taken longest-first by the predicted cost (the proposal and ordering
-    passes are inside the timed step); every mode's error against the FP64
-    oracle on a sample.  For context, the order from the true costs of an
-    earlier run on the same inputs bounds what any cost predictor can
-    give."""
+    (spectral radius and first step), with the network evaluated in the
+    kernel at every spectral-radius point (with_sigma_every), and each of
+    these with the batch taken longest-first by the predicted cost (the
+    proposal and ordering passes are inside the timed step); every mode's
+    error against the FP64 oracle on a sample.  For context, the order from
+    the true costs of an earlier run on the same inputs bounds what any
+    cost predictor can give."""
     import oracle as O
     t_start = time.perf_counter()
     wt = W.massaction(nsys=args.proposal_train, seed=1000 + rank)
     ht = B.register_workload(wt)
     log = torch.full((wt.nsys, wt.neq + 4), float("nan"), dtype=torch.float32, device=dev)
+    lsr = torch.full((wt.nsys, args.proposal_sr_records, wt.neq + 2), float("nan"), dtype=torch.float32, device=dev)
     B.integrate("rkc", ht, torch.from_numpy(wt.y0).to(dev), torch.from_numpy(wt.params).to(dev), wt.t0, wt.tend,
-                wt.rtol, wt.atol, precision=B.ODE_PREC_FP64, log_xy=log, sync=True)
+                wt.rtol, wt.atol, precision=B.ODE_PREC_FP64, log_xy=log, log_sr=lsr,
+                log_sr_every=args.proposal_sr_every, sync=True)
     B.release(ht)
     ok = torch.isfinite(log).all(dim=1)
-    X, Y = log[ok, :wt.neq + 1].contiguous(), log[ok, wt.neq + 1:].contiguous()
+    # first-step records (all three targets) and spectral-radius records
+    # (sigma only: the other targets NaN, which the training skips)
+    r = lsr.reshape(-1, wt.neq + 2)
+    r = r[torch.isfinite(r).all(dim=1)]
+    Y2 = torch.full((r.shape[0], 3), float("nan"), dtype=torch.float32, device=dev)
+    Y2[:, 1] = r[:, wt.neq + 1]
+    X = torch.cat([log[ok, :wt.neq + 1], r[:, :wt.neq + 1]]).contiguous()
+    Y = torch.cat([log[ok, wt.neq + 1:], Y2]).contiguous()
+    n_sr_records = int(r.shape[0])
+    del lsr, r, Y2
     net = B.MLP(wt.neq + 1, seed=0)
     net.fit_normalization(X, Y)
     hist = net.train(X, Y, epochs=args.proposal_epochs, batch=4096, lr=2e-3, seed=0)
@@ -474,7 +487,12 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
 
     def step(mode, counters=None):
         kw = {}
-        if mode.startswith("with_"):
+        if mode.startswith("with_sigma_every"):
+            # the network in the kernel at every spectral-radius point
+            kw = dict(mlp=net)
+            if mode.endswith("_ordered"):
+                kw["cost"] = net.propose(y0, p, stream=stream.cuda_stream, with_cost=True)[2]
+        elif mode.startswith("with_"):
             h0, s0, c = net.propose(y0, p, stream=stream.cuda_stream, with_cost=True)
             # with_sigma*: only the spectral radius (the Euler trial sets h0)
             kw = dict(h0=no_h0 if mode.startswith("with_sigma") else h0, sigma0=s0)
@@ -487,7 +505,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
 
     res = {}
     MODES = ("without", "with_sigma", "with_sigma_ordered", "with_proposal", "with_proposal_ordered",
-             "ordered_by_true_cost")
+             "with_sigma_every", "with_sigma_every_ordered", "ordered_by_true_cost")
     for mode in MODES:
         for _ in range(1):
             step(mode)
@@ -529,7 +547,11 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
         r["meets_target"] = bool(r["err_vs_fp64_oracle_p999"] <= TARGET_P999)
     qual = [k for k in MODES if res[k]["meets_target"] and k != "ordered_by_true_cost"]
     res["fastest_within_target"] = max(qual, key=lambda k: res[k]["systems_per_s"]) if qual else None
-    res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": int(ok.sum().item()), "train_seeds": "1000+rank",
+    res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": int(ok.sum().item()),
+                     "train_sigma_records": n_sr_records,
+                     "sigma_records_per_system": f"estimates 0, {args.proposal_sr_every}, ... (at most "
+                                                 f"{args.proposal_sr_records})",
+                     "train_seeds": "1000+rank",
                      "eval_seed": "4+rank", "epochs": args.proposal_epochs, "batch": 4096, "final_train_loss": float(hist[-1]),
                      "train_seconds_incl_logging": t_train,
                      "network": "14 -> 64 -> 64 -> 3 SiLU (log h0, log sigma, log cost), BF16 weights, "
@@ -1154,6 +1176,9 @@ def main():
     ap.add_argument("--proposal-train", type=int, default=1 << 20)
     ap.add_argument("--proposal-steps", type=int, default=3)
     ap.add_argument("--proposal-epochs", type=int, default=24)
+    ap.add_argument("--proposal-sr-records", type=int, default=4,
+                    help="spectral-radius training records per system (estimates 0, k, 2k, ...)")
+    ap.add_argument("--proposal-sr-every", type=int, default=10)
     ap.add_argument("--proposal-sample", type=int, default=8192, help="systems of the leg compared with the oracle")
     ap.add_argument("--mixed-nsys", type=int, default=262144, help="0 skips the ragged-batch leg")
     ap.add_argument("--mixed-steps", type=int, default=3)

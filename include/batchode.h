@@ -59,7 +59,7 @@ extern "C" {
 #define ODE_ST_MAX_ATTEMPTS 2     /* attempt cap reached before tend */
 #define ODE_ST_NONFINITE 3        /* NaN error estimate or non-finite state */
 #define ODE_ST_SPECRAD_NOCONV 256 /* warning bit: power method did not converge */
-#define ODE_ST_PROPOSED 512       /* information bit: RKC started from a proposed h0 / sigma0 */
+#define ODE_ST_PROPOSED 512       /* information bit: RKC took a proposed h0 / sigma0 or the network's bound (opts.mlp) */
 
 /* right-hand-side families */
 #define ODE_RHS_VDP 1        /* van der Pol: y1' = y2, y2' = mu (1 - y1^2) y2 - y1; params [mu]; neq 2 */
@@ -168,7 +168,10 @@ typedef struct {
     int32_t cost_kind;     /* element type of `cost`: 0 = float32, 1 = int32 (e.g. a previous n_rhs) */
     int32_t carry_mode;    /* ODE_CARRY_CONTINUE (default) or ODE_CARRY_RESTART, see `carry` */
     int32_t specrad;       /* RKC spectral radius: ODE_SPECRAD_POWER (default) / _GERSHGORIN / _POWER_CAPPED */
-    int32_t reserved[6];   /* must be zero */
+    int32_t mlp;           /* proposal network handle (ode_mlp_create) evaluated in-kernel, 0 = none; see below */
+    int32_t log_sr_every;  /* stride of the spectral-radius training log (<= 0: 1); see log_sr */
+    int32_t log_sr_records;/* records per system in log_sr */
+    int32_t reserved[3];   /* must be zero */
     /* RKC, mixed and two-float precisions: optional per-system proposals
      * [nsys] (device arrays, NaN = none) of the initial step and the
      * spectral-radius bound, e.g. from ode_mlp_propose.  A system with a
@@ -221,6 +224,33 @@ typedef struct {
      * together instead of at scattered steps.  The error test judges every
      * step either way. */
     double* carry;
+    /* RKC, ODE_PREC_FP64: optional training log of the spectral-radius
+     * estimates [nsys][log_sr_records][neq + 2] (device).  The power
+     * method's estimates of a system are numbered q = 0, 1, ... (q = 0 at
+     * the start, then the 25-step schedule and the estimates after
+     * rejections, Appendix); estimate q with q % log_sr_every == 0 writes
+     * record q / log_sr_every, if that is below log_sr_records:
+     * log max(|y_k|, 1e-30) of the state it was taken at, the parameter
+     * and log sigma (1.2 x the power method's value).  Records a system
+     * never reaches are left as they were (fill the array with NaN first).
+     *
+     * opts.mlp (ODE_PREC_F2 / ODE_PREC_F2_LEAN, RKC): a network trained to
+     * predict log sigma from those features (n_in = neq + 1), evaluated in
+     * the integration kernel wherever the power method would run -- at the
+     * start (unless sigma0 is given) and every 25 accepted steps, but never
+     * after a rejection.  The warp evaluates it for all its systems at such
+     * a point at once, on the tensor cores (BF16, FP32 accumulation).  Its
+     * bound replaces the power method when it is finite, positive, at
+     * least half the system's previous bound and its features lie inside
+     * the network's training box widened by 5 % of its width on each side;
+     * otherwise the power method runs.  Systems that took a bound from it
+     * carry ODE_ST_PROPOSED.  Where a system runs on more than one thread
+     * (warp or team mappings) the power method runs as without a network.
+     * The network must stay alive until the integration has finished.
+     * Errors: ODE_ERR_HANDLE for an unknown network, ODE_ERR_ARG for a
+     * network of another input count, ODE_ERR_UNSUPPORTED for another
+     * method or precision or a right-hand side without parameters. */
+    float* log_sr;
 } ode_opts;
 
 #define ODE_CARRY_CONTINUE 0
@@ -325,7 +355,7 @@ int rkc_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* par
  * output); opts->io and opts->codegen are ignored (the built-in kernels
  * are used, never run-time generated ones, since loading generated code
  * allocates), and so are opts->h0, sigma0, log_xy, cost, carry and
- * carry_mode.  A batch whose staged arrays need more than the
+ * carry_mode; opts->mlp and log_sr are rejected (ODE_ERR_ARG).  A batch whose staged arrays need more than the
  * scratch offers -- nsys * 8 * (neq + n_params) bytes plus 4 * nsys per
  * requested counter array, each rounded up to 256 bytes, against 16 MiB
  * minus the cursor and table -- is rejected with ODE_ERR_ARG before any GPU
@@ -404,8 +434,12 @@ int ode_ragged_plan_destroy(int64_t plan);
  * training set), outputs log h0, log sigma and log cost (right-hand-side
  * evaluations of the whole integration).  Training minimises squared error
  * on log h0 and log cost plus a pinball loss (quantile 0.9) on log sigma,
- * so sigma leans to over-estimates, with Adam.  Device arrays throughout,
- * rows contiguous (X [n][n_in], Y [n][3]); returns ODE_OK or ODE_ERR_*.
+ * so sigma leans to over-estimates, with Adam.  A NaN target is no
+ * target: it adds nothing to the loss, its gradient or the target's
+ * normalisation (so records of the spectral-radius log, which have a sigma
+ * target only, train beside the first-step records).  Device arrays
+ * throughout, rows contiguous (X [n][n_in], Y [n][3]); returns ODE_OK or
+ * ODE_ERR_*.
  * The parameter vector layout: W1 [64][n_in], b1 [64], W2 [64][64],
  * b2 [64], W3 [3][64], b3 [3]; the normalisation block: x_mean, x_scale,
  * x_min, x_max [ODE_MLP_MAX_IN each], y_mean, y_scale [3 each]. */
@@ -441,6 +475,10 @@ int ode_mlp_apply(int32_t mlp_handle, const float* X, int64_t n, float* out, voi
  * cost [nsys] (may be NULL): the predicted right-hand-side evaluations, NaN only where not finite */
 int ode_mlp_propose(int32_t mlp_handle, int64_t nsys, int32_t neq, const double* y0, const double* params,
                     float margin, float* h0, float* sigma0, float* cost, void* stream);
+/* outputs 0 and 1 (log h0, log sigma) for raw feature rows X [n][n_in], evaluated as the integration
+ * kernels evaluate the network in-kernel (opts.mlp): one warp per 32 rows, mma.sync products with BF16
+ * inputs, weights and activations and FP32 accumulation; out [n][2]; no box check */
+int ode_mlp_apply_warp(int32_t mlp_handle, const float* X, int64_t n, float* out, void* stream);
 /* host copies of the FP32 parameters [num_params] and the normalisation block (either may be NULL) */
 int ode_mlp_get_params(int32_t mlp_handle, float* params, float* norm);
 int ode_mlp_set_params(int32_t mlp_handle, const float* params, const float* norm);

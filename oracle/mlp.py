@@ -4,7 +4,9 @@ Plain numpy restatement of the network and losses the CUDA kernels train:
 inputs normalised by (x - mean) / scale, layers n_in -> 64 -> 64 -> 3 with
 SiLU, outputs (log h0, log sigma, log cost) de-normalised by
 y * scale + mean; loss = mean over rows of
-(p0 - t0)^2 + pinball_0.9(t1 - p1) + (p2 - t2)^2 on normalised targets.
+(p0 - t0)^2 + pinball_0.9(t1 - p1) + (p2 - t2)^2 on normalised targets,
+where a NaN target contributes no term (rows logged at spectral-radius
+points carry a sigma target only).
 The parameter vector layout: W1 [64][n_in], b1 [64], W2 [64][64], b2 [64],
 W3 [3][64], b3 [3]; the normalisation block x_mean, x_scale, x_min, x_max
 [33 each], y_mean, y_scale [3 each].
@@ -50,14 +52,19 @@ def silu_grad(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def forward(params, norm, X):
-    """De-normalised outputs (log h0, log sigma, log cost) for raw feature rows X."""
+def forward(params, norm, X, bf16_operands: bool = False):
+    """De-normalised outputs (log h0, log sigma, log cost) for raw feature rows X.
+
+    bf16_operands: round the normalised inputs and both layers' activations
+    to BF16 before each product, as a tensor-core evaluation with BF16
+    operands does (the weights are rounded by the caller)."""
     n_in = X.shape[1]
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in)
     xm, xs, ym, ys = unpack_norm(norm, n_in)
-    x = (np.asarray(X, np.float64) - xm) / xs
-    a1 = silu(x @ W1.T + b1)
-    a2 = silu(a1 @ W2.T + b2)
+    rnd = bf16_round if bf16_operands else (lambda v: v)
+    x = rnd((np.asarray(X, np.float64) - xm) / xs)
+    a1 = rnd(silu(x @ W1.T + b1))
+    a2 = rnd(silu(a1 @ W2.T + b2))
     return (a2 @ W3.T + b3) * ys + ym
 
 
@@ -74,11 +81,15 @@ def loss_and_grad(params, norm, X, Y):
     a2 = silu(z2)
     p = a2 @ W3.T + b3
     n = x.shape[0]
+    have = np.isfinite(t)  # a NaN target is no target
+    t = np.where(have, t, 0.0)
     r0 = p[:, 0] - t[:, 0]
     r1 = t[:, 1] - p[:, 1]
     r2 = p[:, 2] - t[:, 2]
-    loss = np.mean(r0 ** 2 + np.where(r1 > 0, TAU * r1, (TAU - 1.0) * r1) + r2 ** 2)
-    g = np.stack([2.0 * r0, np.where(r1 > 0, -TAU, 1.0 - TAU), 2.0 * r2], axis=1) / n
+    terms = np.stack([r0 ** 2, np.where(r1 > 0, TAU * r1, (TAU - 1.0) * r1), r2 ** 2], axis=1)
+    loss = np.sum(np.where(have, terms, 0.0)) / n
+    g = np.stack([2.0 * r0, np.where(r1 > 0, -TAU, 1.0 - TAU), 2.0 * r2], axis=1)
+    g = np.where(have, g, 0.0) / n
     gW3 = g.T @ a2
     gb3 = g.sum(axis=0)
     d2 = (g @ W3) * silu_grad(z2)

@@ -31,7 +31,7 @@ ODE_CODEGEN_AUTO, ODE_CODEGEN_OFF, ODE_CODEGEN_ON = 0, 1, 2
 EXPORTED = ["ode_rhs_register", "ode_rhs_release", "ode_rhs_prepare", "rkck_integrate", "rkc_integrate",
             "rkc_integrate_noalloc", "ode_last_error", "ode_version", "bode_fma_peak", "bode_stoich_bench",
             "ode_mlp_create", "ode_mlp_release", "ode_mlp_num_params", "ode_mlp_fit_normalization",
-            "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_propose", "ode_mlp_get_params",
+            "ode_mlp_train", "ode_mlp_gradient", "ode_mlp_apply", "ode_mlp_apply_warp", "ode_mlp_propose", "ode_mlp_get_params",
             "ode_mlp_set_params", "ode_ragged_plan_create", "ode_ragged_plan_launch", "ode_ragged_plan_info",
             "ode_ragged_plan_destroy", "ode_tuning_reset", "ode_cost_order", "ode_cost_order_i32",
             "ode_mapping_info"]
@@ -55,9 +55,10 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mapping", C.c_int32), ("max_attempts", C.c_int32),
                 ("block_size", C.c_int32), ("io", C.c_int32), ("sync", C.c_int32),
                 ("codegen", C.c_int32), ("cost_kind", C.c_int32), ("carry_mode", C.c_int32),
-                ("specrad", C.c_int32), ("reserved", C.c_int32 * 6),
+                ("specrad", C.c_int32), ("mlp", C.c_int32), ("log_sr_every", C.c_int32),
+                ("log_sr_records", C.c_int32), ("reserved", C.c_int32 * 3),
                 ("h0", C.c_void_p), ("sigma0", C.c_void_p), ("log_xy", C.c_void_p), ("cost", C.c_void_p),
-                ("carry", C.c_void_p)]
+                ("carry", C.c_void_p), ("log_sr", C.c_void_p)]
 
 
 class RaggedBatch(C.Structure):
@@ -224,12 +225,16 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
               y_out=None, counters: Counters | None = None, precision: int = ODE_PREC_FP64,
               mapping: int = ODE_MAP_AUTO, block_size: int = 0, max_attempts: int = 0,
               stream=None, sync: bool = False, codegen: int = ODE_CODEGEN_AUTO, h0=None, sigma0=None,
-              log_xy=None, cost=None, carry=None, carry_mode: int = 0, specrad: int = 0):
+              log_xy=None, cost=None, carry=None, carry_mode: int = 0, specrad: int = 0, mlp=None,
+              log_sr=None, log_sr_every: int = 1):
     """Call rkck_integrate / rkc_integrate.  y0 is [neq, nsys] (torch CUDA
     tensor for device io, numpy array for host io); returns y_out.  log_xy
     rows are [neq + 4]; cost (float32 [nsys], device) orders the batch
     longest-first; carry (float64 [carry_words(neq), nsys], device) is the
-    warm-restart state, read and written."""
+    warm-restart state, read and written.  mlp (an MLP or its handle) is
+    the network evaluated in-kernel at every spectral-radius point;
+    log_sr ([nsys, records, neq + 2] float32, device) the spectral-radius
+    training log, every log_sr_every-th estimate."""
     host = isinstance(y0, np.ndarray)
     nsys = int(y0.shape[1])
     if y_out is None:
@@ -243,6 +248,9 @@ def integrate(method: str, handle: int, y0, params, t0: float, tend: float, rtol
     o.cost_kind = 1 if cost is not None and str(getattr(cost, "dtype", "")).endswith("int32") else 0
     o.carry_mode = carry_mode
     o.specrad = specrad
+    o.mlp = 0 if mlp is None else int(getattr(mlp, "handle", mlp))
+    if log_sr is not None:
+        o.log_sr, o.log_sr_every, o.log_sr_records = _ptr(log_sr), log_sr_every, int(log_sr.shape[1])
     s = Stats()
     if counters is not None:
         s.n_accept, s.n_reject, s.n_rhs, s.n_specrad_iter, s.status = [
@@ -349,6 +357,13 @@ class MLP:
         import torch
         out = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
         _check(load().ode_mlp_apply(self.handle, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def apply_warp(self, X, stream=None):
+        """(log h0, log sigma) [n, 2] as the integration kernels evaluate them in-kernel."""
+        import torch
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        _check(load().ode_mlp_apply_warp(self.handle, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)))
         return out
 
     def propose(self, y0, params, margin: float = 0.05, stream=None, with_cost: bool = False):

@@ -27,7 +27,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
 # device headers compiled again at run time (NVRTC) for generated right-hand sides
 JIT_HEADERS = [os.path.join(CSRC, h) for h in (
     "common.cuh", "f2.cuh", "team.cuh", "xmath.cuh", "rkc_coef.cuh", "integrators.cuh", "integrators_f2.cuh",
-    "kernels.cuh", "rhs.cuh")]
+    "kernels.cuh", "rhs.cuh", "mlp.cuh", "mlp_warp.cuh")]
 
 
 def write_jit_sources() -> None:

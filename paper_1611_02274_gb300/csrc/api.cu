@@ -21,6 +21,10 @@
 
 using namespace bode;
 
+namespace bode {
+int mlp_packed_for(int32_t handle, int n_in, const MlpPacked** out);  // mlp.cu
+}  // namespace bode
+
 namespace {
 
 thread_local std::string g_err;
@@ -351,6 +355,7 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
     t.y_out = ws->tune_y;
     t.n_accept = t.n_reject = t.n_rhs = t.n_specrad = t.status = nullptr;
     t.log_xy = nullptr;
+    t.log_sr = nullptr;
     t.carry = nullptr;  // the timing runs neither read nor overwrite the caller's warm-restart state
     t.cursor = ws->cursors + kCursorRing;
     std::vector<std::pair<int, int>> cand;
@@ -407,8 +412,14 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     ode_opts opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 3; ++k)
         if (opts.reserved[k] != 0) return fail(ODE_ERR_ARG, "opts.reserved must be zero");
+    if (opts.log_sr && (method != kRkc || opts.precision != ODE_PREC_FP64))
+        return fail(ODE_ERR_UNSUPPORTED, "the spectral-radius log is written by the plain FP64 RKC");
+    if (opts.log_sr && opts.log_sr_records < 1) return fail(ODE_ERR_ARG, "log_sr needs log_sr_records >= 1");
+    if (opts.mlp && (method != kRkc || !prec_is_f2(opts.precision)))
+        return fail(ODE_ERR_UNSUPPORTED, "the in-kernel network is built for the two-float RKC forms");
+    if (opts.mlp && rhs.n_params < 1) return fail(ODE_ERR_UNSUPPORTED, "the network's last input is the parameter");
     if (opts.specrad < ODE_SPECRAD_POWER || opts.specrad > ODE_SPECRAD_POWER_CAPPED)
         return fail(ODE_ERR_ARG, "unknown specrad mode %d", opts.specrad);
     if (opts.carry_mode != ODE_CARRY_CONTINUE && opts.carry_mode != ODE_CARRY_RESTART)
@@ -429,7 +440,7 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     if (!(atol >= 0.0) || !std::isfinite(atol)) return fail(ODE_ERR_ARG, "atol must be finite and >= 0");
     if (!std::isfinite(t0) || !std::isfinite(tend) || tend < t0) return fail(ODE_ERR_ARG, "need finite t0 <= tend");
     if ((opts.h0 == nullptr) != (opts.sigma0 == nullptr)) return fail(ODE_ERR_ARG, "h0 and sigma0 go together");
-    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy || opts.cost || opts.carry))
+    if (opts.io == ODE_IO_HOST && (opts.h0 || opts.log_xy || opts.log_sr || opts.cost || opts.carry))
         return fail(ODE_ERR_ARG, "proposals, logs, cost ordering and warm-restart state need device io");
     if (opts.cost && nsys > INT32_MAX) return fail(ODE_ERR_ARG, "cost ordering takes at most 2^31 - 1 systems");
     if (nsys == 0) return ODE_OK;
@@ -501,6 +512,13 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     a.h0 = opts.h0;
     a.sigma0 = opts.sigma0;
     a.log_xy = opts.log_xy;
+    a.log_sr = opts.log_sr;
+    a.log_sr_every = opts.log_sr_every > 0 ? opts.log_sr_every : 1;
+    a.log_sr_records = opts.log_sr_records;
+    if (opts.mlp) {
+        rc = mlp_packed_for(opts.mlp, rhs.neq + 1, &a.mlp);
+        if (rc) return rc;
+    }
     a.carry = opts.carry;
     a.carry_mode = opts.carry_mode;
     a.specrad = opts.specrad;

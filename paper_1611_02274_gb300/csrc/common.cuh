@@ -136,6 +136,8 @@ struct BrussConst {
 };
 
 // Everything one batched launch needs besides the model.
+struct MlpPacked;  // mlp_warp.cuh
+
 struct BatchArgs {
     int64_t nsys;
     int32_t neq;
@@ -163,6 +165,14 @@ struct BatchArgs {
     const float* h0;
     const float* sigma0;
     float* log_xy;
+    // optional training log of the spectral-radius estimates (plain RKC):
+    // estimate q of a system (q = 0 at the start) with q % log_sr_every == 0
+    // goes to record q / log_sr_every if below log_sr_records
+    float* log_sr;
+    int32_t log_sr_every, log_sr_records;
+    // optional proposal network evaluated in-kernel at every spectral-radius
+    // point (two-float RKC, one thread per system; mlp_warp.cuh)
+    const MlpPacked* mlp;
     // ragged batches: the queue holds nsys entries index[k] (global system
     // numbers); system i's state starts at offset[i] (components contiguous)
     // and has neq_arr[i] unknowns and its own interval and tolerances.

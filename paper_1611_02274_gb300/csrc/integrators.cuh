@@ -44,7 +44,9 @@ struct ModelSmem<M, void_t_<decltype(M::SMEM_FLOATS)>> {
     static constexpr int value = M::SMEM_FLOATS;
 };
 
-enum : int { PH_DONE = 0, PH_F0, PH_SR, PH_TRIAL, PH_STAGE, PH_FINAL };
+// PH_PROPOSE: waiting for the warp's evaluation of the proposal network
+// (two-float RKC with an in-kernel network, mlp_warp.cuh)
+enum : int { PH_DONE = 0, PH_F0, PH_SR, PH_TRIAL, PH_STAGE, PH_FINAL, PH_PROPOSE };
 
 // Kahan-compensated state update (hi, lo) += d.
 __device__ __forceinline__ void kahan_add(float& hi, float& lo, float d) {
@@ -299,12 +301,14 @@ struct RkcF64 {
     int32_t n_acc, n_rej, n_rhs, n_sr, status, max_att, mmax, num_step, sr_step, n;
     int32_t phase, m, j, sr_iter;
     bool have_sigma, rejected, warm;
-    int64_t idx;  // system index (training log)
+    int64_t idx;    // system index (training logs)
+    int32_t n_est;  // spectral-radius estimates so far (training log)
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
         sys.load(ctx, tm, a.params[i], a.neq_of(i));
         n = a.neq_of(i);
         idx = i;
+        n_est = 0;
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
             const int c = sys.comp(tm, s);
@@ -495,7 +499,27 @@ struct RkcF64 {
         if (a.specrad == ODE_SPECRAD_POWER_CAPPED) sigma = fmin(sigma, sys.gershgorin(tm, yn));
         have_sigma = true;
         sr_step = num_step;
+        if (a.log_sr != nullptr) write_sr_log(a, tm);
+        n_est += 1;
         after_sr(a);
+    }
+
+    // training record of a spectral-radius estimate: features of the state
+    // it was taken at, the parameter and log sigma (n + 2 floats), for the
+    // estimates the log's stride selects
+    __device__ void write_sr_log(const BatchArgs& a, const TM& tm) const {
+        const int every = a.log_sr_every > 0 ? a.log_sr_every : 1;
+        if (n_est % every != 0 || n_est / every >= a.log_sr_records) return;
+        float* rec = a.log_sr + (idx * (int64_t)a.log_sr_records + n_est / every) * (int64_t)(n + 2);
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            if (c >= 0) rec[c] = (float)log(fmax(fabs(yn[s]), 1e-30));
+        }
+        if (tm.lane == 0) {
+            rec[n] = (float)a.params[idx];
+            rec[n + 1] = (float)log(sigma);
+        }
     }
 
     __device__ void after_sr(const BatchArgs& a) {

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "f2.cuh"
+#include "mlp_warp.cuh"
 
 namespace bode {
 
@@ -44,6 +45,8 @@ template <class Model, bool BK64 = false>
 struct RkcF2 {
     static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
     static constexpr int W = Model::W, P = Model::PER;
+    // the proposal network at the spectral-radius points (one thread per
+    // system, up to 32 components + the parameter)
     using R = F2;
     using TM = Team<W>;
     using HT = typename Pick<BK64, double, float>::type;
@@ -63,6 +66,12 @@ struct RkcF2 {
     // that no state pair stays live across the right-hand-side evaluation
     static constexpr int Y_SMEM = (W == 1 && P <= 32) ? 2 * (P | 1) : 0;
     static constexpr int SMEM_FLOATS = V_SMEM + C_SMEM + D2_SMEM + Y_SMEM + ModelSmem<Model>::value;
+    // the proposal network at the spectral-radius points (one thread per
+    // system with rows in shared memory: up to 32 components + the
+    // parameter, the BF16 features staged in the d_{j-2} row)
+    static constexpr int kMlpKs = (P + 1 + 15) / 16;
+    static constexpr bool kWarpPropose = W == 1 && P <= 32 && D2_SMEM >= 8 * kMlpKs && Y_SMEM > 0;
+    static constexpr int kJoin = 12;  // steps before its point a system joins a warp's network evaluation
     mutable F2 vreg[V_SMEM ? 1 : P];
     mutable F2 d2reg[D2_SMEM ? 1 : P];
     mutable F2 yreg[Y_SMEM ? 1 : P];
@@ -125,7 +134,7 @@ struct RkcF2 {
     }
     double t, tend;                   // BK64
     float remf, reml, tendf;          // FP32 scalars: remaining interval as a pair
-    HT hmax, hmin, h, h_old, sigma;
+    HT hmax, hmin, h, h_old, sigma, h_free;
     F2 hh;                            // the step size as a pair (exact for an FP32 h)
     float rtolf, atolf, c3_old, dynrm, sig;
     float4 chi, clo;                  // (mu_j, nu_j, mu~_j, gamma~_j), leading / trailing words
@@ -281,6 +290,25 @@ struct RkcF2 {
         } else {
             if (1.1f * h >= remf) h = remf;
         }
+        if constexpr (kWarpPropose) {
+            // with the network, the schedule counts from each system's last
+            // estimate, and a system within kJoin steps of its point takes
+            // the network's bound when another lane of its warp calls the
+            // network (propose_warp): the warp's points then coincide, even
+            // where the systems started at different times (work queue)
+            if (a.mlp != nullptr && a.specrad == ODE_SPECRAD_POWER) {
+                if (!have_sigma || rejected || num_step - sr_step >= kSpecradEvery) {
+                    if (!rejected) {  // never after a rejection: the power method
+                        phase = PH_PROPOSE;
+                        return;
+                    }
+                    sr_begin(tm);
+                    return;
+                }
+                after_sr(a);
+                return;
+            }
+        }
         if (!have_sigma || rejected || (num_step % kSpecradEvery == 0 && sr_step != num_step)) {
             if (a.specrad == ODE_SPECRAD_GERSHGORIN) {  // the bound replaces the power method
                 sigma = (HT)to_double(sys.gershgorin(tm, yp()));
@@ -293,6 +321,67 @@ struct RkcF2 {
             return;
         }
         after_sr(a);
+    }
+
+    // Learned spectral-radius bound for the lanes at a spectral-radius point
+    // (phase PH_PROPOSE), one warp-wide evaluation of the network on their
+    // current states: features log max(|y_k|, 1e-30) and the parameter,
+    // normalised.  The bound is taken when it is finite, positive, inside
+    // the training box and at least half the system's previous bound;
+    // otherwise the power method runs as without a network.  Lanes at the
+    // start of a step within kJoin steps of their own point join the
+    // evaluation (their step is set up again with the new bound; a joiner
+    // whose bound fails the checks keeps its old one).  Every lane of the
+    // warp calls (warp votes and mma.sync).
+    __device__ void propose_warp(const BatchArgs& a, const TM& tm, bool live, int64_t i) {
+        if constexpr (kWarpPropose) {
+            const MlpPacked* __restrict__ net = a.mlp;
+            if (net == nullptr) return;
+            const bool want = live && phase == PH_PROPOSE;
+            if (!__any_sync(0xffffffffu, want)) return;
+            const bool join = live && phase == PH_STAGE && j == 2 && have_sigma && !rejected &&
+                              num_step - sr_step >= kSpecradEvery - kJoin && num_step != sr_step;
+            const bool mine = want || join;
+            const unsigned take = __ballot_sync(0xffffffffu, mine);
+            // features into this lane's d_{j-2} row (unused at a step's
+            // start) as BF16, zero up to 16 KS; a rolled loop (cold code)
+            bool inside = true;
+            if (mine) {
+                uint16_t* fr = reinterpret_cast<uint16_t*>(d2s);
+                const float par = (float)a.params[i];
+#pragma unroll 1
+                for (int k = 0; k < 16 * kMlpKs; ++k) {
+                    float fx = 0.0f;
+                    if (k <= n) {
+                        const float raw = k < n ? __logf(fmaxf(fabsf(ys[k].hi), 1e-30f)) : par;
+                        fx = (raw - net->x_mean[k]) * net->x_iscale[k];
+                        inside = inside && raw >= net->x_lo[k] && raw <= net->x_hi[k];
+                    }
+                    fr[k] = to_bf16(fx);
+                }
+            }
+            __syncwarp();
+            float o0 = 0.0f, o1 = 0.0f;
+            mlp_warp_eval<kMlpKs>(net, take, reinterpret_cast<const uint32_t*>(d2s), D2_SMEM, o0, o1);
+            __syncwarp();  // every row read before a lane writes its row again
+            if (!mine) return;
+            const float sh = __expf(o1 * net->y_scale[1] + net->y_mean[1]);
+            const bool ok = inside && isfinite(sh) && sh > 0.0f && !(have_sigma && sh < 0.5f * (float)sigma);
+            if (!ok) {
+                if (want) sr_begin(tm);
+                return;
+            }
+            sigma = (HT)sh;
+            have_sigma = true;
+            sr_step = num_step;
+            status |= ODE_ST_PROPOSED;
+            if (want) {
+                after_sr(a);
+            } else {  // a joiner: the step's stage count and set-up again
+                h = h_free;
+                stage_begin(a);
+            }
+        }
     }
 
     // power method (Appendix) with the FP64 perturbation size
@@ -416,6 +505,7 @@ struct RkcF2 {
     }
 
     __device__ void stage_begin(const BatchArgs& a) {
+        h_free = h;  // before the stage-count cap (a joiner sets the step up again)
         m = 1 + (int)sqrt((HT)1.54 * h * sigma + (HT)1);
         if (m > mmax) {
             m = mmax;

@@ -47,6 +47,23 @@ __device__ __forceinline__ bool step_hold(const Method& m, bool live) {
     }
 }
 
+// In-kernel proposal network (methods with kWarpPropose): a warp-wide
+// evaluation for the lanes at a spectral-radius point, before the warp's
+// next right-hand-side evaluation.  Every lane calls.
+template <class M, class = void>
+struct WarpPropose {
+    static constexpr bool value = false;
+};
+template <class M>
+struct WarpPropose<M, void_t_<decltype(M::kWarpPropose)>> {
+    static constexpr bool value = M::kWarpPropose;
+};
+template <class Method>
+__device__ __forceinline__ void warp_propose(Method& m, const BatchArgs& a, const Team<Method::W>& tm, bool live,
+                                             int64_t i) {
+    if constexpr (WarpPropose<Method>::value) m.propose_warp(a, tm, live, i);
+}
+
 // Register budget of a method's kernels: Method::kMaxRegs when it declares
 // one, else 255 (the launch bounds alone decide).  Every block size stays
 // launchable (168 registers x 256 threads fit in an SM's register file).
@@ -83,6 +100,7 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__
         for (;;) {
             const bool live = in_range && !m.done();
             if (!__any_sync(0xffffffffu, live)) break;
+            warp_propose(m, a, tm, live, i);       // every lane takes part
             const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
             if (live && !hold) {
                 R tx;
@@ -135,6 +153,7 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__
     next();
     R x[P], f[P];
     while (__any_sync(0xffffffffu, live)) {
+        warp_propose(m, a, tm, live, i);       // every lane takes part
         const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
         if (live && !hold) {
             R tx;

@@ -20,12 +20,19 @@
 //   k_adam        one thread per parameter (bias-corrected Adam), writes the
 //                 FP32 master and its BF16 copy, clears the gradient.
 //   k_mlp_apply   one thread per sample, weights in shared memory.
+//   k_pack        the inference copy the integration kernels evaluate
+//                 in-kernel (mlp_warp.cuh): B fragments of mma.m16n8k16 in
+//                 fragment-major order, biases, normalisation and the box.
+//
+// A NaN target is no target (no loss, no gradient, not in the statistics),
+// so records with a spectral-radius target only train beside full ones.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -36,6 +43,7 @@
 
 #include "batchode.h"
 #include "mlp.cuh"
+#include "mlp_warp.cuh"
 
 namespace bode {
 int set_last_error(int code, const char* msg);
@@ -62,7 +70,10 @@ struct Mlp {
     MlpNorm norm;
     bool has_norm = false;
     int64_t step = 0;
+    MlpPacked* packed = nullptr;  // inference copy for the integration kernels
 };
+
+constexpr float kBoxMargin = 0.05f;  // in-kernel proposals: the training box widened by 5 % of its width
 
 std::mutex g_mu;
 std::map<int32_t, Mlp> g_mlps;
@@ -89,6 +100,7 @@ __device__ void load_weights(const __nv_bfloat16* w16, float* sw, int np) {
 }
 
 __device__ __forceinline__ float loss_grad(int o, float p, float t, float* loss) {
+    if (isnan(t)) return 0.0f;  // no target
     if (o != 1) {  // squared error: log h0, log cost
         const float r = p - t;
         *loss += r * r;
@@ -282,25 +294,79 @@ __global__ void k_mlp_propose(const __nv_bfloat16* w16, const MlpNorm norm, int 
     }
 }
 
-// Per-block partial sums / extrema of the feature and target columns.
+// Per-block partial sums / extrema / counts of the finite values of the
+// feature and target columns.
 __global__ void k_stats(const float* X, const float* Y, int64_t n, int n_in, double* part) {
     const int F = n_in + kMlpOut;
     const int f = threadIdx.x;  // one column per thread
     if (f >= F) return;
-    double s = 0.0, ss = 0.0;
+    double s = 0.0, ss = 0.0, cnt = 0.0;
     float lo = 3.0e38f, hi = -3.0e38f;
     for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
         const float x = f < n_in ? X[r * n_in + f] : Y[r * kMlpOut + (f - n_in)];
+        if (!isfinite(x)) continue;
         s += x;
         ss += (double)x * x;
+        cnt += 1.0;
         lo = fminf(lo, x);
         hi = fmaxf(hi, x);
     }
-    double* p = part + ((int64_t)blockIdx.x * F + f) * 4;
+    double* p = part + ((int64_t)blockIdx.x * F + f) * 5;
     p[0] = s;
     p[1] = ss;
     p[2] = lo;
     p[3] = hi;
+    p[4] = cnt;
+}
+
+// The inference copy: B fragments (lane l of n-tile nt, k-step ks holds
+// W[8 nt + l / 4][16 ks + 2 (l % 4) + {0, 1, 8, 9}], BF16 pairs, the lower
+// column in the low half), zero outside the layer; biases as the BF16
+// values the other kernels use, widened to FP32.
+__global__ void k_pack(const __nv_bfloat16* __restrict__ w16, int n_in, MlpPacked* out) {
+    const uint16_t* w = reinterpret_cast<const uint16_t*>(w16);
+    auto el = [&](int off, int rows, int cols, int r, int c) -> uint32_t {
+        return (r < rows && c < cols) ? (uint32_t)w[off + r * cols + c] : 0u;
+    };
+    auto frag = [&](int off, int rows, int cols, int KS, int idx) {
+        const int nt = idx / (KS * 32), ks = (idx / 32) % KS, l = idx % 32;
+        const int r = 8 * nt + (l >> 2), c = 16 * ks + 2 * (l & 3);
+        return make_uint2(el(off, rows, cols, r, c) | (el(off, rows, cols, r, c + 1) << 16),
+                          el(off, rows, cols, r, c + 8) | (el(off, rows, cols, r, c + 9) << 16));
+    };
+    for (int k = threadIdx.x; k < 8 * kMlpWarpKs1 * 32; k += blockDim.x)
+        out->w1[k] = frag(mlp_w1(n_in), kH, n_in, kMlpWarpKs1, k);
+    for (int k = threadIdx.x; k < 8 * 4 * 32; k += blockDim.x) out->w2[k] = frag(mlp_w2(n_in), kH, kH, 4, k);
+    for (int k = threadIdx.x; k < 4 * 32; k += blockDim.x) out->w3[k] = frag(mlp_w3(n_in), kMlpOut, kH, 4, k);
+    for (int k = threadIdx.x; k < kH; k += blockDim.x) {
+        out->b1[k] = __bfloat162float(w16[mlp_b1(n_in) + k]);
+        out->b2[k] = __bfloat162float(w16[mlp_b2(n_in) + k]);
+    }
+    if (threadIdx.x < 8) out->b3[threadIdx.x] = threadIdx.x < kMlpOut ? __bfloat162float(w16[mlp_b3(n_in) + threadIdx.x]) : 0.0f;
+}
+
+// Outputs 0 and 1 of raw feature rows through the in-kernel evaluation:
+// one warp per 32 rows (KS k-steps of 16 inputs), the BF16 features staged
+// in a shared-memory row per thread as the integration kernels stage them.
+template <int KS>
+__global__ void __launch_bounds__(128) k_mlp_apply_warp(const MlpPacked* __restrict__ net, const float* __restrict__ X,
+                                                         int64_t n, float* __restrict__ out) {
+    constexpr int kStride = 8 * KS + 1;  // words per row (odd: fewer bank conflicts)
+    __shared__ uint32_t rows[128 * kStride];
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool have = r < n;
+    const unsigned take = __ballot_sync(0xffffffffu, have);
+    const int n_in = net->n_in;
+    uint32_t* mine = rows + threadIdx.x * kStride;
+    uint16_t* fr = reinterpret_cast<uint16_t*>(mine);
+    for (int k = 0; k < 16 * KS; ++k)
+        fr[k] = to_bf16((have && k < n_in) ? (X[r * n_in + k] - net->x_mean[k]) * net->x_iscale[k] : 0.0f);
+    __syncwarp();
+    float o0 = 0.0f, o1 = 0.0f;
+    mlp_warp_eval<KS>(net, take, mine, kStride, o0, o1);
+    if (!have) return;
+    out[2 * r] = o0 * net->y_scale[0] + net->y_mean[0];
+    out[2 * r + 1] = o1 * net->y_scale[1] + net->y_mean[1];
 }
 
 size_t grad_smem(int n_in) { return sizeof(float) * (mlp_nparams(n_in) + kMlpMaxIn + 3 * kH + kMlpOut); }
@@ -313,6 +379,33 @@ int get(int32_t h, Mlp** out) {
     return ODE_OK;
 }
 
+// Rebuilds the inference copy from the BF16 weights and the normalisation
+// (after every change of either); synchronous on s.
+int refresh_packed(Mlp& net, cudaStream_t s) {
+    if (!net.packed) return ODE_OK;
+    k_pack<<<1, 256, 0, s>>>(net.w16, net.n_in, net.packed);
+    MlpPacked h;  // the host-built part: normalisation and the widened box
+    std::memset(&h, 0, sizeof(h));
+    for (int k = 0; k < kMlpMaxIn; ++k) {
+        h.x_mean[k] = net.norm.x_mean[k];
+        h.x_iscale[k] = 1.0f / net.norm.x_scale[k];
+        const float w = net.norm.x_max[k] - net.norm.x_min[k];
+        h.x_lo[k] = net.norm.x_min[k] - kBoxMargin * w;
+        h.x_hi[k] = net.norm.x_max[k] + kBoxMargin * w;
+    }
+    for (int k = 0; k < kMlpOut; ++k) {
+        h.y_mean[k] = net.norm.y_mean[k];
+        h.y_scale[k] = net.norm.y_scale[k];
+    }
+    h.n_in = net.n_in;
+    const size_t off = offsetof(MlpPacked, x_mean);
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(net.packed) + off, reinterpret_cast<const char*>(&h) + off,
+                                    sizeof(MlpPacked) - off, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? ODE_OK : cuda_fail(e, "network inference copy");
+}
+
 // gradient of the summed loss over n rows (device X, Y) into net.grad / net.loss
 int run_grad(Mlp& net, const float* X, const float* Y, const int32_t* perm, int64_t n, cudaStream_t s) {
     const int per_block = 32;
@@ -323,6 +416,20 @@ int run_grad(Mlp& net, const float* X, const float* Y, const int32_t* perm, int6
 }
 
 }  // namespace
+
+namespace bode {
+// The inference copy of network `handle` for an integration whose systems
+// have n_in - 1 components (ODE_ERR_HANDLE / ODE_ERR_ARG otherwise).
+int mlp_packed_for(int32_t handle, int n_in, const MlpPacked** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Mlp* net;
+    int rc = get(handle, &net);
+    if (rc) return rc;
+    if (net->n_in != n_in) return fail(ODE_ERR_ARG, "network takes %d inputs, the systems have %d + 1", net->n_in, n_in - 1);
+    *out = net->packed;
+    return ODE_OK;
+}
+}  // namespace bode
 
 extern "C" {
 
@@ -353,6 +460,7 @@ int ode_mlp_create(int32_t n_in, uint64_t seed, int32_t* handle) {
     if (e == cudaSuccess) e = cudaMalloc(&net.v, nb);
     if (e == cudaSuccess) e = cudaMalloc(&net.grad, nb);
     if (e == cudaSuccess) e = cudaMalloc(&net.loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net.packed, sizeof(MlpPacked));
     if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "mlp allocation failed");
     cudaMemcpy(net.master, w.data(), nb, cudaMemcpyHostToDevice);
     cudaMemset(net.m, 0, nb);
@@ -371,6 +479,7 @@ int ode_mlp_create(int32_t n_in, uint64_t seed, int32_t* handle) {
     }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "mlp initialisation");
+    if (int rc = refresh_packed(net, nullptr)) return rc;
     std::lock_guard<std::mutex> lk(g_mu);
     *handle = g_next++;
     g_mlps[*handle] = net;
@@ -389,6 +498,7 @@ int ode_mlp_release(int32_t handle) {
     cudaFree(net->v);
     cudaFree(net->grad);
     cudaFree(net->loss);
+    cudaFree(net->packed);
     g_mlps.erase(handle);
     return ODE_OK;
 }
@@ -404,25 +514,32 @@ int ode_mlp_fit_normalization(int32_t handle, const float* X, const float* Y, in
     const int blocks = 1024;
     double* part = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMalloc(&part, sizeof(double) * blocks * F * 4);
+    cudaError_t e = cudaMalloc(&part, sizeof(double) * blocks * F * 5);
     if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "statistics buffer");
     k_stats<<<blocks, 64, 0, s>>>(X, Y, n, net->n_in, part);
-    std::vector<double> h((size_t)blocks * F * 4);
+    std::vector<double> h((size_t)blocks * F * 5);
     e = cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(part);
     if (e != cudaSuccess) return cuda_fail(e, "statistics");
     for (int f = 0; f < F; ++f) {
-        double sum = 0, sq = 0, lo = 3e38, hi = -3e38;
+        double sum = 0, sq = 0, lo = 3e38, hi = -3e38, cnt = 0;
         for (int b = 0; b < blocks; ++b) {
-            const double* p = &h[((size_t)b * F + f) * 4];
+            const double* p = &h[((size_t)b * F + f) * 5];
             sum += p[0];
             sq += p[1];
             lo = std::min(lo, p[2]);
             hi = std::max(hi, p[3]);
+            cnt += p[4];
         }
-        const double mean = sum / n;
-        const double sd = std::sqrt(std::max(sq / n - mean * mean, 0.0));
+        if (cnt < 2) {  // no statistics: identity normalisation, unbounded box
+            sum = sq = 0;
+            cnt = 1;
+            lo = -3e38;
+            hi = 3e38;
+        }
+        const double mean = sum / cnt;
+        const double sd = std::sqrt(std::max(sq / cnt - mean * mean, 0.0));
         const float scale = (float)(sd > 1e-12 ? sd : 1.0);
         if (f < net->n_in) {
             net->norm.x_mean[f] = (float)mean;
@@ -435,7 +552,7 @@ int ode_mlp_fit_normalization(int32_t handle, const float* X, const float* Y, in
         }
     }
     net->has_norm = true;
-    return ODE_OK;
+    return refresh_packed(*net, s);
 }
 
 int ode_mlp_gradient(int32_t handle, const float* X, const float* Y, int64_t n, float* grad_out, float* loss_out,
@@ -509,7 +626,7 @@ int ode_mlp_train(int32_t handle, const float* X, const float* Y, int64_t n, con
         if (loss_history) loss_history[ep] = l / (float)n;
     }
     cudaFree(perm);
-    return ODE_OK;
+    return refresh_packed(*net, s);
 }
 
 int ode_mlp_apply(int32_t handle, const float* X, int64_t n, float* out, void* stream) {
@@ -573,7 +690,28 @@ int ode_mlp_set_params(int32_t handle, const float* params, const float* norm) {
         std::memcpy(&net->norm, norm, sizeof(MlpNorm));
         net->has_norm = true;
     }
-    return ODE_OK;
+    return refresh_packed(*net, nullptr);
+}
+
+int ode_mlp_apply_warp(int32_t handle, const float* X, int64_t n, float* out, void* stream) {
+    clear_last_error();
+    std::lock_guard<std::mutex> lk(g_mu);
+    Mlp* net;
+    int rc = get(handle, &net);
+    if (rc) return rc;
+    if (!X || !out || n < 0) return fail(ODE_ERR_ARG, "need device X and out");
+    if (n == 0) return ODE_OK;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ks = (net->n_in + 15) / 16;
+    if (ks == 1)
+        k_mlp_apply_warp<1><<<blocks, 128, 0, s>>>(net->packed, X, n, out);
+    else if (ks == 2)
+        k_mlp_apply_warp<2><<<blocks, 128, 0, s>>>(net->packed, X, n, out);
+    else
+        k_mlp_apply_warp<3><<<blocks, 128, 0, s>>>(net->packed, X, n, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ODE_OK : cuda_fail(e, "mlp warp apply");
 }
 
 int ode_mlp_num_params(int32_t n_in) { return n_in >= 1 && n_in <= kMlpMaxIn ? mlp_nparams(n_in) : -1; }

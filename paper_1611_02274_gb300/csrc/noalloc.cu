@@ -85,6 +85,8 @@ extern "C" int rkc_integrate_noalloc(int32_t handle, int64_t nsys, const double*
     if (opts_in) opts = *opts_in;
     if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_MIXED_LEAN)
         return fail(ODE_ERR_ARG, "precision %d is not built for the allocation-free entry point", opts.precision);
+    if (opts.mlp || opts.log_sr)
+        return fail(ODE_ERR_ARG, "networks and the spectral-radius log are not taken by the allocation-free entry point");
     if (opts.specrad < ODE_SPECRAD_POWER || opts.specrad > ODE_SPECRAD_POWER_CAPPED)
         return fail(ODE_ERR_ARG, "unknown specrad mode %d", opts.specrad);
     switch (rhs.kind) {  // every built-in family; decided before any GPU work

@@ -218,6 +218,7 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
     std::memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
     if (o.precision < ODE_PREC_FP64 || o.precision > ODE_PREC_MIXED_LEAN) return fail(ODE_ERR_ARG, "unknown precision");
+    if (o.mlp || o.log_sr) return fail(ODE_ERR_ARG, "networks and the spectral-radius log are not taken by ragged plans");
     if (o.mapping < ODE_MAP_AUTO || o.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping");
     ode_stats st;
     std::memset(&st, 0, sizeof(st));

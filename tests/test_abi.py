@@ -70,7 +70,7 @@ def test_integrate_argument_errors_before_any_launch():
     # an empty batch is a successful no-op
     B.integrate("rkck", h, np.zeros((2, 0)), np.zeros((1, 0)), 0.0, 1.0, 1e-6, 1e-9)
     o = B.Opts()
-    o.reserved[3] = 1
+    o.reserved[2] = 1
     rc = B.load().rkck_integrate(h, 4, C.c_void_p(y.ctypes.data), C.c_void_p(p.ctypes.data), 0.0, 1.0,
                                  1e-6, 1e-9, C.byref(o), C.c_void_p(y.ctypes.data), None, None)
     assert rc == B.ODE_ERR_ARG
@@ -89,6 +89,37 @@ def test_integrate_argument_errors_before_any_launch():
     assert L.ode_cost_order(None, -1, None, None) == B.ODE_ERR_ARG
     assert L.ode_cost_order(None, 5, None, None) == B.ODE_ERR_ARG
     assert L.ode_cost_order(None, 0, None, None) == B.ODE_OK
+
+
+def test_network_and_log_options_are_checked_before_any_launch():
+    # the in-kernel network is for the two-float RKC forms, the
+    # spectral-radius log for the plain FP64 RKC; both refused elsewhere
+    # before any device work (no GPU needed to see it)
+    lib = B.load()
+    w = W.massaction(4, seed=0)
+    h = B.register_workload(w)
+    y, p = np.ascontiguousarray(w.y0), np.ascontiguousarray(w.params)
+    args = (h, 4, C.c_void_p(y.ctypes.data), C.c_void_p(p.ctypes.data), w.t0, w.tend, w.rtol, w.atol)
+    out = np.empty_like(y)
+    for fn, prec, field, code in ((lib.rkc_integrate, B.ODE_PREC_FP64, "mlp", B.ODE_ERR_UNSUPPORTED),
+                                  (lib.rkck_integrate, B.ODE_PREC_F2_LEAN, "mlp", B.ODE_ERR_UNSUPPORTED),
+                                  (lib.rkc_integrate, B.ODE_PREC_MIXED, "mlp", B.ODE_ERR_UNSUPPORTED),
+                                  (lib.rkc_integrate, B.ODE_PREC_F2_LEAN, "log_sr", B.ODE_ERR_UNSUPPORTED),
+                                  (lib.rkc_integrate, B.ODE_PREC_FP64, "log_sr", B.ODE_ERR_ARG)):
+        o = B.Opts()
+        o.precision = prec
+        o.io = B.ODE_IO_HOST
+        if field == "mlp":
+            o.mlp = 7
+        else:
+            o.log_sr = C.c_void_p(out.ctypes.data)  # records 0: refused
+        rc = fn(*args, C.byref(o), C.c_void_p(out.ctypes.data), None, None)
+        assert rc == code, (field, prec, rc)
+    o = B.Opts()
+    o.mlp = 7
+    rc = lib.rkc_integrate_noalloc(*args, C.byref(o), C.c_void_p(out.ctypes.data), None, None)
+    assert rc == B.ODE_ERR_ARG
+    B.release(h)
 
 
 def test_generated_network_kernels_compile():

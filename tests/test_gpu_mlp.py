@@ -113,54 +113,75 @@ def test_training_log_records_the_first_step():
 
 
 def test_proposal_pipeline_gain(record_property):
+    """The learned proposal on the chosen (two-float) form: trained on a
+    held-out FP64 run, it proposes each system's start and predicts its
+    cost; the batch taken longest-first by that cost runs faster than the
+    batch without the proposal (timed with CUDA events, proposal and
+    ordering passes inside the timed region), at unchanged accuracy."""
     import torch
-    # train on held-out seeds
-    X, Y = log_pairs(W.massaction(1 << 15, seed=1001))
+    X, Y = log_pairs(W.massaction(1 << 16, seed=1001))
     net = B.MLP(14, seed=0)
     net.fit_normalization(X, Y)
-    hist = net.train(X, Y, epochs=30, batch=1024, lr=3e-3, seed=0)
+    hist = net.train(X, Y, epochs=24, batch=4096, lr=2e-3, seed=0)
     assert hist[-1] < hist[0]
-    # evaluate on another seed, with and without the proposal
-    w = W.massaction(8192, seed=5)
+    w = W.massaction(1 << 18, seed=5)   # 262,144 systems: 4.5 waves of resident blocks
     h = B.register_workload(w)
     y0 = torch.from_numpy(w.y0).cuda()
     p = torch.from_numpy(w.params).cuda()
-    h0, s0, cost = net.propose(y0, p, with_cost=True)
-    runs = {}
-    for name, kw in (("plain", {}), ("proposal", dict(h0=h0, sigma0=s0)),
-                     ("proposal_ordered", dict(h0=h0, sigma0=s0, cost=cost))):
+    yout = torch.empty_like(y0)
+    CH = B.ODE_PREC_F2_LEAN
+    B.prepare(h, "rkc", CH)
+
+    def step(mode, cnt=None):
+        kw = {}
+        if mode != "plain":
+            h0, s0, c = net.propose(y0, p, with_cost=True)
+            kw = dict(h0=h0, sigma0=s0)
+            if mode == "proposal_ordered":
+                kw["cost"] = c
+        B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=cnt, precision=CH,
+                    mapping=B.ODE_MAP_THREAD, **kw)
+
+    ms, runs = {}, {}
+    for mode in ("plain", "proposal", "proposal_ordered"):
+        step(mode)
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(mode)
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        ms[mode] = min(t)
         cnt = B.counters_like(w.nsys, "cuda")
-        y = B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, counters=cnt,
-                        precision=B.ODE_PREC_MIXED_LEAN, sync=True, **kw)
-        runs[name] = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
-        runs[name]["y"] = y.cpu().numpy()
+        step(mode, cnt)
+        torch.cuda.synchronize()
+        runs[mode] = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
+        runs[mode]["y"] = yout[:, :4096].cpu().numpy()
+    c_pred = np.log(net.propose(y0, p, with_cost=True)[2].cpu().numpy())
     B.release(h)
     net.release()
-    ref = O.integrate_workload(w)
+    ref = O.integrate_workload(W.subset(w, np.arange(4096)))
     pr, pl = runs["proposal"], runs["plain"]
     # taking the systems longest-first changes nothing but the time
     for k in pr:
         np.testing.assert_array_equal(runs["proposal_ordered"][k], pr[k], err_msg=k)
-    # the predicted cost tracks the actual one
-    c_pred = np.log(cost.cpu().numpy())
-    c_true = np.log(pr["n_rhs"].astype(np.float64))
-    corr = float(np.corrcoef(c_pred, c_true)[0, 1])
-    record_property("cost_corr", corr)
-    print("log-cost correlation", corr)
-    assert corr > 0.8
+    corr = float(np.corrcoef(c_pred, np.log(pr["n_rhs"].astype(np.float64)))[0, 1])
     used = np.mean((pr["status"] & B.ODE_ST_PROPOSED) != 0)
-    runs.pop("proposal_ordered")
-    rej = {k: float(np.sum(r["n_reject"]) / np.sum(r["n_accept"] + r["n_reject"])) for k, r in runs.items()}
-    rhs = {k: float(np.mean(r["n_rhs"])) for k, r in runs.items()}
-    sr = {k: float(np.mean(r["n_specrad_iter"])) for k, r in runs.items()}
     err = {k: float(np.quantile(rel_err(r["y"], ref.y, w.atol), 0.999)) for k, r in runs.items()}
-    for key, val in (("proposal_used", used), ("reject_rate", rej), ("mean_rhs", rhs), ("mean_specrad_iter", sr),
+    speedup = ms["plain"] / ms["proposal_ordered"]
+    for key, val in (("ms", ms), ("speedup", speedup), ("cost_corr", corr), ("proposal_used", used),
                      ("p999_err", err)):
         record_property(key, val)
-    print("proposal used", used, "reject rate", rej, "mean RHS", rhs, "mean power iterations", sr, "p99.9 err", err)
-    assert used > 0.9
+    print("ms", ms, "speed-up", speedup, "log-cost correlation", corr, "used", used, "p99.9 err", err)
+    assert corr > 0.9
+    assert used > 0.99
     assert ((pr["status"] & 0xFF) == 0).all()
     # the initial power method and trial step are skipped where the proposal is used
-    assert sr["proposal"] < sr["plain"]
-    # accuracy is kept: the error test still judges every step
-    assert err["proposal"] < 5 * err["plain"] + 1e-6
+    assert pr["n_specrad_iter"].mean() < pl["n_specrad_iter"].mean()
+    # accuracy is kept within the chosen form's bar: the error test still judges every step
+    assert err["proposal"] <= 1e-5
+    # the pipeline pays: longest-first by the predicted cost
+    assert speedup >= 1.1, ms

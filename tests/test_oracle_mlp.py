@@ -85,3 +85,51 @@ def test_bf16_rounding():
     r = M.bf16_round(x)
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125   # ties to even, then round up
     assert abs(r[3] / -3.14159 - 1) < 2 ** -8
+
+
+def entry_term(params, norm, X, Y, r, c):
+    """Loss term of target (r, c), straight from the definition on the
+    network's normalised output."""
+    p = (M.forward(params, norm, X[r:r + 1])[0, c] - norm[YM + c]) / norm[YS + c]
+    t = (Y[r, c] - norm[YM + c]) / norm[YS + c]
+    if c == 1:
+        d = t - p
+        return M.TAU * d if d > 0 else (M.TAU - 1.0) * d
+    return (p - t) ** 2
+
+
+def test_nan_target_drops_its_term():
+    # a NaN target adds nothing: the mean loss loses exactly that entry's term
+    params, norm, X, Y = random_case(n=6, seed=3)
+    n = X.shape[0]
+    loss, _ = M.loss_and_grad(params, norm, X, Y)
+    Y2 = Y.copy()
+    masked = [(0, 0), (2, 2), (3, 0), (3, 2), (5, 1)]
+    for r, c in masked:
+        Y2[r, c] = np.nan
+    loss2, g2 = M.loss_and_grad(params, norm, X, Y2)
+    drop = sum(entry_term(params, norm, X, Y, r, c) for r, c in masked)
+    assert loss2 * n == pytest.approx(loss * n - drop, rel=1e-12, abs=1e-12)
+    assert np.all(np.isfinite(g2))
+    # a row with no target at all adds neither loss nor gradient
+    Y3 = Y.copy()
+    Y3[4, :] = np.nan
+    l_all, g_all = M.loss_and_grad(params, norm, X, Y3)
+    keep = [0, 1, 2, 3, 5]
+    l_sub, g_sub = M.loss_and_grad(params, norm, X[keep], Y[keep])
+    assert l_all * n == pytest.approx(l_sub * len(keep), rel=1e-12)
+    np.testing.assert_allclose(g_all * n, g_sub * len(keep), rtol=1e-10, atol=1e-14)
+
+
+def test_masked_gradient_matches_finite_differences():
+    params, norm, X, Y = random_case(n=5, seed=4)
+    Y[1, 0] = Y[2, 2] = Y[3, 0] = Y[3, 2] = np.nan  # spectral-radius records: sigma target only
+    _, g = M.loss_and_grad(params, norm, X, Y)
+    rng = np.random.default_rng(5)
+    eps = 1e-6
+    for k in rng.choice(params.size, 40, replace=False):
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += eps
+        p2[k] -= eps
+        fd = (M.loss_and_grad(p1, norm, X, Y)[0] - M.loss_and_grad(p2, norm, X, Y)[0]) / (2 * eps)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-8), k
