@@ -152,17 +152,28 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__
     };
     next();
     R x[P], f[P];
+    // The evaluation loop runs until a system of the warp finishes; the
+    // switch to the next systems runs outside it, before the next
+    // evaluation (the same order of events as switching inside it).  Kept
+    // apart, the loop does not carry the register demand of the set-up code:
+    // with the switch inside, the compiler spilled the method's state around
+    // it in every iteration.
     while (__any_sync(0xffffffffu, live)) {
-        warp_propose(m, a, tm, live, i);       // every lane takes part
-        const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
-        if (live && !hold) {
-            R tx;
-            m.point(x, tx);
-            m.sys.rhs(tm, tx, x, f);
-            if (m.consume(a, tm, x, f)) {
-                m.store(a, tm, i);
-                next();
+        bool fin = false;
+        for (;;) {
+            warp_propose(m, a, tm, live, i);       // every lane takes part
+            const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
+            if (live && !hold) {
+                R tx;
+                m.point(x, tx);
+                m.sys.rhs(tm, tx, x, f);
+                fin = m.consume(a, tm, x, f);
             }
+            if (__any_sync(0xffffffffu, fin)) break;
+        }
+        if (fin) {
+            m.store(a, tm, i);
+            next();
         }
     }
 }
