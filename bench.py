@@ -55,13 +55,25 @@ L2_FLUSH_BYTES = 256 << 20
 
 # The precision forms of rkc_integrate (ODE_PREC_*), their kernels and the
 # arithmetic each computes in.
-FORMS = {"f2_lean": 4, "f2": 3, "mixed_lean": 2, "mixed_spec_split": 1, "plain_fp64": 0}
-FORM_KERNELS = {"f2_lean": "RkcF2<JitMass, false>", "f2": "RkcF2<JitMass, true>",
+FORMS = {"f2_lean_learned": 4, "f2_lean": 4, "f2": 3, "mixed_lean": 2, "mixed_spec_split": 1, "plain_fp64": 0}
+# forms whose step also runs the learned proposal: the network's pre-pass
+# (spectral-radius bound and cost per system, the Euler trial still setting
+# the first step) and the longest-first order by the predicted cost
+LEARNED_FORMS = {"f2_lean_learned"}
+# our kernel launches per step: the integration kernel; for the generated
+# two-float forms the rate-constant prologue; for the learned forms the
+# proposal pre-pass and the four kernels of the cost order
+LAUNCHES = {"f2_lean_learned": 7, "f2_lean": 2, "f2": 2, "mixed_lean": 1, "mixed_spec_split": 1, "plain_fp64": 1}
+FORM_KERNELS = {"f2_lean_learned": "RkcF2<JitMass, false>", "f2_lean": "RkcF2<JitMass, false>",
+                "f2": "RkcF2<JitMass, true>",
                 "mixed_lean": "RkcMixed<JitMass, false>", "mixed_spec_split": "RkcMixed<JitMass, true>",
                 "plain_fp64": "RkcF64<JitMass>"}
-FORM_DTYPES = {"f2_lean": "f32x2", "f2": "f32x2+f64", "mixed_lean": "f32", "mixed_spec_split": "f32+f64",
+FORM_DTYPES = {"f2_lean_learned": "f32x2", "f2_lean": "f32x2", "f2": "f32x2+f64", "mixed_lean": "f32", "mixed_spec_split": "f32+f64",
                "plain_fp64": "f64"}
 FORM_TEXT = {
+    "f2_lean_learned": "the two-float form (f2_lean) with the learned proposal: a BF16 network's pre-pass gives "
+                       "each system's initial spectral-radius bound and predicted cost, and the batch runs "
+                       "longest-first by that cost (network trained before timing on held-out seeds)",
     "f2_lean": "two-float (FP32 pair, ~48-bit) state, stages, evaluation points and RHS; FP32 step size, spectral "
                "radius and error norm; remaining interval as an FP32 pair; FP64-built coefficients as pairs",
     "f2": "two-float state, stages, evaluation points and RHS; FP64 time, step size, spectral radius and error-norm "
@@ -74,10 +86,8 @@ FORM_TEXT = {
 # DRAM bytes (read + write) per system of each form's generated kernel, from
 # one ncu capture of k_static on 262,144 systems of this workload; traffic
 # grows with the number of systems (each state is read once, written once).
-# mixed_lean: 29.883 MB read + 0.899 MB written; f2_lean: 30.470 MB read +
-# 0.483 MB written.
-NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
-                                "f2_lean": (30.470144e6 + 0.48256e6) / 262144}
+# mixed_lean: 29.883 MB read + 0.899 MB written.
+NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
                       "(null when another kernel ran or no capture of this kernel exists)")
 
@@ -230,17 +240,32 @@ def run_ours(args):
 
     MAPPING = {"auto": B.ODE_MAP_AUTO, "thread": B.ODE_MAP_THREAD, "queue": B.ODE_MAP_QUEUE}[args.mapping]
 
-    def step(prec, counters=None):
-        B.integrate("rkc", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=yout, counters=counters,
-                    precision=prec, mapping=MAPPING, block_size=args.block, stream=stream.cuda_stream)
+    # the learned proposal's network (trained before any timing, on held-out seeds)
+    net, net_info = None, None
+    if args.chosen in LEARNED_FORMS or args.plain_steps > 0 or args.proposal_nsys > 0:
+        net, net_info = train_proposal(args, B, torch, dev, rank)
+    no_h0 = torch.full((w.nsys,), float("nan"), dtype=torch.float32, device=dev)
+
+    def step(name, counters=None, y_in=None, p_in=None, y_res=None):
+        y_in = y0 if y_in is None else y_in
+        p_in = p if p_in is None else p_in
+        kw = {}
+        if name in LEARNED_FORMS:
+            # the network's bound replaces the initial power method (the Euler
+            # trial still sets the first step); its cost orders the batch
+            _, s0, c = net.propose(y_in, p_in, stream=stream.cuda_stream, with_cost=True)
+            kw = dict(h0=no_h0, sigma0=s0, cost=c)
+        B.integrate("rkc", h, y_in, p_in, w.t0, w.tend, w.rtol, w.atol, y_out=yout if y_res is None else y_res,
+                    counters=counters, precision=FORMS[name], mapping=MAPPING, block_size=args.block,
+                    stream=stream.cuda_stream, **kw)
 
     CHOSEN = FORMS[args.chosen]
-    for prec in FORMS.values():
+    for prec in set(FORMS.values()):
         B.prepare(h, "rkc", prec)       # generated network kernels compiled before any timing
 
-    def timed(prec, steps, warmup):
+    def timed(name, steps, warmup):
         for _ in range(warmup):
-            step(prec)
+            step(name)
         torch.cuda.synchronize()
         evs = []
         barrier()
@@ -250,7 +275,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(prec)
+            step(name)
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -260,8 +285,8 @@ def run_ours(args):
         total = max_over_ranks(total, world, dev)
         return total / steps, ms
 
-    def counted(prec):
-        step(prec, cnt)
+    def counted(name):
+        step(name, cnt)
         torch.cuda.synchronize()
         c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "n_specrad_iter", "status")}
         return c, yout.cpu().numpy()
@@ -274,18 +299,29 @@ def run_ours(args):
 
     # chosen form: timed with the clock sampler running
     with ClockSampler(gpu_id) as clk:
-        ms_chosen, per_step = timed(CHOSEN, args.steps, args.warmup)
+        ms_chosen, per_step = timed(args.chosen, args.steps, args.warmup)
     clocks = clk.summary()
     runs = {}
-    c_ch, y_ch = counted(CHOSEN)
+    c_ch, y_ch = counted(args.chosen)
     runs[args.chosen] = {"ms": ms_chosen, "c": c_ch, "y": y_ch}
+    # the learned form's pre-pass alone (the proposal kernel), so that the
+    # integration kernel's share of the step is known
+    ms_prepass = 0.0
+    if args.chosen in LEARNED_FORMS:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            net.propose(y0, p, stream=stream.cuda_stream, with_cost=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_prepass = e0.elapsed_time(e1) / args.steps
     if args.plain_steps > 0:
         # every other form on the same inputs
-        for name, prec in FORMS.items():
+        for name in FORMS:
             if name == args.chosen:
                 continue
-            ms, _ = timed(prec, args.plain_steps, 1)
-            c, y = counted(prec)
+            ms, _ = timed(name, args.plain_steps, 1)
+            c, y = counted(name)
             runs[name] = {"ms": ms, "c": c, "y": y}
 
     # the kernel the chosen form ran (ODE_MAP_AUTO's choice unless --mapping fixes it)
@@ -300,11 +336,21 @@ def run_ours(args):
     hp = torch.from_numpy(w.params).pin_memory()
     hy = torch.empty_like(hy0).pin_memory()
     e2e_ms = []
+    dy0, dp, dy = torch.empty_like(y0), torch.empty_like(p), torch.empty_like(y0)
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
-                    precision=CHOSEN, mapping=MAPPING, block_size=args.block)
+        if args.chosen in LEARNED_FORMS:
+            # the proposal needs device arrays: pinned host -> device, the
+            # step, device -> pinned host, all inside the timed region
+            dy0.copy_(hy0, non_blocking=True)
+            dp.copy_(hp, non_blocking=True)
+            step(args.chosen, y_in=dy0, p_in=dp, y_res=dy)
+            hy.copy_(dy, non_blocking=True)
+            torch.cuda.synchronize()
+        else:
+            B.integrate("rkc", h, hy0.numpy(), hp.numpy(), w.t0, w.tend, w.rtol, w.atol, y_out=hy.numpy(),
+                        precision=CHOSEN, mapping=MAPPING, block_size=args.block)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
@@ -322,7 +368,11 @@ def run_ours(args):
         peak32, _ = B.fma_peak(False, 1 << 20)
         peak64, _ = B.fma_peak(True, 1 << 14)
         peak32, peak64 = peak32 / 1e3, peak64 / 1e3
-        achieved = flops[args.chosen] / (ms_chosen * 1e-3) / 1e12
+        # the integration kernel's time: the step less the learned pre-pass
+        # (the rate-constant prologue and the order kernels, ~1 % of the
+        # step, stay inside: a lower bound on the kernel's rate)
+        ms_kernel = ms_chosen - ms_prepass
+        achieved = flops[args.chosen] / (ms_kernel * 1e-3) / 1e12
         two_float = args.chosen.startswith("f2")
         ms_plain = runs["plain_fp64"]["ms"] if "plain_fp64" in runs else None
         out = {
@@ -344,12 +394,13 @@ def run_ours(args):
                                         "the kernel runs on)",
                          "peak_measured_fma": peak32, "frac_of_measured": achieved / peak32,
                          "flops_per_launch": flops[args.chosen],
+                         "kernel_ms": ms_kernel, "prepass_ms": ms_prepass,
                          "flops_model": "method flops (3|R| + 2|P| per mass-action evaluation, N (13 + 9 (m - 1)) + "
                                         "15 (m - 1) per attempt, 6 N per power iteration, 5 N for the start)"},
             "fp64_fma_measured_tflops": peak64, "fp32_fma_measured_tflops": peak32,
             "e2e": {"value": aggregate_rate(w.nsys, world, e2e_step), "unit": UNIT,
                     "h2d_bytes_per_step": int(w.y0.nbytes + w.params.nbytes), "d2h_bytes_per_step": int(w.y0.nbytes)},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * LAUNCHES[args.chosen],
             "clocks": clocks,
             "status_ok_frac": float(np.mean((runs[args.chosen]["c"]["status"] & 0xFF) == 0)),
         }
@@ -402,8 +453,14 @@ def run_ours(args):
         c1 = c1_leg(args, B, torch, dev, stream, rank, world, barrier)
         if rank == 0:
             out["c1_bruss_rkc"] = c1
+    if rank == 0 and net_info is not None:
+        out["proposal_network"] = {"train_pairs": net_info["pairs"], "train_sigma_records": net_info["sigma_records"],
+                                   "train_seconds_incl_logging": net_info["seconds"],
+                                   "final_train_loss": float(net_info["hist"][-1]), "train_seeds": "1000+rank",
+                                   "note": "trained once before any timing; used by the learned forms and the "
+                                           "learned_proposal leg"}
     if args.proposal_nsys > 0:
-        prop = proposal_leg(args, B, torch, dev, stream, rank, world, barrier)
+        prop = proposal_leg(args, B, torch, dev, stream, rank, world, barrier, net, net_info)
         if rank == 0:
             out["learned_proposal"] = prop
     if args.mixed_nsys > 0:
@@ -429,25 +486,17 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(out), flush=True)
     B.release(h)
+    if net is not None:
+        net.release()
     if world > 1:
         dist.destroy_process_group()
 
 
-def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
-    """The learned proposal on the 4,194,304-system mass-action batch:
-    trained on records the plain FP64 solver logs on held-out seeds (state
+def train_proposal(args, B, torch, dev, rank):
+    """The learned proposal's network, trained before any timing on records
+    the plain FP64 solver logs on held-out seeds (first-step records: state
     features -> first step, spectral-radius bound, whole-integration cost;
-    and state features -> spectral-radius bound at later estimates), then
-    the chosen form timed without it, with the proposed spectral radius
-    (the Euler trial still sets the first step), with the proposed start
-    (spectral radius and first step), with the network evaluated in the
-    kernel at every spectral-radius point (with_sigma_every), and each of
-    these with the batch taken longest-first by the predicted cost (the
-    proposal and ordering passes are inside the timed step); every mode's
-    error against the FP64 oracle on a sample.  For context, the order from
-    the true costs of an earlier run on the same inputs bounds what any
-    cost predictor can give."""
-    import oracle as O
+    spectral-radius records along the trajectories: state features -> bound)."""
     t_start = time.perf_counter()
     wt = W.massaction(nsys=args.proposal_train, seed=1000 + rank)
     ht = B.register_workload(wt)
@@ -466,13 +515,32 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     Y2[:, 1] = r[:, wt.neq + 1]
     X = torch.cat([log[ok, :wt.neq + 1], r[:, :wt.neq + 1]]).contiguous()
     Y = torch.cat([log[ok, wt.neq + 1:], Y2]).contiguous()
-    n_sr_records = int(r.shape[0])
+    info = {"pairs": int(ok.sum().item()), "sigma_records": int(r.shape[0])}
     del lsr, r, Y2
     net = B.MLP(wt.neq + 1, seed=0)
     net.fit_normalization(X, Y)
-    hist = net.train(X, Y, epochs=args.proposal_epochs, batch=4096, lr=2e-3, seed=0)
-    t_train = time.perf_counter() - t_start
-    del log, X, Y
+    info["hist"] = net.train(X, Y, epochs=args.proposal_epochs, batch=4096, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    info["seconds"] = time.perf_counter() - t_start
+    return net, info
+
+
+def proposal_leg(args, B, torch, dev, stream, rank, world, barrier, net, info):
+    """The learned proposal on the 4,194,304-system mass-action batch:
+    trained on records the plain FP64 solver logs on held-out seeds (state
+    features -> first step, spectral-radius bound, whole-integration cost;
+    and state features -> spectral-radius bound at later estimates), then
+    the chosen form timed without it, with the proposed spectral radius
+    (the Euler trial still sets the first step), with the proposed start
+    (spectral radius and first step), with the network evaluated in the
+    kernel at every spectral-radius point (with_sigma_every), and each of
+    these with the batch taken longest-first by the predicted cost (the
+    proposal and ordering passes are inside the timed step); every mode's
+    error against the FP64 oracle on a sample.  For context, the order from
+    the true costs of an earlier run on the same inputs bounds what any
+    cost predictor can give."""
+    import oracle as O
+    t_train, n_sr_records, hist, n_pairs = info["seconds"], info["sigma_records"], info["hist"], info["pairs"]
 
     w = W.massaction(nsys=args.proposal_nsys, seed=4 + rank)
     h = B.register_workload(w)
@@ -537,7 +605,6 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
     res["ordered_by_true_cost"]["note"] = ("upper bound: order from the n_rhs counters of an earlier run on the "
                                            "same inputs (the previous global step in operator splitting)")
     B.release(h)
-    net.release()
     ref = O.integrate_workload(W.subset(w, np.arange(args.proposal_sample)))
     for k, r in res.items():
         e = (np.abs(r.pop("y_sample") - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
@@ -547,7 +614,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier):
         r["meets_target"] = bool(r["err_vs_fp64_oracle_p999"] <= TARGET_P999)
     qual = [k for k in MODES if res[k]["meets_target"] and k != "ordered_by_true_cost"]
     res["fastest_within_target"] = max(qual, key=lambda k: res[k]["systems_per_s"]) if qual else None
-    res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": int(ok.sum().item()),
+    res["config"] = {"nsys_per_gpu": w.nsys, "train_pairs": n_pairs,
                      "train_sigma_records": n_sr_records,
                      "sigma_records_per_system": f"estimates 0, {args.proposal_sr_every}, ... (at most "
                                                  f"{args.proposal_sr_records})",
@@ -1163,7 +1230,7 @@ def main():
     ap.add_argument("--nsys", type=int, default=NSYS)
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the forms other than the chosen one "
                                                                "(0 skips them)")
-    ap.add_argument("--chosen", choices=sorted(FORMS), default="f2_lean",
+    ap.add_argument("--chosen", choices=sorted(FORMS), default="f2_lean_learned",
                     help="the headline form (the fastest one that meets the accuracy target, as measured)")
     ap.add_argument("--mapping", choices=["auto", "thread", "queue"], default="auto",
                     help="mapping of the main leg (fix it under a profiler, whose overhead distorts the "

@@ -64,6 +64,12 @@ struct Workspace {
         int64_t cap = 0;
     };
     std::map<cudaStream_t, OrderBuf> order;
+    // precomputed right-hand-side constants per stream (grow-only)
+    struct ConstBuf {
+        void* ptr = nullptr;
+        size_t bytes = 0;
+    };
+    std::map<cudaStream_t, ConstBuf> consts;
     double* tab64 = nullptr;
     float4* tab32 = nullptr;
     void* stage = nullptr;
@@ -538,6 +544,25 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     const int meth = method == kRkck ? kMethodRkck : kMethodRkc;
     const bool use_jit = rhs.kind == ODE_RHS_MASSACTION &&
                          (opts.codegen == ODE_CODEGEN_ON || (opts.codegen == ODE_CODEGEN_AUTO && jit_available()));
+    if (use_jit && prec_is_f2(opts.precision) && meth == kMethodRkc) {
+        // the network's rate constants, once per system, before the
+        // integration kernel (and before any tuning run, which reads them too)
+        Workspace::ConstBuf& cb = ws->consts[stream];
+        const size_t need = 2 * sizeof(float) * (size_t)rhs.net.n_reactions * (size_t)nsys;
+        if (cb.bytes < need) {
+            cudaFree(cb.ptr);
+            cb.ptr = nullptr;
+            cb.bytes = 0;
+            e = cudaMalloc(&cb.ptr, need);
+            if (e != cudaSuccess) return fail(ODE_ERR_NOMEM, "rate-constant table of %zu bytes", need);
+            cb.bytes = need;
+        }
+        std::string why;
+        rc = jit_rates(rhs, meth, opts.precision, d_p, nsys, cb.ptr, stream, &why);
+        if (rc) return fail(rc, "%s", why.c_str());
+        a.pre_consts = cb.ptr;
+        a.pre_stride = nsys;
+    }
     if (opts.mapping == ODE_MAP_AUTO) {
         rc = tune_mapping(ws, handle, rhs, meth, opts.precision, use_jit, opts.block_size, a, &cfg);
         if (rc) return rc;

@@ -193,6 +193,16 @@ struct BatchArgs {
     double* carry;
     int32_t carry_mode;  // ODE_CARRY_CONTINUE / ODE_CARRY_RESTART
     int32_t specrad;     // ODE_SPECRAD_POWER / _GERSHGORIN / _POWER_CAPPED (RKC)
+    // set by the launcher for the work-queue kernel: methods that keep a
+    // warp's spectral-radius points together (two-float RKC) count the
+    // schedule per system and let lanes join each other's estimates
+    int32_t warp_sched;
+    // optional per-system constants of the right-hand side computed before
+    // the integration kernel (generated mass-action networks, two-float
+    // forms: rate constants as pairs, constant j of system i at
+    // pre_consts[j * pre_stride + i]); NULL = computed at each system's set-up
+    const void* pre_consts;
+    int64_t pre_stride;
 
     __host__ __device__ int64_t sys_of(int64_t k) const { return index ? (int64_t)index[k] : k; }
     __host__ __device__ int64_t cidx(int64_t i, int w) const { return i + nsys * (int64_t)w; }

@@ -41,6 +41,16 @@ struct ConstSmem<S, void_t_<decltype(S::CONST_SMEM)>> {
     static constexpr int value = S::CONST_SMEM;
 };
 
+// Systems whose constants may come precomputed (Sys::kPreConsts, load_pre).
+template <class S, class = void>
+struct PreConsts {
+    static constexpr bool value = false;
+};
+template <class S>
+struct PreConsts<S, void_t_<decltype(S::kPreConsts)>> {
+    static constexpr bool value = S::kPreConsts;
+};
+
 template <class Model, bool BK64 = false>
 struct RkcF2 {
     static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
@@ -144,7 +154,14 @@ struct RkcF2 {
     bool have_sigma, rejected, warm;
 
     __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
-        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        if constexpr (PreConsts<typename Model::template Sys<F2>>::value) {
+            if (a.pre_consts != nullptr)
+                sys.load_pre(static_cast<const F2*>(a.pre_consts), i, a.pre_stride, a.neq_of(i));
+            else
+                sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        } else {
+            sys.load(ctx, tm, a.params[i], a.neq_of(i));
+        }
         n = a.neq_of(i);
 #pragma unroll(P <= 64 ? P : 4)
         for (int s = 0; s < P; ++s) {
@@ -291,12 +308,14 @@ struct RkcF2 {
             if (1.1f * h >= remf) h = remf;
         }
         if constexpr (kWarpPropose) {
-            // with the network, the schedule counts from each system's last
-            // estimate, and a system within kJoin steps of its point takes
-            // the network's bound when another lane of its warp calls the
-            // network (propose_warp): the warp's points then coincide, even
-            // where the systems started at different times (work queue)
-            if (a.mlp != nullptr && a.specrad == ODE_SPECRAD_POWER) {
+            // with the network, or in the work queue, the schedule counts
+            // from each system's last estimate, and a system within kJoin
+            // steps of its point takes its estimate (the network's bound, or
+            // the power method) when another lane of its warp does
+            // (propose_warp): the warp's points then coincide, even where
+            // the systems started at different times (work queue), so the
+            // lanes stay in one phase of the step
+            if ((a.mlp != nullptr || a.warp_sched) && a.specrad == ODE_SPECRAD_POWER) {
                 if (!have_sigma || rejected || num_step - sr_step >= kSpecradEvery) {
                     if (!rejected) {  // never after a rejection: the power method
                         phase = PH_PROPOSE;
@@ -336,11 +355,16 @@ struct RkcF2 {
     __device__ void propose_warp(const BatchArgs& a, const TM& tm, bool live, int64_t i) {
         if constexpr (kWarpPropose) {
             const MlpPacked* __restrict__ net = a.mlp;
-            if (net == nullptr) return;
+            if (net == nullptr && !a.warp_sched) return;
             const bool want = live && phase == PH_PROPOSE;
             if (!__any_sync(0xffffffffu, want)) return;
             const bool join = live && phase == PH_STAGE && j == 2 && have_sigma && !rejected &&
                               num_step - sr_step >= kSpecradEvery - kJoin && num_step != sr_step;
+            if (net == nullptr) {  // the power method, started together
+                if (join) h = h_free;
+                if (want || join) sr_begin(tm);
+                return;
+            }
             const bool mine = want || join;
             const unsigned take = __ballot_sync(0xffffffffu, mine);
             // features into this lane's d_{j-2} row (unused at a step's

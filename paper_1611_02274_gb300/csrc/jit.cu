@@ -155,6 +155,17 @@ std::string model_source(const RhsEntry& r) {
           << " k[" << j << "] = (R)clip((double)ldexpf(exp2f((float)(l2 - li)), (int)li)); }\n";
     o << "      }\n"
       << "    }\n"
+      // the two-float forms read the constants that bode_jit_rates wrote
+      // (the same FP64 series, once per system, in a kernel of its own):
+      // a system's set-up then runs no series, which matters in the work
+      // queue, where set-ups interleave with the evaluation loop and their
+      // code would push the loop's out of the instruction cache
+      << "    static constexpr bool kPreConsts = true;\n"
+      << "    __device__ void load_pre(const bode::F2* tab, long long i, long long stride, int neq) {\n"
+      << "      n = neq;\n"
+      << "      if constexpr (bode::ConstStore<R, " << NR << ">::SMEM_FLOATS > 0)\n"
+      << "        for (int j = 0; j < " << NR << "; ++j) k[j] = tab[(long long)j * stride + i];\n"
+      << "    }\n"
       << "    __device__ int comp(const bode::Team<1>&, int s) const { return s; }\n"
       << "    template <class T> __device__ T ordered_sum(const bode::Team<1>&, const T* x) const {\n"
       << "      T acc = T(0);\n";
@@ -241,6 +252,20 @@ std::string model_source(const RhsEntry& r) {
       << "    }\n"
       << "  };\n"
       << "};\n";
+    // every system's rate constants from its temperature params[i] as
+    // two-float pairs, reaction-major (out[j * nsys + i]); the expression of
+    // the FP64 branch of load() above
+    o << "extern \"C\" __global__ void bode_jit_rates(const double* __restrict__ Tv, long long nsys,\n"
+      << "                                             bode::F2* __restrict__ out) {\n"
+      << "  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
+      << "  if (i >= nsys) return;\n"
+      << "  using S = JitMass::Sys<bode::F2>;\n"
+      << "  const double T = Tv[i];\n"
+      << "  const double lnT = bode::xm::log_series(T);\n";
+    for (int j = 0; j < NR; ++j)
+        o << "  out[" << j << "LL * nsys + i] = bode::F2(S::clip(bode::xm::exp_series(bode::xm::kLn10 * "
+          << lit(net.log10A[j]) << " + " << lit(net.beta[j]) << " * lnT - " << lit(net.Ea[j]) << " / T)));\n";
+    o << "}\n";
     return o.str();
 }
 
@@ -284,7 +309,7 @@ void write_file(const std::string& dir, const std::string& path, const std::vect
 
 struct JitKernels {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t kstatic = nullptr, kqueue = nullptr;
+    cudaKernel_t kstatic = nullptr, kqueue = nullptr, krates = nullptr;
     int smem_floats = 0;  // dynamic shared memory per thread, as the integrator declares it
 };
 
@@ -422,6 +447,7 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
     cudaError_t e = cudaLibraryLoadData(&out->lib, img.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kstatic, out->lib, img.low_static.c_str());
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->kqueue, out->lib, img.low_queue.c_str());
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&out->krates, out->lib, "bode_jit_rates");
     void* dptr = nullptr;
     size_t bytes = 0;
     if (e == cudaSuccess) e = cudaLibraryGetGlobal(&dptr, &bytes, out->lib, "bode_jit_smem_floats");
@@ -566,6 +592,22 @@ int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err) {
     return get_kernels(r, method, prec, &k, err);
 }
 
+int jit_rates(const RhsEntry& r, int method, int prec, const double* T, int64_t nsys, void* out, cudaStream_t s,
+              std::string* err) {
+    JitKernels k;
+    int rc = get_kernels(r, method, prec, &k, err);
+    if (rc) return rc;
+    if (nsys <= 0) return ODE_OK;
+    long long n = (long long)nsys;
+    void* params[] = {(void*)&T, &n, &out};
+    const cudaError_t e = cudaLaunchKernel((const void*)k.krates, dim3((unsigned)((nsys + 255) / 256)), dim3(256), params, 0, s);
+    if (e != cudaSuccess) {
+        *err = std::string("rate-constant kernel launch: ") + cudaGetErrorString(e);
+        return ODE_ERR_CUDA;
+    }
+    return ODE_OK;
+}
+
 int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, const LaunchCfg& c, std::string* err) {
     JitKernels k;
     int rc = get_kernels(r, method, prec, &k, err);
@@ -598,6 +640,7 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
         int64_t grid = (int64_t)per_sm * c.sm_count;
         const int64_t need = (threads + block - 1) / block;
         if (grid > need) grid = need;
+        args.warp_sched = 1;
         e = cudaLaunchKernel((const void*)k.kqueue, dim3((unsigned)grid), dim3(block), params, smem, c.stream);
     } else {
         const int64_t grid = (threads + block - 1) / block;

@@ -15,6 +15,12 @@ bool jit_available();
 // description in *err.
 int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, const LaunchCfg& c, std::string* err);
 
+// Every system's rate constants of network r (temperatures T[nsys], the
+// parameters' first row) as two-float pairs out[j * nsys + i], computed by the
+// generated module of (method, precision) on stream s.
+int jit_rates(const RhsEntry& r, int method, int prec, const double* T, int64_t nsys, void* out, cudaStream_t s,
+              std::string* err);
+
 // Compile (and, with a device present, load) the generated kernels of r.
 int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err);
 

@@ -51,7 +51,9 @@ cudaError_t launch_method(const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c
         int64_t grid = (int64_t)per_sm * c.sm_count;
         const int64_t need = (threads + block - 1) / block;
         if (grid > need) grid = need;
-        k_queue<Method, Ctx><<<(unsigned)grid, block, smem, c.stream>>>(a, ctx);
+        BatchArgs q = a;
+        q.warp_sched = 1;
+        k_queue<Method, Ctx><<<(unsigned)grid, block, smem, c.stream>>>(q, ctx);
     } else {
         const int64_t grid = (threads + block - 1) / block;
         k_static<Method, Ctx><<<(unsigned)grid, block, smem, c.stream>>>(a, ctx);
