@@ -213,6 +213,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
+def map_text(B, h, prec, mapping, block):
+    """The kernel and block size a form's calls ran with (ODE_MAP_AUTO's
+    cached choice unless the mapping is fixed)."""
+    if mapping != B.ODE_MAP_AUTO:
+        return ("thread" if mapping == B.ODE_MAP_THREAD else "queue") + f", block {block or 128}"
+    m, b, tuned = B.mapping_info(h, "rkc", prec, block_size=block)
+    return ("thread" if m == B.ODE_MAP_THREAD else "queue") + f", block {b}" + ("" if tuned else " (default)")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -422,6 +431,7 @@ def run_ours(args):
                            "frac_peak_measured": ach / (peak64 if peak_kind == "fp64" else peak32),
                            "peak": peak_kind, "form": FORM_TEXT[name],
                            "speedup_vs_plain": (ms_plain / r["ms"]) if ms_plain else None,
+                           "mapping": map_text(B, h, FORMS[name], MAPPING, args.block),
                            "status_ok_frac": float(np.mean((r["c"]["status"] & 0xFF) == 0))}
         out["forms"] = forms
         if ms_plain:

@@ -344,8 +344,10 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
     if (a.nsys < kTuneMinSystems || cap != cudaStreamCaptureStatusNone) return ODE_OK;
 
-    // sample: the first systems of the batch, output to a scratch buffer
-    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(65536, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
+    // sample: the first systems of the batch, output to a scratch buffer;
+    // 262,144 systems give the work queue ~4 systems per lane, so that the
+    // cost of its system switches shows (at one per lane it never does)
+    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(262144, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
     const size_t bytes = sizeof(double) * (size_t)sample * rhs.neq;
     if (ws->tune_bytes < bytes) {
         if (ws->tune_y) cudaFree(ws->tune_y);

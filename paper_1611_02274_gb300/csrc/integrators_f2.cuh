@@ -51,7 +51,12 @@ struct PreConsts<S, void_t_<decltype(S::kPreConsts)>> {
     static constexpr bool value = S::kPreConsts;
 };
 
-template <class Model, bool BK64 = false>
+// NET: the variant with the warp-level code of the in-kernel network and of
+// the joined spectral-radius estimates (the work queue, ode_opts.mlp); the
+// plain variant, for the one-launch mapping without a network, leaves that
+// code out of its evaluation loop, whose instructions are fetched every
+// iteration.
+template <class Model, bool BK64 = false, bool NET = false>
 struct RkcF2 {
     static constexpr bool kStepSync = true;  // variable stage count: hold at the step end
     static constexpr int W = Model::W, P = Model::PER;
@@ -80,7 +85,7 @@ struct RkcF2 {
     // system with rows in shared memory: up to 32 components + the
     // parameter, the BF16 features staged in the d_{j-2} row)
     static constexpr int kMlpKs = (P + 1 + 15) / 16;
-    static constexpr bool kWarpPropose = W == 1 && P <= 32 && D2_SMEM >= 8 * kMlpKs && Y_SMEM > 0;
+    static constexpr bool kWarpPropose = NET && W == 1 && P <= 32 && D2_SMEM >= 8 * kMlpKs && Y_SMEM > 0;
     static constexpr int kJoin = 12;  // steps before its point a system joins a warp's network evaluation
     mutable F2 vreg[V_SMEM ? 1 : P];
     mutable F2 d2reg[D2_SMEM ? 1 : P];
@@ -144,7 +149,7 @@ struct RkcF2 {
     }
     double t, tend;                   // BK64
     float remf, reml, tendf;          // FP32 scalars: remaining interval as a pair
-    HT hmax, hmin, h, h_old, sigma, h_free;
+    HT hmax, hmin, h, h_old, sigma;
     F2 hh;                            // the step size as a pair (exact for an FP32 h)
     float rtolf, atolf, c3_old, dynrm, sig;
     float4 chi, clo;                  // (mu_j, nu_j, mu~_j, gamma~_j), leading / trailing words
@@ -361,7 +366,6 @@ struct RkcF2 {
             const bool join = live && phase == PH_STAGE && j == 2 && have_sigma && !rejected &&
                               num_step - sr_step >= kSpecradEvery - kJoin && num_step != sr_step;
             if (net == nullptr) {  // the power method, started together
-                if (join) h = h_free;
                 if (want || join) sr_begin(tm);
                 return;
             }
@@ -401,8 +405,8 @@ struct RkcF2 {
             status |= ODE_ST_PROPOSED;
             if (want) {
                 after_sr(a);
-            } else {  // a joiner: the step's stage count and set-up again
-                h = h_free;
+            } else {  // a joiner: the step's stage count and set-up again (from
+                      // its step size as it stands: a cap the old bound set stays)
                 stage_begin(a);
             }
         }
@@ -529,7 +533,6 @@ struct RkcF2 {
     }
 
     __device__ void stage_begin(const BatchArgs& a) {
-        h_free = h;  // before the stage-count cap (a joiner sets the step up again)
         m = 1 + (int)sqrt((HT)1.54 * h * sigma + (HT)1);
         if (m > mmax) {
             m = mmax;

@@ -316,9 +316,12 @@ struct JitKernels {
 std::mutex g_jit_mu;
 std::map<std::string, JitKernels> g_cache;  // key: device + source hash + form
 
-std::string method_type(int method, int prec) {
-    if (prec == ODE_PREC_F2) return "bode::RkcF2<JitMass, true>";
-    if (prec == ODE_PREC_F2_LEAN) return "bode::RkcF2<JitMass, false>";
+// net: the two-float variant with the warp-level code (work queue, in-kernel
+// network); the other forms have one variant
+std::string method_type(int method, int prec, bool net) {
+    const std::string nv = net ? "true" : "false";
+    if (prec == ODE_PREC_F2) return "bode::RkcF2<JitMass, true, " + nv + ">";
+    if (prec == ODE_PREC_F2_LEAN) return "bode::RkcF2<JitMass, false, " + nv + ">";
     if (method == kMethodRkck)
         return prec == ODE_PREC_FP64 ? "bode::RkckF64<JitMass>"
                : prec == ODE_PREC_MIXED ? "bode::RkckMixed<JitMass, true>" : "bode::RkckMixed<JitMass, false>";
@@ -331,9 +334,9 @@ struct JitImage {
     std::vector<char> cubin;
 };
 
-int compile_image(const RhsEntry& r, int method, int prec, JitImage* img, std::string* err) {
+int compile_image(const RhsEntry& r, int method, int prec, bool net, JitImage* img, std::string* err) {
     const std::string model = model_source(r);
-    const std::string meth = method_type(method, prec);
+    const std::string meth = method_type(method, prec, net);
     const std::string nstatic = "bode::k_static<" + meth + ", bode::NoCtx>";
     const std::string nqueue = "bode::k_queue<" + meth + ", bode::NoCtx>";
     // the two kernels are instantiated through their name expressions
@@ -461,22 +464,27 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
     return ODE_OK;
 }
 
-std::string cache_key(const RhsEntry& r, int method, int prec, int dev) {
+std::string cache_key(const RhsEntry& r, int method, int prec, bool net, int dev) {
     char key[96];
-    snprintf(key, sizeof(key), "%d/%d/%d/%016llx/%d", dev, method, prec, (unsigned long long)fnv1a(model_source(r)),
-             jit_min_blocks(prec));
+    snprintf(key, sizeof(key), "%d/%d/%d/%d/%016llx/%d", dev, method, prec, (int)net,
+             (unsigned long long)fnv1a(model_source(r)), jit_min_blocks(prec));
     return key;
 }
 
+// whether a launch takes the two-float variant with the warp-level code
+bool wants_net(int prec, const BatchArgs& a, int mapping) {
+    return prec_is_f2(prec) && (a.mlp != nullptr || mapping == ODE_MAP_QUEUE);
+}
+
 // kernels for the current device, built and loaded at first use
-int get_kernels(const RhsEntry& r, int method, int prec, JitKernels* k, std::string* err) {
+int get_kernels(const RhsEntry& r, int method, int prec, bool net, JitKernels* k, std::string* err) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
         return ODE_ERR_CUDA;
     }
-    const std::string key = cache_key(r, method, prec, dev);
+    const std::string key = cache_key(r, method, prec, net, dev);
     std::lock_guard<std::mutex> lk(g_jit_mu);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
@@ -484,7 +492,7 @@ int get_kernels(const RhsEntry& r, int method, int prec, JitKernels* k, std::str
         return ODE_OK;
     }
     JitImage img;
-    int rc = compile_image(r, method, prec, &img, err);
+    int rc = compile_image(r, method, prec, net, &img, err);
     if (rc == ODE_OK) rc = load_image(img, k, err);
     if (rc == ODE_OK) g_cache[key] = *k;
     return rc;
@@ -583,19 +591,30 @@ bool jit_available() { return nvrtc().ok; }
 
 int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err) {
     int ndev = 0;
+    // the two-float forms in both variants (the work queue and the in-kernel
+    // network take the one with the warp-level code)
+    const int variants = prec_is_f2(prec) ? 2 : 1;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();  // clear the no-device error
-        JitImage img;
-        return compile_image(r, method, prec, &img, err);
+        for (int v = 0; v < variants; ++v) {
+            JitImage img;
+            const int rc = compile_image(r, method, prec, v == 1, &img, err);
+            if (rc) return rc;
+        }
+        return ODE_OK;
     }
-    JitKernels k;
-    return get_kernels(r, method, prec, &k, err);
+    for (int v = 0; v < variants; ++v) {
+        JitKernels k;
+        const int rc = get_kernels(r, method, prec, v == 1, &k, err);
+        if (rc) return rc;
+    }
+    return ODE_OK;
 }
 
 int jit_rates(const RhsEntry& r, int method, int prec, const double* T, int64_t nsys, void* out, cudaStream_t s,
               std::string* err) {
     JitKernels k;
-    int rc = get_kernels(r, method, prec, &k, err);
+    int rc = get_kernels(r, method, prec, false, &k, err);
     if (rc) return rc;
     if (nsys <= 0) return ODE_OK;
     long long n = (long long)nsys;
@@ -610,7 +629,7 @@ int jit_rates(const RhsEntry& r, int method, int prec, const double* T, int64_t 
 
 int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, const LaunchCfg& c, std::string* err) {
     JitKernels k;
-    int rc = get_kernels(r, method, prec, &k, err);
+    int rc = get_kernels(r, method, prec, wants_net(prec, a, c.mapping), &k, err);
     if (rc) return rc;
     NoCtx ctx;
     BatchArgs args = a;

@@ -28,13 +28,24 @@ cudaError_t run_model_mixed(int method, int prec, const BatchArgs& a, const Ctx&
     return run_model_prec<Model, ODE_PREC_MIXED_LEAN>(method, a, ctx, c);
 }
 
+// two-float forms: the variant with the warp-level code (M1) for the work
+// queue and the in-kernel network, where the model supports it; otherwise
+// the plain variant (M0)
+template <class M0, class M1, class Ctx>
+cudaError_t launch_f2(const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c) {
+    if constexpr (M1::kWarpPropose) {
+        if (a.mlp != nullptr || c.mapping == ODE_MAP_QUEUE) return launch_method<M1>(a, ctx, c);
+    }
+    return launch_method<M0>(a, ctx, c);
+}
+
 // two-float forms: RKC only
 template <class Model, class Ctx>
 cudaError_t run_model_f2(int method, int prec, const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c, bool* ok) {
     *ok = method == kMethodRkc;
     if (!*ok) return cudaSuccess;
-    if (prec == ODE_PREC_F2) return launch_method<RkcF2<Model, true>>(a, ctx, c);
-    return launch_method<RkcF2<Model, false>>(a, ctx, c);
+    if (prec == ODE_PREC_F2) return launch_f2<RkcF2<Model, true, false>, RkcF2<Model, true, true>>(a, ctx, c);
+    return launch_f2<RkcF2<Model, false, false>, RkcF2<Model, false, true>>(a, ctx, c);
 }
 
 template <class Model, class Ctx>
