@@ -60,6 +60,9 @@ FORMS = {"f2_lean_learned": 4, "f2_lean": 4, "f2": 3, "mixed_lean": 2, "mixed_sp
 # (spectral-radius bound and cost per system, the Euler trial still setting
 # the first step) and the longest-first order by the predicted cost
 LEARNED_FORMS = {"f2_lean_learned"}
+# the precision form underneath (what the other legs run when they take the
+# headline's precision without its proposal)
+BASE_FORM = {"f2_lean_learned": "f2_lean"}
 # our kernel launches per step: the integration kernel; for the generated
 # two-float forms the rate-constant prologue; for the learned forms the
 # proposal pre-pass and the four kernels of the cost order
@@ -86,8 +89,12 @@ FORM_TEXT = {
 # DRAM bytes (read + write) per system of each form's generated kernel, from
 # one ncu capture of k_static on 262,144 systems of this workload; traffic
 # grows with the number of systems (each state is read once, written once).
-# mixed_lean: 29.883 MB read + 0.899 MB written.
-NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144}
+# mixed_lean: 29.883 MB read + 0.899 MB written.  f2_lean_learned (the
+# kernel reads its systems through the predicted-cost order, so each 8-byte
+# state access is a 32-byte sector of its own; it also reads the rate
+# table of the prologue): 437.880 MB read + 67.929 MB written.
+NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
+                                "f2_lean_learned": (437.879552e6 + 67.928576e6) / 262144}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
                       "(null when another kernel ran or no capture of this kernel exists)")
 
@@ -389,7 +396,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_chosen, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPES[args.chosen],
             "data": "synthetic (seeded mass-action network and states; no dataset)",
-            "config": {"workload": "massaction-13sp-27rx RKC, 1,048,576 systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
+            "config": {"workload": f"massaction-13sp-27rx RKC, {w.nsys:,} systems/GPU, t in [0,1e-4], rtol 1e-6, atol 1e-12",
                        "nsys_per_gpu": w.nsys, "method": "rkc", "form": FORM_TEXT[args.chosen],
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"independent batches x{world}"},
             "rhs_evals_per_s": float(np.sum(runs[args.chosen]["c"]["n_rhs"])) * world / (ms_chosen * 1e-3),
@@ -635,7 +642,7 @@ def proposal_leg(args, B, torch, dev, stream, rank, world, barrier, net, info):
                                 "FP32 accumulate"}
     for k in MODES[1:]:
         res["speedup_" + k] = res["without"]["ms_per_step"] / res[k]["ms_per_step"]
-    res["config"]["form"] = FORM_TEXT[args.chosen]
+    res["config"]["form"] = FORM_TEXT[BASE_FORM.get(args.chosen, args.chosen)]
     res["config"]["oracle_sample"] = args.proposal_sample
     return res
 
@@ -775,8 +782,8 @@ def kinetics_leg(args, B, torch, dev, stream, rank, world, barrier):
 
 
 def specrad_leg(args, B, torch, dev, stream, rank, world, barrier):
-    """The chosen form on the mass-action batch with each spectral-radius
-    estimate: the Appendix's power method (the paper's), the Gershgorin
+    """The chosen form's precision (without the learned proposal) on the
+    mass-action batch with each spectral-radius estimate: the Appendix's power method (the paper's), the Gershgorin
     bound instead of it, and the power method capped by the bound."""
     import torch.distributed as dist
     w = W.massaction(nsys=args.nsys, seed=rank)
@@ -906,7 +913,7 @@ def split_leg(args, B, torch, dev, stream, rank, world, barrier):
     res["speedup_vs_cold"] = {m: res["cold"]["ms_per_chain"] / res[m]["ms_per_chain"] for m in MODES}
     res["config"] = {"nsys_per_gpu": w.nsys, "global_steps": args.split_steps, "interval": [w.t0, w.tend],
                      "timed": f"{args.split_reps} repetitions of the whole chain after one warm-up repetition",
-                     "precision": FORM_TEXT[args.chosen],
+                     "precision": FORM_TEXT[BASE_FORM.get(args.chosen, args.chosen)],
                      "state": "device resident (the paper copies each global step)"}
     return res
 

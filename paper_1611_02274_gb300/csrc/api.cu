@@ -346,8 +346,11 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
 
     // sample: the first systems of the batch, output to a scratch buffer;
     // 262,144 systems give the work queue ~4 systems per lane, so that the
-    // cost of its system switches shows (at one per lane it never does)
-    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(262144, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
+    // cost of its system switches shows (at one per lane it never does);
+    // the FP64 forms, ~10x slower per system, keep 65,536 (their timing
+    // would otherwise cost more than one integration of a 1M batch)
+    const int64_t sample_cap = prec == ODE_PREC_FP64 ? 65536 : 262144;
+    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(sample_cap, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
     const size_t bytes = sizeof(double) * (size_t)sample * rhs.neq;
     if (ws->tune_bytes < bytes) {
         if (ws->tune_y) cudaFree(ws->tune_y);
