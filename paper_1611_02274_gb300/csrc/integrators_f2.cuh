@@ -16,7 +16,7 @@
 // rounding perturbs the step sequence by ~1e-7 relative, far below the
 // controller's sensitivity), the remaining interval as an FP32 pair; with
 // BK64 the time, step size and spectral radius are FP64 and the error norm
-// is accumulated in FP64, as the spec split keeps bookkeeping.
+// is accumulated in FP64 (time and step-size bookkeeping in FP64).
 // Chebyshev coefficients come from the FP64-built table as two-float pairs.
 // The power method runs in two-float arithmetic with the FP64 perturbation
 // size sqrt(uround) (the difference quotient keeps ~7 digits).
