@@ -551,20 +551,25 @@ struct RkcF2 {
     // d_j = mu_j d_{j-1} + nu_j d_{j-2} + mu~_j h f_{j-1} + gamma~_j h F_n
     // (at j = 2, d_0 = 0 and the nu term is an exact zero: skipped).  The
     // products stay unnormalised and the three- or four-term sum is lazy,
-    // with one renormalisation per component.
+    // with one renormalisation per component.  At j = 2, d_1 = mu~_1 h F_n,
+    // so d_2 = (mu_2 mu~_1 + gamma~_2) h F_n + mu~_2 h f_1: the scalar
+    // coefficient once per step, two products and one sum per component
+    // (the two-stage step is the one every system takes at tight
+    // tolerances).
     __device__ void stage_consume(const F2* f) {
         const F2 mu(chi.x, clo.x), nu(chi.y, clo.y);
-        const F2 muth = F2(chi.z, clo.z) * hh, gth = F2(chi.w, clo.w) * hh;
+        const F2 muth = F2(chi.z, clo.z) * hh;
         const bool keep = j < m;  // d_{j-1} is the next stage's d_{j-2}
         if (j == 2) {
+            const F2 c2h = (mu * cs.mut1f2() + F2(chi.w, clo.w)) * hh;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
-                const F2 dj = normalize(add_lazy(add_lazy(mul_lazy(mu, d1[s]), mul_lazy(muth, f[s])),
-                                                 mul_lazy(gth, Fn[s])));
+                const F2 dj = normalize(add_lazy(mul_lazy(c2h, Fn[s]), mul_lazy(muth, f[s])));
                 if (keep) D2s(s, d1[s]);
                 d1[s] = dj;
             }
         } else {
+            const F2 gth = F2(chi.w, clo.w) * hh;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
                 const F2 dj = normalize(add_lazy(
