@@ -115,6 +115,23 @@ int jit_min_blocks(int prec) {
     return n >= 1 && n <= 16 ? n : def;
 }
 
+// Block lockstep of the generated one-launch kernels (BODE_LOCKSTEP in
+// kernels.cuh): the two-float forms take 2, the block-wide step-end hold.
+// Their evaluation and step code is several times the FP32 forms' and the
+// kernel waits on instruction fetch; with the hold, the four warps of a
+// block run the same phase of the step at the same time.  Measured per
+// 1M-system mass-action step, results bit-identical: two-float with FP32
+// scalars 156.5 -> 133.0 ms (cost-ordered) and 207 -> 184 ms (unordered);
+// with FP64 bookkeeping 229 -> 210 ms.  The FP32 forms lose with it (lean
+// 40.4 -> 42.2 ms, the specified split 121 -> 126 ms) and FP64 is
+// unchanged, so they keep 0.  BATCHODE_JIT_LOCKSTEP (0-2) overrides.
+int jit_lockstep(int prec) {
+    const int def = prec_is_f2(prec) ? 2 : 0;
+    const char* v = getenv("BATCHODE_JIT_LOCKSTEP");
+    const int n = v ? atoi(v) : def;
+    return n >= 0 && n <= 2 ? n : def;
+}
+
 std::string lit(double x) {
     char buf[64];
     snprintf(buf, sizeof(buf), "%.17g", x);
@@ -353,6 +370,7 @@ int compile_image(const RhsEntry& r, int method, int prec, bool net, JitImage* i
         opts.push_back("-DBODE_MAX_THREADS=128");
         opts.push_back("-DBODE_MIN_BLOCKS=" + std::to_string(minb));
     }
+    if (jit_lockstep(prec) > 0) opts.push_back("-DBODE_LOCKSTEP=" + std::to_string(jit_lockstep(prec)));
     const char* verbose = getenv("BATCHODE_JIT_VERBOSE");  // print the ptxas resource report
     if (verbose && *verbose == '1') opts.push_back("-Xptxas=-v");
     std::string key_text = src + "\n" + nstatic + "\n" + nqueue;
@@ -465,9 +483,9 @@ int load_image(const JitImage& img, JitKernels* out, std::string* err) {
 }
 
 std::string cache_key(const RhsEntry& r, int method, int prec, bool net, int dev) {
-    char key[96];
-    snprintf(key, sizeof(key), "%d/%d/%d/%d/%016llx/%d", dev, method, prec, (int)net,
-             (unsigned long long)fnv1a(model_source(r)), jit_min_blocks(prec));
+    char key[128];
+    snprintf(key, sizeof(key), "%d/%d/%d/%d/%016llx/%d/%d", dev, method, prec, (int)net,
+             (unsigned long long)fnv1a(model_source(r)), jit_min_blocks(prec), jit_lockstep(prec));
     return key;
 }
 

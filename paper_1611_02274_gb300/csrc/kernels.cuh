@@ -13,6 +13,14 @@
 #ifndef BODE_MIN_BLOCKS
 #define BODE_MIN_BLOCKS 1
 #endif
+// Block lockstep of the one-launch mapping (run-time compiled kernels):
+// 0 -- each warp loops on its own; 1 -- the warps of a block take their
+// iterations together (a block-wide vote ends the loop); 2 -- as 1, and the
+// step-end hold waits for every system of the block, so the block's warps
+// also run the same phase of the step.
+#ifndef BODE_LOCKSTEP
+#define BODE_LOCKSTEP 0
+#endif
 
 namespace bode {
 
@@ -37,10 +45,11 @@ __device__ __forceinline__ void bind_method_smem(Method& m) {
 // with fewer stages.  Every iteration in which a lane is in its stages
 // advances that lane, so the hold always ends.  The arithmetic of each
 // system is unchanged.
-template <class Method>
+template <class Method, int LOCK = 0>
 __device__ __forceinline__ bool step_hold(const Method& m, bool live) {
     if constexpr (Method::kStepSync && Method::W < 32) {
-        const bool staging = __any_sync(0xffffffffu, live && m.in_stages());
+        const bool staging = LOCK == 2 ? __syncthreads_or(live && m.in_stages()) != 0
+                                       : __any_sync(0xffffffffu, live && m.in_stages());
         return live && staging && m.at_step_end();
     } else {
         return false;
@@ -99,9 +108,13 @@ __global__ void __launch_bounds__(BODE_MAX_THREADS, BODE_MIN_BLOCKS) __maxnreg__
     if constexpr (Method::kStepSync && W < 32) {
         for (;;) {
             const bool live = in_range && !m.done();
-            if (!__any_sync(0xffffffffu, live)) break;
-            warp_propose(m, a, tm, live, i);       // every lane takes part
-            const bool hold = step_hold(m, live);  // a warp vote: every lane takes part
+            if constexpr (BODE_LOCKSTEP > 0) {
+                if (!__syncthreads_or(live)) break;  // every thread of the block takes part
+            } else {
+                if (!__any_sync(0xffffffffu, live)) break;
+            }
+            warp_propose(m, a, tm, live, i);                      // every lane takes part
+            const bool hold = step_hold<Method, BODE_LOCKSTEP>(m, live);  // a vote: every lane takes part
             if (live && !hold) {
                 R tx;
                 m.point(x, tx);
