@@ -345,13 +345,19 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
     if (a.nsys < kTuneMinSystems || cap != cudaStreamCaptureStatusNone) return ODE_OK;
 
     // sample: the first systems of the batch, output to a scratch buffer;
-    // 262,144 systems give the work queue ~4 systems per lane, so that the
-    // cost of its system switches shows (at one per lane it never does);
-    // the FP64 forms, ~10x slower per system, keep 65,536 (their timing
-    // would otherwise cost more than one integration of a 1M batch)
-    const int64_t sample_cap = prec == ODE_PREC_FP64 ? 65536 : 262144;
-    const int64_t sample = std::min<int64_t>(a.nsys, std::min<int64_t>(sample_cap, std::max<int64_t>(4096, (1 << 22) / rhs.neq)));
-    const size_t bytes = sizeof(double) * (size_t)sample * rhs.neq;
+    // up to 262,144 systems give the work queue ~4 systems per lane, so that
+    // the cost of its system switches shows (at one per lane it never
+    // does).  A probe run of the first candidate on 32,768 systems (also the
+    // warm-up: code paging, caches) prices a system; the sample then takes
+    // what ~50 ms per candidate buys, between 65,536 and 262,144 systems.
+    // Cheap systems (van der Pol RKCK in FP64, the FP32 and two-float
+    // forms) get the full sample; expensive ones (FP64 mass-action, n-body)
+    // keep 65,536, so that the timing costs less than one integration of a
+    // 1M batch.
+    const int64_t probe = kTuneMinSystems;
+    const int64_t cap_sys = std::min<int64_t>(a.nsys, std::max<int64_t>(4096, (1 << 22) / rhs.neq));
+    const int64_t sample_max = std::min<int64_t>(cap_sys, 262144);
+    const size_t bytes = sizeof(double) * (size_t)sample_max * rhs.neq;
     if (ws->tune_bytes < bytes) {
         if (ws->tune_y) cudaFree(ws->tune_y);
         ws->tune_y = nullptr;
@@ -360,9 +366,9 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
         ws->tune_bytes = bytes;
     }
     BatchArgs t = a;
-    t.nsys = sample;
+    t.nsys = std::min<int64_t>(probe, sample_max);
     t.ld_in = a.nsys;
-    t.ld_out = sample;
+    t.ld_out = sample_max;
     t.y_out = ws->tune_y;
     t.n_accept = t.n_reject = t.n_rhs = t.n_specrad = t.status = nullptr;
     t.log_xy = nullptr;
@@ -370,21 +376,31 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
     t.carry = nullptr;  // the timing runs neither read nor overwrite the caller's warm-restart state
     t.cursor = ws->cursors + kCursorRing;
     std::vector<std::pair<int, int>> cand;
+    // generated kernels with a multi-block register budget launch at most
+    // 128 threads per block: a larger candidate would time the same launch
+    const int bmax = use_jit ? jit_max_block(prec) : 256;
     for (int b : {64, 128, 256})
-        if (!block_req || b == block_req) cand.push_back({ODE_MAP_THREAD, b});
-    if (block_req && block_req != 64 && block_req != 128 && block_req != 256) cand.push_back({ODE_MAP_THREAD, block_req});
-    cand.push_back({ODE_MAP_QUEUE, block_req ? block_req : 128});
+        if ((!block_req || b == block_req) && b <= bmax) cand.push_back({ODE_MAP_THREAD, b});
+    if (block_req && block_req != 64 && block_req != 128 && block_req != 256 && block_req <= bmax)
+        cand.push_back({ODE_MAP_THREAD, block_req});
+    if (cand.empty()) cand.push_back({ODE_MAP_THREAD, bmax});
+    cand.push_back({ODE_MAP_QUEUE, block_req ? std::min(block_req, bmax) : 128});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-    float best = 3.0e38f;
+    float best = 3.0e38f, best_probe_ms = 0.0f;
     int rc = ODE_OK;
     for (size_t k = 0; k <= cand.size() && rc == ODE_OK; ++k) {
-        // k = 0 warms up (code paging, caches) with the first candidate
+        // k = 0 is the probe (and warm-up) with the first candidate
         LaunchCfg c = *cfg;
         c.mapping = cand[k ? k - 1 : 0].first;
         c.block = cand[k ? k - 1 : 0].second;
+        if (k == 1) {  // the sample the probe's price allows
+            const double per_sys = (double)best_probe_ms / (double)t.nsys;
+            const int64_t want = per_sys > 0.0 ? (int64_t)(50.0 / per_sys) : sample_max;
+            t.nsys = std::min<int64_t>(sample_max, std::max<int64_t>(std::min<int64_t>(65536, sample_max), want));
+        }
         e = cudaEventRecord(e0, c.stream);
         if (e == cudaSuccess) rc = dispatch(rhs, meth, prec, use_jit, t, c);
         if (rc) break;
@@ -396,6 +412,7 @@ int tune_mapping(Workspace* ws, int32_t handle, const RhsEntry& rhs, int meth, i
             rc = cuda_fail(e, "mapping tuning");
             break;
         }
+        if (k == 0) best_probe_ms = ms;
         if (k && ms < best) {
             best = ms;
             cfg->mapping = c.mapping;
@@ -710,6 +727,7 @@ int ode_mapping_info(int32_t rhs_handle, int32_t method, int32_t precision, int3
     } else {
         default_mapping(&cfg, block_size);
     }
+    if (use_jit && cfg.block > jit_max_block(precision)) cfg.block = jit_max_block(precision);  // what launches
     *mapping = cfg.mapping;
     *block = cfg.block;
     return t != g_map_tuned.end() ? ODE_OK : ODE_ERR_UNSUPPORTED;

@@ -583,6 +583,8 @@ int compile_program(const std::string& src, const std::vector<std::string>& name
 
 }  // namespace
 
+int jit_max_block(int prec) { return jit_min_blocks(prec) > 1 ? 128 : 256; }
+
 int jit_program(const std::string& src, const std::vector<std::string>& names, std::vector<cudaKernel_t>* kernels,
                 std::string* err) {
     int dev = 0;
@@ -652,7 +654,7 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
     NoCtx ctx;
     BatchArgs args = a;
     void* params[] = {&args, &ctx};
-    const int block = jit_min_blocks(prec) > 1 && c.block > 128 ? 128 : c.block;
+    const int block = c.block > jit_max_block(prec) ? jit_max_block(prec) : c.block;
     // the generated model is one thread per system with PER = species count
     const size_t smem = sizeof(float) * (size_t)k.smem_floats * (size_t)block;
     const int64_t threads = a.nsys;  // one thread per system

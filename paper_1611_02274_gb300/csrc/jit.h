@@ -21,6 +21,11 @@ int jit_launch(const RhsEntry& r, int method, int prec, const BatchArgs& a, cons
 int jit_rates(const RhsEntry& r, int method, int prec, const double* T, int64_t nsys, void* out, cudaStream_t s,
               std::string* err);
 
+// The largest block the generated kernels of a precision form launch with:
+// 128 for the forms compiled with a register budget of several resident
+// blocks (larger requested blocks run as 128), else 256.
+int jit_max_block(int prec);
+
 // Compile (and, with a device present, load) the generated kernels of r.
 int jit_prepare(const RhsEntry& r, int method, int prec, std::string* err);
 
