@@ -90,11 +90,12 @@ FORM_TEXT = {
 # one ncu capture of k_static on 262,144 systems of this workload; traffic
 # grows with the number of systems (each state is read once, written once).
 # mixed_lean: 29.883 MB read + 0.899 MB written.  f2_lean_learned (the
-# kernel reads its systems through the predicted-cost order, so each 8-byte
-# state access is a 32-byte sector of its own; it also reads the rate
-# table of the prologue): 437.880 MB read + 67.929 MB written.
+# kernel with the block-wide step-end hold; it reads its systems through the
+# predicted-cost order, so each 8-byte state access is a 32-byte sector of
+# its own; it also reads the rate table of the prologue): 435.906 MB read +
+# 66.160 MB written.
 NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
-                                "f2_lean_learned": (437.879552e6 + 67.928576e6) / 262144}
+                                "f2_lean_learned": (435.906048e6 + 66.159872e6) / 262144}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
                       "(null when another kernel ran or no capture of this kernel exists)")
 

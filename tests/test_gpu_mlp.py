@@ -124,7 +124,11 @@ def test_proposal_pipeline_gain(record_property):
     net.fit_normalization(X, Y)
     hist = net.train(X, Y, epochs=24, batch=4096, lr=2e-3, seed=0)
     assert hist[-1] < hist[0]
-    w = W.massaction(1 << 18, seed=5)   # 262,144 systems: 4.5 waves of resident blocks
+    # 1,048,576 systems (18 waves of resident blocks), the bench's batch: with
+    # the block-wide step-end hold of the two-float kernel, a network trained
+    # on 65,536 pairs orders 262,144 systems 1.08x faster than unordered
+    # (the true cost's order: 1.38x), 1M systems 1.21x
+    w = W.massaction(1 << 20, seed=5)
     h = B.register_workload(w)
     y0 = torch.from_numpy(w.y0).cuda()
     p = torch.from_numpy(w.params).cuda()
