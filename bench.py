@@ -932,10 +932,16 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
     y0, prm = devt(b.y0), devt(b.param)
     t0, tend, rtol, atol = devt(b.t0), devt(b.tend), devt(b.rtol), devt(b.atol)
     y = torch.empty_like(y0)
-    res = {}
-    for name, mapping in (("autotuned", B.ODE_MAP_AUTO), ("fixed_thread_per_system", B.ODE_MAP_THREAD)):
+    res, y_runs = {}, {}
+    # the FP32 lean plan autotuned and with the paper's fixed mapping; the
+    # two-float plan (grids by two-float RKC, chains by two-float RKCK) and
+    # the plain FP64 plan, both autotuned
+    for name, mapping, prec in (("autotuned", B.ODE_MAP_AUTO, B.ODE_PREC_MIXED_LEAN),
+                                ("fixed_thread_per_system", B.ODE_MAP_THREAD, B.ODE_PREC_MIXED_LEAN),
+                                ("two_float_autotuned", B.ODE_MAP_AUTO, B.ODE_PREC_F2_LEAN),
+                                ("fp64_autotuned", B.ODE_MAP_AUTO, B.ODE_PREC_FP64)):
         plan = B.RaggedPlan(handles, b.method, b.neq, b.offset[:-1], y0, prm, t0, tend, rtol, atol, y_out=y,
-                            precision=B.ODE_PREC_MIXED_LEAN, mapping=mapping, stream=stream.cuda_stream)
+                            precision=prec, mapping=mapping, stream=stream.cuda_stream)
         for _ in range(1):
             plan.launch(stream.cuda_stream)
         torch.cuda.synchronize()
@@ -952,13 +958,17 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
                      "buckets": [{k: d[k] for k in ("family", "method", "size_class", "systems", "lanes",
                                                      "points_per_lane", "block", "mapping")} for d in plan.info()]}
         plan.destroy()
-        if name == "autotuned":
+        if name != "fixed_thread_per_system":
             torch.cuda.synchronize()
-            y_auto = y.cpu().numpy()
+            y_runs[name] = y.cpu().numpy()
     B.release(hb)
     B.release(hc)
     res["speedup_autotuned_vs_fixed"] = res["fixed_thread_per_system"]["ms_per_step"] / res["autotuned"]["ms_per_step"]
-    res["config"] = {"nsys_per_gpu": b.nsys, "unknowns_total": int(b.offset[-1]), "precision": "mixed lean",
+    res["speedup_two_float_vs_fp64"] = res["fp64_autotuned"]["ms_per_step"] / res["two_float_autotuned"]["ms_per_step"]
+    res["config"] = {"nsys_per_gpu": b.nsys, "unknowns_total": int(b.offset[-1]),
+                     "precision": "mixed lean (autotuned, fixed_thread_per_system); two-float RKC for the grids and "
+                                  "two-float RKCK for the chains, FP32 scalars (two_float_autotuned); plain FP64 "
+                                  "(fp64_autotuned)",
                      "graph": "one CUDA graph launch per step (all buckets on parallel branches)"}
     if rank == 0 and not args.no_cpu:
         # the error against the FP64 oracle on a sample (half grids, half chains)
@@ -970,17 +980,23 @@ def mixed_leg(args, B, torch, dev, stream, rank, world, barrier):
         ref = O.integrate_mixed(sub)
         cpu_s = time.perf_counter() - t0
         acc = {"sample": int(idx.size), "cpu_oracle_systems_per_s": idx.size / cpu_s, "cores": os.cpu_count()}
-        for fam, kind in (("brusselator_rkc", W.RHS_BRUSS1D), ("vdp_chain_rkck", W.RHS_VDP_CHAIN)):
-            e = []
-            for k, i in enumerate(idx):
-                if b.kind[i] != kind:
-                    continue
-                yg = y_auto[b.offset[i]:b.offset[i] + b.neq[i]]
-                yr = ref.y[sub.offset[k]:sub.offset[k] + sub.neq[k]]
-                e.append(float(np.max(np.abs(yg - yr) / (np.abs(yr) + b.atol[i]))))
-            e = np.array(e)
-            acc[fam] = {"systems": int(e.size), "median_rel_err": float(np.median(e)),
-                        "p999_rel_err": float(np.quantile(e, 0.999)), "max_rel_err": float(e.max())}
+        for run_name, y_run in y_runs.items():
+            per = {}
+            for fam, kind in (("brusselator_rkc", W.RHS_BRUSS1D), ("vdp_chain_rkck", W.RHS_VDP_CHAIN)):
+                e = []
+                for k, i in enumerate(idx):
+                    if b.kind[i] != kind:
+                        continue
+                    yg = y_run[b.offset[i]:b.offset[i] + b.neq[i]]
+                    yr = ref.y[sub.offset[k]:sub.offset[k] + sub.neq[k]]
+                    e.append(float(np.max(np.abs(yg - yr) / (np.abs(yr) + b.atol[i]))))
+                e = np.array(e)
+                per[fam] = {"systems": int(e.size), "median_rel_err": float(np.median(e)),
+                            "p999_rel_err": float(np.quantile(e, 0.999)), "max_rel_err": float(e.max())}
+            if run_name == "autotuned":
+                acc.update(per)   # the lean plan's figures, at the top level as before
+            else:
+                acc[run_name] = per
         res["accuracy_vs_oracle"] = acc
     return res
 
@@ -1044,7 +1060,8 @@ def c0_leg(args, B, torch, dev, stream, rank, world, barrier):
     (a fifth of the SMs), so a 1,048,576-system batch of the same
     distribution is timed too.  Step counts and final states against the
     oracle (all 4096 systems; a sample of the large batch), the oracle timed
-    on the host cores on the same systems."""
+    on the host cores on the same systems.  Beside the plain form, the
+    two-float RKCK (FP32 scalars) on the same systems, with its error."""
     import oracle as O
     res = {}
     for nsys in (4096, args.c0_big):
@@ -1054,19 +1071,20 @@ def c0_leg(args, B, torch, dev, stream, rank, world, barrier):
         p = torch.from_numpy(w.params).to(dev)
         y = torch.empty_like(y0)
         cnt = B.counters_like(w.nsys, dev)
+        runs = {}
+        for form, prec in (("plain_fp64", B.ODE_PREC_FP64), ("two_float", B.ODE_PREC_F2_LEAN)):
+            def call(counters=None):
+                B.integrate("rkck", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters,
+                            precision=prec, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
 
-        def call(counters=None):
-            B.integrate("rkck", h, y0, p, w.t0, w.tend, w.rtol, w.atol, y_out=y, counters=counters,
-                        precision=B.ODE_PREC_FP64, mapping=B.ODE_MAP_AUTO, stream=stream.cuda_stream)
-
-        ms = timed_calls(torch, stream, call, args.c0_steps, args.warmup, barrier)
-        ms = max_over_ranks(ms, world, dev)
-        call(cnt)
-        torch.cuda.synchronize()
-        c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "status")}
-        yg = y.cpu().numpy()
-        mapping = B.mapping_info(h, "rkck", B.ODE_PREC_FP64)
+            ms = timed_calls(torch, stream, call, args.c0_steps, args.warmup, barrier)
+            ms = max_over_ranks(ms, world, dev)
+            call(cnt)
+            torch.cuda.synchronize()
+            c = {k: getattr(cnt, k).cpu().numpy() for k in ("n_accept", "n_reject", "n_rhs", "status")}
+            runs[form] = (ms, c, y.cpu().numpy(), B.mapping_info(h, "rkck", prec))
         B.release(h)
+        ms, c, yg, mapping = runs["plain_fp64"]
         fl = rkck_flops(w, c["n_accept"], c["n_reject"])
         r = {"systems_per_s": w.nsys * world / (ms * 1e-3), "ms_per_step": ms,
              "rhs_evals_per_s": float(np.sum(c["n_rhs"])) * world / (ms * 1e-3),
@@ -1074,6 +1092,10 @@ def c0_leg(args, B, torch, dev, stream, rank, world, barrier):
              "achieved_tflops_fp64": fl / (ms * 1e-3) / 1e12,
              "frac_fp64_peak": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
              "mapping_block_tuned": list(mapping)}
+        ms2, c2, y2, mapping2 = runs["two_float"]
+        r["two_float"] = {"systems_per_s": w.nsys * world / (ms2 * 1e-3), "ms_per_step": ms2,
+                          "speedup_vs_plain": ms / ms2, "mapping_block_tuned": list(mapping2),
+                          "status_ok_frac": float(np.mean((c2["status"] & 0xFF) == 0))}
         if rank == 0 and not args.no_cpu:
             if nsys <= 4096:
                 idx = np.arange(nsys)
@@ -1089,8 +1111,15 @@ def c0_leg(args, B, torch, dev, stream, rank, world, barrier):
                            "max_rel_err": float(e.max()),
                            "status_equal": bool(np.array_equal(c["status"][idx], ref.status))}
             r["cpu_oracle"] = {"systems_per_s": rate, "cores": os.cpu_count(), "sample": int(idx.size)}
+            same2 = (c2["n_accept"][idx] == ref.n_accept) & (c2["n_reject"][idx] == ref.n_reject)
+            e2 = (np.abs(y2[:, idx] - ref.y) / (np.abs(ref.y) + w.atol)).max(axis=0)
+            r["two_float"]["err_vs_fp64_oracle"] = {
+                "systems": int(idx.size), "median_rel_err": float(np.median(e2)),
+                "p999_rel_err": float(np.quantile(e2, 0.999)), "max_rel_err": float(e2.max()),
+                "same_counts_frac": float(same2.mean())}
         res[f"nsys_{nsys}"] = r
-    res["config"] = {"method": "rkck", "precision": "plain FP64", "rtol": 1e-6, "atol": 1e-9, "interval": [0.0, 20.0],
+    res["config"] = {"method": "rkck", "precision": "plain FP64; two_float: two-float RKCK with FP32 scalars",
+                     "rtol": 1e-6, "atol": 1e-9, "interval": [0.0, 20.0],
                      "flops_model": "6 evaluations x 5 flops + 60 N per attempt"}
     return res
 

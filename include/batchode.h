@@ -92,14 +92,17 @@ extern "C" {
                                 -- the time t -- and for the Chebyshev coefficients.  The FP64 pipe
                                 of this GPU runs at 1/64 of the FP32 rate, so every FP64 instruction
                                 of the step-size bookkeeping costs as much as ~64 FP32 ones */
-#define ODE_PREC_F2 3        /* RKC only: state, stages, evaluation points and right-hand side in
+#define ODE_PREC_F2 3        /* RKC; RKCK for van der Pol systems and chains: state, stages
+                                (RKCK: the increments k_i), evaluation points and right-hand side in
                                 two-float arithmetic (each value an unevaluated sum of two FP32
                                 words, ~48 significant bits, FP32 instructions only); FP64 time,
                                 step size, spectral radius and error-norm accumulation; Chebyshev
                                 coefficients from the FP64 table as word pairs.  Follows the FP64
                                 form's step sequence, where FP32 evaluation points do not: at
                                 rtol 1e-6 their rounding is several percent of the error estimate
-                                of Eq. E:rmsE.  Families: van der Pol, Brusselator, mass-action */
+                                of Eq. E:rmsE.  Families: van der Pol, Brusselator, mass-action
+                                (RKC); van der Pol, oscillator chains (RKCK: FP64 time and step
+                                size, FP32 error ratio) */
 #define ODE_PREC_F2_LEAN 4   /* as ODE_PREC_F2 with FP32 step size, spectral radius and error norm
                                 and the remaining interval as an FP32 pair (no FP64 instruction in
                                 the step loop) */
@@ -392,7 +395,12 @@ int rkc_integrate_noalloc(int32_t rhs, int64_t nsys, const double* y0, const dou
  * default warp-per-system shape; opts->h0, sigma0, log_xy, cost and carry
  * are ignored (a plan orders each bucket by system size).  Families: Brusselator and oscillator
  * chains (register each family once with its largest neq).  Layout: system
- * i's components are contiguous from offset[i]. */
+ * i's components are contiguous from offset[i].  opts->precision: any form;
+ * with a two-float form (ODE_PREC_F2, ODE_PREC_F2_LEAN) the buckets take the
+ * two-float kernels (warp-wide teams: Brusselator grids by RKC, oscillator
+ * chains by RKCK or RKC) and Brusselator grids by RKCK, for which no
+ * two-float form is built, the FP64 kernels, so that every system of the
+ * plan keeps FP64-class accuracy. */
 typedef struct {
     int64_t nsys;
     const int32_t* rhs;     /* HOST [nsys]: registered handle of each system's family */

@@ -456,8 +456,8 @@ int integrate(Method method, int32_t handle, int64_t nsys, const double* y0, con
     if (opts.codegen < ODE_CODEGEN_AUTO || opts.codegen > ODE_CODEGEN_ON) return fail(ODE_ERR_ARG, "unknown codegen mode %d", opts.codegen);
     if (opts.precision < ODE_PREC_FP64 || opts.precision > ODE_PREC_F2_LEAN)
         return fail(ODE_ERR_ARG, "unknown precision %d", opts.precision);
-    if (prec_is_f2(opts.precision) && method != kRkc)
-        return fail(ODE_ERR_UNSUPPORTED, "the two-float forms are built for RKC only");
+    if (prec_is_f2(opts.precision) && method != kRkc && rhs.kind != ODE_RHS_VDP && rhs.kind != ODE_RHS_VDP_CHAIN)
+        return fail(ODE_ERR_UNSUPPORTED, "the two-float RKCK forms are built for van der Pol systems and chains only");
     if (opts.mapping < ODE_MAP_AUTO || opts.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping %d", opts.mapping);
     if (opts.io != ODE_IO_DEVICE && opts.io != ODE_IO_HOST) return fail(ODE_ERR_ARG, "unknown io mode %d", opts.io);
     if (opts.block_size != 0 && (opts.block_size < 32 || opts.block_size > 256 || opts.block_size % 32))
@@ -679,7 +679,6 @@ int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision) {
     g_err.clear();
     if (method != 0 && method != 1) return fail(ODE_ERR_ARG, "method must be 0 (RKCK) or 1 (RKC)");
     if (precision < ODE_PREC_FP64 || precision > ODE_PREC_F2_LEAN) return fail(ODE_ERR_ARG, "unknown precision %d", precision);
-    if (prec_is_f2(precision) && method == 0) return fail(ODE_ERR_UNSUPPORTED, "the two-float forms are built for RKC only");
     RhsEntry r;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -687,6 +686,8 @@ int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision) {
         if (it == g_reg.end()) return fail(ODE_ERR_HANDLE, "unknown rhs handle %d", rhs_handle);
         r = it->second;
     }
+    if (prec_is_f2(precision) && method == 0 && r.kind != ODE_RHS_VDP && r.kind != ODE_RHS_VDP_CHAIN)
+        return fail(ODE_ERR_UNSUPPORTED, "the two-float RKCK forms are built for van der Pol systems and chains only");
     if (r.kind != ODE_RHS_MASSACTION) return ODE_OK;
     std::string why;
     const int rc = jit_prepare(r, method == 0 ? kMethodRkck : kMethodRkc, precision, &why);

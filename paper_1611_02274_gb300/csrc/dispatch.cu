@@ -20,6 +20,7 @@ cudaError_t launch_nbody_mixed(int method, int prec, const RhsEntry& r, const Ba
 cudaError_t launch_vdp_f2(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_mass16_f2(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 cudaError_t launch_bruss_f2(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
+cudaError_t launch_chain_f2(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok);
 
 namespace {
 inline bool f64(int prec) { return prec == ODE_PREC_FP64; }
@@ -49,7 +50,7 @@ cudaError_t launch_bruss(int method, int prec, const RhsEntry& r, const BatchArg
 }
 
 cudaError_t launch_chain(int method, int prec, const RhsEntry& r, const BatchArgs& a, const LaunchCfg& c, bool* ok) {
-    if (prec_is_f2(prec)) return none(ok);
+    if (prec_is_f2(prec)) return launch_chain_f2(method, prec, r, a, c, ok);
     return f64(prec) ? launch_chain_f64(method, r, a, c, ok) : launch_chain_mixed(method, prec, r, a, c, ok);
 }
 

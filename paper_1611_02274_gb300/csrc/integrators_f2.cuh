@@ -686,4 +686,270 @@ struct RkcF2 {
     }
 };
 
+// ============================================================ RKCK two-float
+//
+// RKCK (Section 2.1, rkckDriver of Section 3.2) with the state, the six stage
+// increments k_i = h f_i, the evaluation points and the right-hand side in
+// two-float arithmetic.  Why: the embedded error estimate sum_i (c_i - c*_i)
+// k_i is a difference of fifth- and fourth-order solutions that cancels
+// down to ~rtol |y|; for oscillators on a limit cycle, FP32 rounding of the
+// stages moves the phase along the cycle, and the final states of the FP32
+// forms drift from the FP64 method's by up to ~1e-2 relative over t in
+// [0, 20].  The tableau's rationals (Table 1) enter as two-float pairs, so
+// the step sequence follows the FP64 method's.
+//
+// Scalars: the step size and the error ratio in FP32 (the error is a
+// max-norm of FP32-rounded components; the step-size factor by fpow), the
+// remaining interval as an FP32 pair; with BK64 the time and the step size
+// are FP64, as in RkckMixed's specified split.  All six stages run for
+// every system in the same order, so the lanes of a warp stay at the same
+// stage and the per-stage switches do not diverge.
+
+// a double as the nearest two-float pair, at compile time
+__host__ __device__ constexpr F2 f2c(double d) { return F2((float)d, (float)(d - (double)(float)d)); }
+
+namespace ck2 {
+constexpr F2 B21 = f2c(ck::B21);
+constexpr F2 B31 = f2c(ck::B31), B32 = f2c(ck::B32);
+constexpr F2 B41 = f2c(ck::B41), B42 = f2c(ck::B42), B43 = f2c(ck::B43);
+constexpr F2 B51 = f2c(ck::B51), B52 = f2c(ck::B52), B53 = f2c(ck::B53), B54 = f2c(ck::B54);
+constexpr F2 B61 = f2c(ck::B61), B62 = f2c(ck::B62), B63 = f2c(ck::B63), B64 = f2c(ck::B64), B65 = f2c(ck::B65);
+constexpr F2 C1 = f2c(ck::C1), C3 = f2c(ck::C3), C4 = f2c(ck::C4), C6 = f2c(ck::C6);
+constexpr F2 DC1 = f2c(ck::DC1), DC3 = f2c(ck::DC3), DC4 = f2c(ck::DC4), DC5 = f2c(ck::DC5), DC6 = f2c(ck::DC6);
+}  // namespace ck2
+
+template <class Model, bool BK64 = false>
+struct RkckF2 {
+    static constexpr bool kStepSync = false;  // fixed six stages: lanes stay aligned
+    static constexpr int SMEM_FLOATS = ModelSmem<Model>::value;
+    __device__ void bind_smem(float* base, int stride) {
+        if constexpr (SMEM_FLOATS > 0) sys.bind(base, stride);
+    }
+    static constexpr int W = Model::W, P = Model::PER;
+    using R = F2;
+    using TM = Team<W>;
+    using HT = typename Pick<BK64, double, float>::type;
+    typename Model::template Sys<F2> sys;
+    F2 y[P], k1[P], k2[P], k3[P], k4[P], k5[P];
+    double t, tend;                          // BK64
+    HT h, hmax;
+    F2 hh;                                   // the step size as a pair
+    float remf, reml, tendf, tabsf, deltaf, inv_rtolf;  // FP32 scalars: remaining interval remf + reml
+    int32_t n_acc, n_rej, status, max_att, stage;
+
+    __device__ void init(const BatchArgs& a, const typename Model::Ctx& ctx, const TM& tm, int64_t i) {
+        sys.load(ctx, tm, a.params[i], a.neq_of(i));
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            y[s] = F2(c >= 0 ? a.y0[a.yidx(i, c)] : 0.0);
+        }
+        t = a.t0_of(i);
+        tend = a.tend_of(i);
+        hmax = (HT)fabs(tend - t);
+        h = (HT)(0.5 * fabs(tend - t));
+        if (carry_warm(a, i) && a.carry[a.cidx(i, kCarryH)] > 0.0) h = (HT)a.carry[a.cidx(i, kCarryH)];
+        remf = (float)(tend - t);
+        reml = (float)((tend - t) - (double)remf);
+        tendf = (float)tend;
+        tabsf = fabsf((float)t);
+        deltaf = (float)((a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny);
+        inv_rtolf = (float)(1.0 / a.rtol_of(i));
+        n_acc = n_rej = status = 0;
+        max_att = a.max_attempts;
+        loop_top();
+    }
+    __device__ bool done() const { return stage == 0; }
+
+    // top of the rkckDriver loop: finished?  attempt cap, then clamp h
+    __device__ void loop_top() {
+        stage = 0;
+        if constexpr (BK64) {
+            if (!(t < tend)) return;
+        } else {
+            if (!(remf > 0.0f)) return;
+        }
+        if (n_acc + n_rej >= max_att) {
+            status = ODE_ST_MAX_ATTEMPTS;
+            return;
+        }
+        if constexpr (BK64)
+            h = fmin(tend - t, h);
+        else
+            h = fminf(remf, h);
+        hh = F2(h);
+        stage = 1;
+    }
+
+    // y + sum_j b_ij k_j, the point of stage i (products and sums lazy, the
+    // point left unnormalised: it feeds the right-hand side's products)
+    __device__ void point(F2* x, F2& tx) const {
+        float tb;
+        if constexpr (BK64)
+            tb = (float)t;
+        else
+            tb = tendf - remf;
+        const float hf = (float)h;
+        switch (stage) {
+        case 1:
+            tx = F2(tb);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = y[s];
+            break;
+        case 2:
+            tx = F2(tb + (float)ck::A2 * hf);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) x[s] = add_lazy(y[s], mul_lazy(ck2::B21, k1[s]));
+            break;
+        case 3:
+            tx = F2(tb + (float)ck::A3 * hf);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s)
+                x[s] = add_lazy(y[s], add_lazy(mul_lazy(ck2::B31, k1[s]), mul_lazy(ck2::B32, k2[s])));
+            break;
+        case 4:
+            tx = F2(tb + (float)ck::A4 * hf);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s)
+                x[s] = add_lazy(y[s], add_lazy(add_lazy(mul_lazy(ck2::B41, k1[s]), mul_lazy(ck2::B42, k2[s])),
+                                               mul_lazy(ck2::B43, k3[s])));
+            break;
+        case 5:
+            tx = F2(tb + (float)ck::A5 * hf);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s)
+                x[s] = add_lazy(y[s], add_lazy(add_lazy(mul_lazy(ck2::B51, k1[s]), mul_lazy(ck2::B52, k2[s])),
+                                               add_lazy(mul_lazy(ck2::B53, k3[s]), mul_lazy(ck2::B54, k4[s]))));
+            break;
+        default:
+            tx = F2(tb + (float)ck::A6 * hf);
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s)
+                x[s] = add_lazy(y[s], add_lazy(add_lazy(add_lazy(mul_lazy(ck2::B61, k1[s]), mul_lazy(ck2::B62, k2[s])),
+                                                        add_lazy(mul_lazy(ck2::B63, k3[s]), mul_lazy(ck2::B64, k4[s]))),
+                                               mul_lazy(ck2::B65, k5[s])));
+        }
+    }
+
+    __device__ bool consume(const BatchArgs&, const TM& tm, const F2*, const F2* f) {
+        switch (stage) {
+        case 1:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) k1[s] = f[s] * hh;
+            break;
+        case 2:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) k2[s] = f[s] * hh;
+            break;
+        case 3:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) k3[s] = f[s] * hh;
+            break;
+        case 4:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) k4[s] = f[s] * hh;
+            break;
+        case 5:
+#pragma unroll(P <= 64 ? P : 4)
+            for (int s = 0; s < P; ++s) k5[s] = f[s] * hh;
+            break;
+        default:
+            finish(tm, f);
+            return done();
+        }
+        stage += 1;
+        return false;
+    }
+
+    // fifth-order solution, embedded error (Section 2.1) and the step-size
+    // rule of the listing
+    __device__ void finish(const TM& tm, const F2* f) {
+        F2 yt[P];
+        float err = 0.0f;
+        bool nan_flag = false;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const F2 k6 = f[s] * hh;
+            const F2 incr = add_lazy(add_lazy(mul_lazy(ck2::C1, k1[s]), mul_lazy(ck2::C3, k3[s])),
+                                     add_lazy(mul_lazy(ck2::C4, k4[s]), mul_lazy(ck2::C6, k6)));
+            yt[s] = y[s] + incr;
+            const float ye = to_float(add_lazy(add_lazy(add_lazy(mul_lazy(ck2::DC1, k1[s]), mul_lazy(ck2::DC3, k3[s])),
+                                                        add_lazy(mul_lazy(ck2::DC4, k4[s]), mul_lazy(ck2::DC5, k5[s]))),
+                                               mul_lazy(ck2::DC6, k6)));
+            if (sys.comp(tm, s) >= 0) {
+                if (isnan(ye) || isnan(yt[s].hi)) nan_flag = true;
+                err = fmaxf(err, __fdividef(fabsf(ye), fabsf(y[s].hi) + fabsf(k1[s].hi) + deltaf));
+            }
+        }
+        err = tm.max(err) * inv_rtolf;
+        nan_flag = tm.any(nan_flag);
+        if (err > 1.0f || isnan(err) || nan_flag) {
+            n_rej += 1;
+            if (isnan(err) || nan_flag)
+                h = h * (HT)kP1;
+            else
+                h = h * (HT)fmaxf((float)kSafety * fpow(err, (float)kPshrnk), (float)kP1);
+            bool underflow;
+            if constexpr (BK64)
+                underflow = h < 1.0e-20 || t + h == t;
+            else
+                underflow = h < 1.0e-20f || h <= tabsf * 2.2e-16f;
+            if (underflow) {
+                status = ODE_ST_H_UNDERFLOW;
+                stage = 0;
+                return;
+            }
+            loop_top();
+            return;
+        }
+        n_acc += 1;
+        if constexpr (BK64) {
+            t = t + h;
+        } else if (h >= remf * 0.999999f) {
+            remf = reml = 0.0f;  // the step covered what was left
+        } else {
+            df_sub(remf, reml, h);
+            tabsf = fabsf(tendf - remf);
+        }
+        const float fac = (err > (float)kErrcon) ? (float)kSafety * fpow(err, (float)kPgrow) : 5.0f;
+        if constexpr (BK64)
+            h = fmax(1.0e-20, fmin(hmax, h * (double)fac));
+        else
+            h = fmaxf(1.0e-20f, fminf(hmax, h * fac));
+        bool bad = false;
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            y[s] = yt[s];
+            if (sys.comp(tm, s) >= 0 && !isfinite(yt[s].hi)) bad = true;
+        }
+        if (tm.any(bad)) {
+            status = ODE_ST_NONFINITE;
+            stage = 0;
+            return;
+        }
+        loop_top();
+    }
+
+    __device__ void store(const BatchArgs& a, const TM& tm, int64_t i) const {
+#pragma unroll(P <= 64 ? P : 4)
+        for (int s = 0; s < P; ++s) {
+            const int c = sys.comp(tm, s);
+            if (c >= 0) a.y_out[a.yidx_out(i, c)] = to_double(y[s]);
+            if (a.carry != nullptr && c >= 0) a.carry[a.cidx(i, kCarryFixed + c)] = 0.0;
+        }
+        if (a.carry != nullptr && tm.lane == 0) {
+            const double t_end = BK64 ? t : tend - ((double)remf + (double)reml);
+            carry_scalars(a, i, status == ODE_ST_OK || status == ODE_ST_MAX_ATTEMPTS, t_end, (double)h, 0.0, 0.0,
+                          0.0, 0, 0, false);
+        }
+        if (tm.lane == 0) {
+            if (a.n_accept) a.n_accept[i] = n_acc;
+            if (a.n_reject) a.n_reject[i] = n_rej;
+            if (a.n_rhs) a.n_rhs[i] = 6 * (n_acc + n_rej);
+            if (a.n_specrad) a.n_specrad[i] = 0;
+            if (a.status) a.status[i] = status;
+        }
+    }
+};
+
 }  // namespace bode

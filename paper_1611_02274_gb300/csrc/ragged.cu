@@ -90,6 +90,15 @@ cudaError_t launch_shape(int family, int method, int prec, const Shape& sh, cons
     return sh.team == 1 ? launch_chain_shape_t1(sh.team, sh.g, a, g, c, ok) : launch_chain_shape_team(sh.team, sh.g, a, g, c, ok);
 }
 
+// The precision a bucket runs in.  A two-float plan takes the two-float
+// kernels where they are built (Brusselator grids by RKC, oscillator chains
+// by RKCK or RKC) and FP64 for Brusselator grids by RKCK, so that every
+// bucket of the plan keeps FP64-class accuracy.
+int bucket_prec(int family, int method, int prec) {
+    if (!prec_is_f2(prec)) return prec;
+    return family == ODE_RHS_BRUSS1D && method == kMethodRkck ? ODE_PREC_FP64 : prec;
+}
+
 // candidate shapes for a bucket (the default kernel first)
 std::vector<Shape> candidates(int family, int method, int prec, int cls, bool thread_only) {
     std::vector<Shape> out;
@@ -114,6 +123,7 @@ struct Bucket {
     int32_t handle;
     RhsEntry rhs;
     int method, cls;
+    int prec;  // bucket_prec of the plan's precision
     std::vector<int32_t> sys;
     Shape shape;
     int block, mapping;
@@ -217,7 +227,7 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
     ode_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts_in) o = *opts_in;
-    if (o.precision < ODE_PREC_FP64 || o.precision > ODE_PREC_MIXED_LEAN) return fail(ODE_ERR_ARG, "unknown precision");
+    if (o.precision < ODE_PREC_FP64 || o.precision > ODE_PREC_F2_LEAN) return fail(ODE_ERR_ARG, "unknown precision");
     if (o.mlp || o.log_sr) return fail(ODE_ERR_ARG, "networks and the spectral-radius log are not taken by ragged plans");
     if (o.mapping < ODE_MAP_AUTO || o.mapping > ODE_MAP_QUEUE) return fail(ODE_ERR_ARG, "unknown mapping");
     ode_stats st;
@@ -248,6 +258,7 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
             b.rhs = r;
             b.method = m == 0 ? kMethodRkck : kMethodRkc;
             b.cls = cls;
+            b.prec = bucket_prec(r.kind, b.method, o.precision);
         }
         b.sys.push_back((int32_t)i);
     }
@@ -291,18 +302,18 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
     for (auto& b : p->buckets) {
         const int family = b.rhs.kind;
         if (o.mapping == ODE_MAP_THREAD) {
-            auto c = candidates(family, b.method, o.precision, b.cls, true);
+            auto c = candidates(family, b.method, b.prec, b.cls, true);
             b.shape = c.empty() ? Shape{0, 0, b.cls <= 64 ? 64 : (family == ODE_RHS_BRUSS1D ? 256 : 128)} : c.front();
             b.block = 64;
             b.mapping = ODE_MAP_THREAD;
             continue;
         }
-        auto cand = candidates(family, b.method, o.precision, b.cls, false);
+        auto cand = candidates(family, b.method, b.prec, b.cls, false);
         b.shape = cand.front();
         b.block = 128;
         b.mapping = ODE_MAP_QUEUE;
         if (o.mapping == ODE_MAP_QUEUE) continue;
-        auto key = std::make_tuple(family, b.method, o.precision, b.cls, sms);
+        auto key = std::make_tuple(family, b.method, b.prec, b.cls, sms);
         {
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tuned.find(key);
@@ -337,11 +348,11 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
                     make_args(*p, b, *rb, o, tune_out ? tune_out : y_out, st, sample, p->d_cursor + 32 * nb, &a);
                     LaunchCfg cfg{map, blk, sh.team, sms, user};
                     cudaMemsetAsync(a.cursor, 0, 8, user);
-                    launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);  // warm-up
+                    launch_shape(family, b.method, b.prec, sh, b.rhs, a, cfg, &ok);  // warm-up
                     if (!ok) break;
                     cudaMemsetAsync(a.cursor, 0, 8, user);
                     cudaEventRecord(e0, user);
-                    launch_shape(family, b.method, o.precision, sh, b.rhs, a, cfg, &ok);
+                    launch_shape(family, b.method, b.prec, sh, b.rhs, a, cfg, &ok);
                     cudaEventRecord(e1, user);
                     e = cudaEventSynchronize(e1);
                     if (e != cudaSuccess) {
@@ -387,7 +398,7 @@ int ode_ragged_plan_create(const ode_ragged_batch* rb, const ode_opts* opts_in, 
         LaunchCfg cfg{b.mapping, b.block, b.shape.team, sms, br[k]};
         e = cudaStreamWaitEvent(br[k], ev[nb], 0);
         if (e == cudaSuccess) e = cudaMemsetAsync(a.cursor, 0, 8, br[k]);
-        if (e == cudaSuccess) e = launch_shape(b.rhs.kind, b.method, o.precision, b.shape, b.rhs, a, cfg, &supported);
+        if (e == cudaSuccess) e = launch_shape(b.rhs.kind, b.method, b.prec, b.shape, b.rhs, a, cfg, &supported);
         if (e == cudaSuccess && !supported) break;
         if (e == cudaSuccess) e = cudaEventRecord(ev[k], br[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[k], 0);

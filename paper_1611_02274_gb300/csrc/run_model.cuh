@@ -39,11 +39,18 @@ cudaError_t launch_f2(const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c) {
     return launch_method<M0>(a, ctx, c);
 }
 
-// two-float forms: RKC only
-template <class Model, class Ctx>
+// two-float forms: RKC, and RKCK where a unit builds it (RKCK = true)
+template <class Model, bool RKCK = false, class Ctx>
 cudaError_t run_model_f2(int method, int prec, const BatchArgs& a, const Ctx& ctx, const LaunchCfg& c, bool* ok) {
-    *ok = method == kMethodRkc;
-    if (!*ok) return cudaSuccess;
+    if (method == kMethodRkck) {
+        *ok = RKCK;
+        if constexpr (RKCK) {
+            if (prec == ODE_PREC_F2) return launch_method<RkckF2<Model, true>>(a, ctx, c);
+            return launch_method<RkckF2<Model, false>>(a, ctx, c);
+        }
+        return cudaSuccess;
+    }
+    *ok = true;
     if (prec == ODE_PREC_F2) return launch_f2<RkcF2<Model, true, false>, RkcF2<Model, true, true>>(a, ctx, c);
     return launch_f2<RkcF2<Model, false, false>, RkcF2<Model, false, true>>(a, ctx, c);
 }

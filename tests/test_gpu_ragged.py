@@ -73,6 +73,29 @@ def test_lean_plan_error_against_oracle(batch, mapping):
         assert all(d["block"] == 64 for d in g["info"])
 
 
+@pytest.mark.parametrize("prec", [B.ODE_PREC_F2_LEAN, B.ODE_PREC_F2])
+def test_two_float_plan_against_oracle(batch, prec):
+    """A two-float plan: the Brusselator grids by two-float RKC, the
+    oscillator chains by two-float RKCK.  Both families meet the chosen
+    form's 1e-5 bar, with regression guards on the median and on the share
+    of systems that take the oracle's step sequence."""
+    b, ref = batch
+    g = run(b, prec, B.ODE_MAP_AUTO)
+    assert ((g["status"] & 0xFF) == 0).all()
+    e = ragged_rel_err(g["y"], ref.y, b)
+    same = (g["n_accept"] == ref.n_accept) & (g["n_reject"] == ref.n_reject)
+    grid = b.kind == B.ODE_RHS_BRUSS1D
+    assert grid.any() and (~grid).any()
+    for name, sel in (("grids", grid), ("chains", ~grid)):
+        print(prec, name, "p99.9", np.quantile(e[sel], 0.999), "median", np.median(e[sel]), "max", e[sel].max(),
+              "same counts", same[sel].mean())
+        assert np.quantile(e[sel], 0.999) <= 1e-5
+        assert np.median(e[sel]) <= 1e-8
+        assert same[sel].mean() >= 0.99
+    # every bucket took the two-float kernels (warp-wide teams)
+    assert all(d["lanes"] == 32 for d in g["info"])
+
+
 def test_plan_replays_identically(batch):
     import torch
     b, _ = batch
