@@ -96,6 +96,13 @@ FORM_TEXT = {
 # 66.160 MB written.
 NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
                                 "f2_lean_learned": (435.906048e6 + 66.159872e6) / 262144}
+# FP32 pipe use of the chosen kernel from the same capture (ncu --set full)
+NCU_PIPE_CONTEXT = {"f2_lean_learned": {
+    "fma_pipe_cycles_active": 0.548, "issue_active": 0.676, "fp32_thread_inst_per_method_flop": 3.6,
+    # 526.9 G FADD + 2 x 138.2 G FFMA + 50.7 G FMUL thread instructions on 262,144 systems
+    "fp32_flops_executed_per_system": 853.9e9 / 262144,
+    "source": "ncu --set full of k_static<RkcF2> on 262,144 systems of this workload, 128-thread blocks, "
+              "block-wide step-end hold (summary under profiles/)"}}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
                       "(null when another kernel ran or no capture of this kernel exists)")
 
@@ -427,6 +434,17 @@ def run_ours(args):
             out["roofline"]["method_tflops_vs_fp64_peak"] = {
                 "achieved": achieved, "peak_rated": FP64_PEAK_TFLOPS, "peak_measured_fma": peak64,
                 "frac_rated": achieved / FP64_PEAK_TFLOPS, "frac_measured": achieved / peak64}
+        if args.chosen in NCU_PIPE_CONTEXT and amap == B.ODE_MAP_THREAD:
+            # each method flop is several FP32 instructions in two-float
+            # arithmetic: the kernel's own use of the FP32 pipe, from its
+            # ncu capture (context for frac, not a timing)
+            ctx = dict(NCU_PIPE_CONTEXT[args.chosen])
+            # the FP32 flops the kernel executes (FMA = 2, from the capture's
+            # instruction mix, per system) at the live kernel time
+            ex = ctx["fp32_flops_executed_per_system"] * w.nsys / (ms_kernel * 1e-3) / 1e12
+            ctx["fp32_flops_executed_tflops"] = ex
+            ctx["fp32_flops_executed_frac"] = ex / peak32_nominal
+            out["roofline"]["ncu_pipe_context"] = ctx
         forms = {}
         for name, r in runs.items():
             fl = flops[name]

@@ -67,6 +67,17 @@ def test_vdp_rkck_f2(prec, mapping):
 
 
 @pytest.mark.parametrize("prec", F2_FORMS)
+@pytest.mark.parametrize("method", ["rkck", "rkc"])
+@pytest.mark.parametrize("n", [1, 3, 32, 40, 64])
+def test_chain_f2(prec, method, n):
+    # oscillator chains (warp-wide teams, one or two oscillators per lane)
+    # by two-float RKCK and RKC: 40 systems over t in [0, 5]
+    from test_gpu_parity import chain_workload
+    w = chain_workload(40, n, n, W.METHOD_RKCK if method == "rkck" else W.METHOD_RKC)
+    check_f2(w, prec, method=method, p999=BAR, same_frac=0.9, max_bound=BAR, rhs_frac=None)
+
+
+@pytest.mark.parametrize("prec", F2_FORMS)
 @pytest.mark.parametrize("codegen", [B.ODE_CODEGEN_ON, B.ODE_CODEGEN_OFF])
 def test_massaction_f2(prec, codegen):
     # 2048 systems: 16 blocks of 128 threads; generated and generic network code
