@@ -753,8 +753,11 @@ struct RkckF2 {
         reml = (float)((tend - t) - (double)remf);
         tendf = (float)tend;
         tabsf = fabsf((float)t);
-        deltaf = (float)((a.atol_of(i) > 0.0) ? a.atol_of(i) / a.rtol_of(i) : kTiny);
-        inv_rtolf = (float)(1.0 / a.rtol_of(i));
+        // FP32 divisions: in the work queue each lane sets up its own
+        // systems, so FP64 set-up code runs once per system, not per warp
+        const float rtolf = (float)a.rtol_of(i);
+        deltaf = a.atol_of(i) > 0.0 ? (float)a.atol_of(i) / rtolf : (float)kTiny;
+        inv_rtolf = 1.0f / rtolf;
         n_acc = n_rej = status = 0;
         max_att = a.max_attempts;
         loop_top();
