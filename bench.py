@@ -55,28 +55,32 @@ L2_FLUSH_BYTES = 256 << 20
 
 # The precision forms of rkc_integrate (ODE_PREC_*), their kernels and the
 # arithmetic each computes in.
-FORMS = {"f2_lean_learned": 4, "f2_lean": 4, "f2": 3, "mixed_lean": 2, "mixed_spec_split": 1, "plain_fp64": 0}
+FORMS = {"f2_lean_learned": 4, "f2_lean": 4, "f2_learned": 3, "f2": 3, "mixed_lean": 2, "mixed_spec_split": 1,
+         "plain_fp64": 0}
 # forms whose step also runs the learned proposal: the network's pre-pass
 # (spectral-radius bound and cost per system, the Euler trial still setting
 # the first step) and the longest-first order by the predicted cost
-LEARNED_FORMS = {"f2_lean_learned"}
+LEARNED_FORMS = {"f2_lean_learned", "f2_learned"}
 # the precision form underneath (what the other legs run when they take the
 # headline's precision without its proposal)
-BASE_FORM = {"f2_lean_learned": "f2_lean"}
+BASE_FORM = {"f2_lean_learned": "f2_lean", "f2_learned": "f2"}
 # our kernel launches per step: the integration kernel; for the generated
 # two-float forms the rate-constant prologue; for the learned forms the
 # proposal pre-pass and the four kernels of the cost order
-LAUNCHES = {"f2_lean_learned": 7, "f2_lean": 2, "f2": 2, "mixed_lean": 1, "mixed_spec_split": 1, "plain_fp64": 1}
+LAUNCHES = {"f2_lean_learned": 7, "f2_lean": 2, "f2_learned": 7, "f2": 2, "mixed_lean": 1, "mixed_spec_split": 1,
+            "plain_fp64": 1}
 FORM_KERNELS = {"f2_lean_learned": "RkcF2<JitMass, false>", "f2_lean": "RkcF2<JitMass, false>",
-                "f2": "RkcF2<JitMass, true>",
+                "f2_learned": "RkcF2<JitMass, true>", "f2": "RkcF2<JitMass, true>",
                 "mixed_lean": "RkcMixed<JitMass, false>", "mixed_spec_split": "RkcMixed<JitMass, true>",
                 "plain_fp64": "RkcF64<JitMass>"}
-FORM_DTYPES = {"f2_lean_learned": "f32x2", "f2_lean": "f32x2", "f2": "f32x2+f64", "mixed_lean": "f32", "mixed_spec_split": "f32+f64",
+FORM_DTYPES = {"f2_lean_learned": "f32x2", "f2_lean": "f32x2", "f2_learned": "f32x2+f64", "f2": "f32x2+f64", "mixed_lean": "f32", "mixed_spec_split": "f32+f64",
                "plain_fp64": "f64"}
 FORM_TEXT = {
     "f2_lean_learned": "the two-float form (f2_lean) with the learned proposal: a BF16 network's pre-pass gives "
                        "each system's initial spectral-radius bound and predicted cost, and the batch runs "
                        "longest-first by that cost (network trained before timing on held-out seeds)",
+    "f2_learned": "the two-float form with FP64 bookkeeping (f2: the specified split's FP64 time, step size and "
+                  "error-norm reduction) with the learned proposal, as f2_lean_learned",
     "f2_lean": "two-float (FP32 pair, ~48-bit) state, stages, evaluation points and RHS; FP32 step size, spectral "
                "radius and error norm; remaining interval as an FP32 pair; FP64-built coefficients as pairs",
     "f2": "two-float state, stages, evaluation points and RHS; FP64 time, step size, spectral radius and error-norm "
