@@ -550,8 +550,10 @@ struct RkcF2 {
 
     // d_j = mu_j d_{j-1} + nu_j d_{j-2} + mu~_j h f_{j-1} + gamma~_j h F_n
     // (at j = 2, d_0 = 0 and the nu term is an exact zero: skipped).  The
-    // products stay unnormalised and the three- or four-term sum is lazy,
-    // with one renormalisation per component.  At j = 2, d_1 = mu~_1 h F_n,
+    // products and the three- or four-term sum are lazy and d_j stays
+    // unnormalised: every use of it (the next evaluation point, the next
+    // stage's products, the error estimate's separate words, the accepted
+    // state's full sum) takes an unnormalised pair.  At j = 2, d_1 = mu~_1 h F_n,
     // so d_2 = (mu_2 mu~_1 + gamma~_2) h F_n + mu~_2 h f_1: the scalar
     // coefficient once per step, two products and one sum per component
     // (the two-stage step is the one every system takes at tight
@@ -564,7 +566,7 @@ struct RkcF2 {
             const F2 c2h = (mu * cs.mut1f2() + F2(chi.w, clo.w)) * hh;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
-                const F2 dj = normalize(add_lazy(mul_lazy(c2h, Fn[s]), mul_lazy(muth, f[s])));
+                const F2 dj = add_lazy(mul_lazy(c2h, Fn[s]), mul_lazy(muth, f[s]));
                 if (keep) D2s(s, d1[s]);
                 d1[s] = dj;
             }
@@ -572,9 +574,9 @@ struct RkcF2 {
             const F2 gth = F2(chi.w, clo.w) * hh;
 #pragma unroll(P <= 64 ? P : 4)
             for (int s = 0; s < P; ++s) {
-                const F2 dj = normalize(add_lazy(
+                const F2 dj = add_lazy(
                     add_lazy(add_lazy(mul_lazy(mu, d1[s]), mul_lazy(nu, D2g(s))), mul_lazy(muth, f[s])),
-                    mul_lazy(gth, Fn[s])));
+                    mul_lazy(gth, Fn[s]));
                 if (keep) D2s(s, d1[s]);
                 d1[s] = dj;
             }
@@ -594,7 +596,7 @@ struct RkcF2 {
     __device__ void final_consume(const BatchArgs& a, const TM& tm, const F2* x, const F2* f) {
         n_rhs += m;
         const HT ms = weighted_ssq(tm, [&](int s) {
-            const F2 sum = Fn[s] + f[s];
+            const F2 sum = add_lazy(Fn[s], f[s]);  // feeds the product below: left unnormalised
             const float p = hh.hi * sum.hi;
             float e = fmaf(hh.hi, sum.hi, -p);
             e = fmaf(hh.hi, sum.lo, e);
