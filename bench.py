@@ -96,15 +96,15 @@ FORM_TEXT = {
 # mixed_lean: 29.883 MB read + 0.899 MB written.  f2_lean_learned (the
 # kernel with the block-wide step-end hold; it reads its systems through the
 # predicted-cost order, so each 8-byte state access is a 32-byte sector of
-# its own; it also reads the rate table of the prologue): 435.906 MB read +
-# 66.160 MB written.
+# its own; it also reads the rate table of the prologue): 439.148 MB read +
+# 66.671 MB written.
 NCU_TRAFFIC_BYTES_PER_SYSTEM = {"mixed_lean": (29.88288e6 + 0.89856e6) / 262144,
-                                "f2_lean_learned": (435.906048e6 + 66.159872e6) / 262144}
+                                "f2_lean_learned": (439.148032e6 + 66.67136e6) / 262144}
 # FP32 pipe use of the chosen kernel from the same capture (ncu --set full)
 NCU_PIPE_CONTEXT = {"f2_lean_learned": {
-    "fma_pipe_cycles_active": 0.548, "issue_active": 0.676, "fp32_thread_inst_per_method_flop": 3.6,
-    # 526.9 G FADD + 2 x 138.2 G FFMA + 50.7 G FMUL thread instructions on 262,144 systems
-    "fp32_flops_executed_per_system": 853.9e9 / 262144,
+    "fma_pipe_cycles_active": 0.540, "issue_active": 0.670, "fp32_thread_inst_per_method_flop": 3.5,
+    # 506.2 G FADD + 2 x 138.2 G FFMA + 50.7 G FMUL thread instructions on 262,144 systems
+    "fp32_flops_executed_per_system": 833.3e9 / 262144,
     "source": "ncu --set full of k_static<RkcF2> on 262,144 systems of this workload, 128-thread blocks, "
               "block-wide step-end hold (summary under profiles/)"}}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of k_static on 262,144 systems, scaled by the system count "
