@@ -40,6 +40,9 @@ cudaError_t launch_bruss_shape_team(int team, int g, const BatchArgs& a, const G
 cudaError_t launch_bruss_shape_t1(int team, int g, const BatchArgs& a, const GridCtx& ctx, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_shape_team(int team, int g, const BatchArgs& a, const GridCtx& ctx, const LaunchCfg& c, bool* ok);
 cudaError_t launch_chain_shape_t1(int team, int g, const BatchArgs& a, const GridCtx& ctx, const LaunchCfg& c, bool* ok);
+cudaError_t launch_bruss_shape_f2(int team, int g, const BatchArgs& a, const GridCtx& ctx, const LaunchCfg& c, bool* ok);
+cudaError_t launch_chain_shape_f2(int method, int team, int g, const BatchArgs& a, const GridCtx& ctx,
+                                  const LaunchCfg& c, bool* ok);
 }  // namespace bode
 
 using namespace bode;
@@ -72,6 +75,9 @@ struct Shape {
 // (Brusselator grids: RKC, oscillator chains: RKCK)
 const Shape kBrussShapes[] = {{1, 4, 8}, {8, 1, 16}, {16, 1, 32}, {32, 2, 128}, {32, 3, 192}, {1, 128, 256}};
 const Shape kChainShapes[] = {{1, 4, 8}, {8, 1, 16}, {16, 1, 32}, {1, 64, 128}};
+// two-float shapes (FP32 scalars) for the small classes, both families;
+// the warp-wide default kernels take the rest
+const Shape kF2Shapes[] = {{8, 1, 16}, {16, 1, 32}};
 
 bool tuned_method(int family, int method) {
     return (family == ODE_RHS_BRUSS1D && method == kMethodRkc) || (family == ODE_RHS_VDP_CHAIN && method == kMethodRkck);
@@ -85,6 +91,9 @@ cudaError_t launch_shape(int family, int method, int prec, const Shape& sh, cons
         rr.neq = sh.max_neq;  // size of the default kernel to use
         return family == ODE_RHS_BRUSS1D ? launch_bruss(method, prec, rr, a, c, ok) : launch_chain(method, prec, rr, a, c, ok);
     }
+    if (prec == ODE_PREC_F2_LEAN)
+        return family == ODE_RHS_BRUSS1D ? launch_bruss_shape_f2(sh.team, sh.g, a, g, c, ok)
+                                         : launch_chain_shape_f2(method, sh.team, sh.g, a, g, c, ok);
     if (family == ODE_RHS_BRUSS1D)
         return sh.team == 1 ? launch_bruss_shape_t1(sh.team, sh.g, a, g, c, ok) : launch_bruss_shape_team(sh.team, sh.g, a, g, c, ok);
     return sh.team == 1 ? launch_chain_shape_t1(sh.team, sh.g, a, g, c, ok) : launch_chain_shape_team(sh.team, sh.g, a, g, c, ok);
@@ -104,6 +113,11 @@ std::vector<Shape> candidates(int family, int method, int prec, int cls, bool th
     std::vector<Shape> out;
     const int def_max = family == ODE_RHS_BRUSS1D ? (cls <= 64 ? 64 : 256) : (cls <= 64 ? 64 : 128);
     if (!thread_only) out.push_back({0, 0, def_max});
+    if (prec == ODE_PREC_F2_LEAN && !thread_only) {
+        for (const Shape& sh : kF2Shapes)
+            if (sh.max_neq >= cls) out.push_back(sh);
+        return out;
+    }
     if (prec == ODE_PREC_MIXED_LEAN && tuned_method(family, method)) {
         const Shape* s = family == ODE_RHS_BRUSS1D ? kBrussShapes : kChainShapes;
         const int n = family == ODE_RHS_BRUSS1D ? (int)(sizeof(kBrussShapes) / sizeof(Shape))

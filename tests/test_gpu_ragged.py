@@ -92,8 +92,11 @@ def test_two_float_plan_against_oracle(batch, prec):
         assert np.quantile(e[sel], 0.999) <= 1e-5
         assert np.median(e[sel]) <= 1e-8
         assert same[sel].mean() >= 0.99
-    # every bucket took the two-float kernels (warp-wide teams)
-    assert all(d["lanes"] == 32 for d in g["info"])
+    # every bucket took two-float kernels: the warp-wide defaults, or (FP32
+    # scalars, classes of up to 16 points or oscillators) 8- and 16-lane teams
+    lanes = {32} if prec == B.ODE_PREC_F2 else {8, 16, 32}
+    assert all(d["lanes"] in lanes for d in g["info"])
+    assert all(d["lanes"] == 32 for d in g["info"] if d["size_class"] > 32)
 
 
 def test_plan_replays_identically(batch):
