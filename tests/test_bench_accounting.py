@@ -65,3 +65,28 @@ def test_rkck_and_other_families():
 def test_aggregate_rate_is_all_ranks_units_over_the_slowest_time():
     assert bench.aggregate_rate(1 << 20, 1, 52.0) == (1 << 20) / 0.052
     assert bench.aggregate_rate(1 << 20, 8, 52.0) == 8 * (1 << 20) / 0.052
+
+
+def test_every_precision_form_is_described_everywhere():
+    # each form the bench times has its precision code, kernel, dtype,
+    # launch count and description; the learned forms name the form
+    # underneath them, which has the same precision code
+    for table in (bench.FORM_KERNELS, bench.FORM_DTYPES, bench.LAUNCHES, bench.FORM_TEXT):
+        assert set(bench.FORMS) <= set(table)
+    for name in bench.LEARNED_FORMS:
+        base = bench.BASE_FORM[name]
+        assert bench.FORMS[name] == bench.FORMS[base]
+        assert bench.FORM_KERNELS[name] == bench.FORM_KERNELS[base]
+        # proposal pre-pass, four cost-order kernels, rate prologue, integration
+        assert bench.LAUNCHES[name] == bench.LAUNCHES[base] + 5
+    assert bench.FORMS["plain_fp64"] == 0
+
+
+def test_ncu_context_of_the_chosen_form_is_self_consistent():
+    # the executed FP32 flops per system and the instructions per method
+    # flop come from one capture of 262,144 systems
+    ctx = bench.NCU_PIPE_CONTEXT["f2_lean_learned"]
+    assert 0.0 < ctx["fma_pipe_cycles_active"] <= ctx["issue_active"] <= 1.0
+    flops_262k = ctx["fp32_flops_executed_per_system"] * 262144
+    # FP32 flops (FMA = 2) exceed the FP32 instructions, which exceed the method flops
+    assert flops_262k > ctx["fp32_thread_inst_per_method_flop"] * 197.86e9 > 197.86e9
