@@ -122,6 +122,31 @@ def test_network_and_log_options_are_checked_before_any_launch():
     B.release(h)
 
 
+def test_two_float_rkck_families_are_checked_before_any_launch():
+    # the two-float RKCK is built for van der Pol systems and chains: other
+    # families are refused by the argument checks (no GPU needed), while
+    # these two pass them and go on to the device
+    lib = B.load()
+    cases = ((W.massaction(4, seed=0), B.ODE_ERR_UNSUPPORTED), (W.bruss(4, n=3, seed=0), B.ODE_ERR_UNSUPPORTED),
+             (W.vdp(4, seed=0), None))
+    for w, code in cases:
+        h = B.register_workload(w)
+        y, p = np.ascontiguousarray(w.y0), np.ascontiguousarray(w.params)
+        out = np.empty_like(y)
+        for prec in (B.ODE_PREC_F2, B.ODE_PREC_F2_LEAN):
+            o = B.Opts()
+            o.precision = prec
+            o.io = B.ODE_IO_HOST
+            rc = lib.rkck_integrate(h, 4, C.c_void_p(y.ctypes.data), C.c_void_p(p.ctypes.data), w.t0, w.tend,
+                                    w.rtol, w.atol, C.byref(o), C.c_void_p(out.ctypes.data), None, None)
+            if code is not None:
+                assert rc == code, (w.name, prec, rc)
+            else:
+                assert rc != B.ODE_ERR_UNSUPPORTED and rc != B.ODE_ERR_ARG, (w.name, prec, rc)
+        assert lib.ode_rhs_prepare(h, 0, B.ODE_PREC_F2_LEAN) == (B.ODE_ERR_UNSUPPORTED if code else B.ODE_OK)
+        B.release(h)
+
+
 def test_generated_network_kernels_compile():
     """ode_rhs_prepare compiles the straight-line network kernels (NVRTC);
     without a device this is a compile-only check."""
