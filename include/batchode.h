@@ -310,8 +310,10 @@ int ode_rhs_release(int32_t rhs_handle);
  * on disk (directory BATCHODE_CACHE_DIR, else $HOME/.cache/batchode).
  * BATCHODE_JIT_MINBLOCKS overrides the register budget of the generated
  * kernels (that many 128-thread blocks resident per SM; defaults 2 for
- * ODE_PREC_FP64, 3 for the mixed forms) and BATCHODE_JIT_VERBOSE=1 prints
- * the compiler's resource report to stderr.
+ * ODE_PREC_FP64, 3 for the mixed forms), BATCHODE_JIT_LOCKSTEP (0-2) the
+ * one-launch kernel's step-end hold (2, block-wide, for the two-float forms;
+ * 0, warp-level, for the others) and BATCHODE_JIT_VERBOSE=1 prints the
+ * compiler's resource report to stderr.
  * Without a visible device only the compilation (and disk cache) happens.
  * Other families need no preparation and return ODE_OK.  Errors:
  * ODE_ERR_HANDLE, ODE_ERR_ARG, ODE_ERR_UNSUPPORTED (NVRTC missing or the
@@ -321,8 +323,11 @@ int ode_rhs_prepare(int32_t rhs_handle, int32_t method, int32_t precision);
 /* Integrate nsys systems from t0 to tend with the adaptive RKCK method.
  * y0, params: [neq][nsys] and [n_params][nsys] FP64; y_out: [neq][nsys].
  * rtol > 0, atol >= 0, tend > t0 (tend == t0 copies y0).  opts may be NULL
- * (defaults).  Errors: ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA,
- * ODE_ERR_NOMEM, ODE_ERR_UNSUPPORTED. */
+ * (defaults).  Precision forms: FP64 and the FP32 forms for every family;
+ * the two-float forms for van der Pol systems and oscillator chains (other
+ * families: ODE_ERR_UNSUPPORTED before any device work).  Errors:
+ * ODE_ERR_ARG, ODE_ERR_HANDLE, ODE_ERR_CUDA, ODE_ERR_NOMEM,
+ * ODE_ERR_UNSUPPORTED. */
 int rkck_integrate(int32_t rhs, int64_t nsys, const double* y0, const double* params, double t0,
                    double tend, double rtol, double atol, const ode_opts* opts, double* y_out,
                    const ode_stats* stats, void* stream);
