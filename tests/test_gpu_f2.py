@@ -63,7 +63,9 @@ def test_vdp_rkck_f2(prec, mapping):
     # configuration c0 (4096 van der Pol systems, RKCK over t in [0, 20],
     # rtol 1e-6) in two-float RKCK: the systems cross their limit cycles
     # several times, where FP32 stages drift by ~3e-4
-    check_f2(W.vdp(4096, seed=0), prec, method="rkck", mapping=mapping, p999=BAR, same_frac=0.99, max_bound=1e-3)
+    # (measured: p99.9 2.3e-7 / 5.0e-7, max 1.0e-6 / 2.4e-6, 99.95 % / 99.98 %
+    # identical step counts for F2 / F2_LEAN, both mappings)
+    check_f2(W.vdp(4096, seed=0), prec, method="rkck", mapping=mapping, p999=2e-6, same_frac=0.999, max_bound=BAR)
 
 
 @pytest.mark.parametrize("prec", F2_FORMS)
@@ -74,7 +76,8 @@ def test_chain_f2(prec, method, n):
     # by two-float RKCK and RKC: 40 systems over t in [0, 5]
     from test_gpu_parity import chain_workload
     w = chain_workload(40, n, n, W.METHOD_RKCK if method == "rkck" else W.METHOD_RKC)
-    check_f2(w, prec, method=method, p999=BAR, same_frac=0.9, max_bound=BAR, rhs_frac=None)
+    # (measured: every system takes the oracle's steps, max error 5.3e-7)
+    check_f2(w, prec, method=method, p999=5e-6, same_frac=0.95, max_bound=5e-6, rhs_frac=None)
 
 
 @pytest.mark.parametrize("prec", F2_FORMS)

@@ -86,10 +86,12 @@ def test_two_float_plan_against_oracle(batch, prec):
     same = (g["n_accept"] == ref.n_accept) & (g["n_reject"] == ref.n_reject)
     grid = b.kind == B.ODE_RHS_BRUSS1D
     assert grid.any() and (~grid).any()
-    for name, sel in (("grids", grid), ("chains", ~grid)):
+    # (measured: grids p99.9 1.3e-9 / 1.8e-10, chains 2.3e-6 / 7.4e-10 for
+    # F2_LEAN / F2, every step count equal)
+    for name, sel, p999 in (("grids", grid, 1e-7), ("chains", ~grid, 1e-5)):
         print(prec, name, "p99.9", np.quantile(e[sel], 0.999), "median", np.median(e[sel]), "max", e[sel].max(),
               "same counts", same[sel].mean())
-        assert np.quantile(e[sel], 0.999) <= 1e-5
+        assert np.quantile(e[sel], 0.999) <= p999
         assert np.median(e[sel]) <= 1e-8
         assert same[sel].mean() >= 0.99
     # every bucket took two-float kernels: the warp-wide defaults, or (FP32
